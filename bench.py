@@ -1,0 +1,450 @@
+"""Benchmark: useful TFLOP/s of the irrep-aligned contraction, split-BF16 vs FP64.
+
+Workload (default): the MPS transfer step under Z_8 symmetry,
+  E'[g,d] = sum_{a,b,s} E[a,b] A[a,s,g] A[b,s,d],
+evaluated as two irrep-aligned contractions X = einsum('ab,asg->bsg', E, A) and
+E' = einsum('bsg,bsd->gd', X, A), with bond dimension 8 sectors x 128 and
+physical dimension 8 sectors x 2 (seeded synthetic N(0,1) reduced forms).
+One step = both contractions, standard reduced forms in and out.
+
+Metric: useful TFLOP/s = symmetry-reduced GEMM flops (2 * n_Q * M * N * K per
+contraction) / device time of the step.  The split-BF16 form is the headline
+value; the FP64 form and the relative errors of both against the CPU float64
+oracle are reported beside it.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                       [--workload mps|cc_ladder] [--precision split_bf16|fp64|tf32]
+Multi-GPU (torchrun): replicas only; each rank runs the whole workload.
+"""
+from __future__ import annotations
+
+import os
+
+_CORES = len(os.sched_getaffinity(0))
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, str(_CORES))
+
+import argparse
+import hashlib
+import json
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as WL  # noqa: E402
+
+L2_FLUSH_BYTES = 256 << 20
+
+
+def spec(t):
+    return (t.signs, t.charge, t.dims)
+
+
+# ---------------------------------------------------------------------------
+# workloads: list of (einsum, moduli, sym_u, sym_v) steps and input arrays
+# ---------------------------------------------------------------------------
+
+def mps_workload():
+    E = WL.draw(WL.MPS_E, (WL.MPS_G,))
+    A = WL.draw(WL.MPS_A, (WL.MPS_G,))
+    name = "mps_transfer_Z8_bond8x128_phys8x2 (X=E.A, E'=X.A; two aligned contractions)"
+    return name, E, A
+
+
+def cc_workload():
+    c = WL.CC_LADDER
+    return "cc_ladder_Z8_virt8x32_occ8x8 (w=v.t)", WL.draw(c.u, c.moduli), WL.draw(c.v, c.moduli)
+
+
+# ---------------------------------------------------------------------------
+# oracle (CPU float64) -- cpu_baseline leg and the reference arm only
+# ---------------------------------------------------------------------------
+
+def oracle_step(workload, a, b):
+    import oracle as O
+    if workload == "mps":
+        g = O.Group((WL.MPS_G,))
+        p1 = O.plan(WL.MPS_STEP1, g, O.Sym(*spec(WL.MPS_E)), O.Sym(*spec(WL.MPS_A)))
+        p2 = O.plan(WL.MPS_STEP2, g, p1.sym_w, O.Sym(*spec(WL.MPS_A)))
+
+        def run():
+            x = O.contract_blockloop(p1, a, b)
+            return O.contract_blockloop(p2, x, b)
+        return run
+    c = WL.CC_LADDER
+    p = O.plan(c.einsum, O.Group(c.moduli), O.Sym(*spec(c.u)), O.Sym(*spec(c.v)))
+    # bounded sample: one irrep Q of the block loop (1/G of the flops)
+    return lambda: O.contract_blockloop(p, a, b)
+
+
+def time_oracle(workload, a, b, budget_s=12.0, max_reps=50):
+    run = oracle_step(workload, a, b)
+    out = run()
+    ts = []
+    t_end = time.perf_counter() + budget_s
+    while len(ts) < max_reps and (not ts or time.perf_counter() < t_end):
+        t0 = time.perf_counter()
+        run()
+        ts.append(time.perf_counter() - t0)
+    return out, statistics.median(ts), len(ts)
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index=0):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.dev = device_index
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}",
+                                          f"--query-gpu={self.FIELDS}", "--format=csv,noheader",
+                                          "-lms", "100"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        try:
+            rows = [l.strip().split(", ") for l in open(self.path) if l.strip()]
+        except Exception:
+            return out
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1].split()[0]))
+                mx.append(float(r[2].split()[0]))
+                for n, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(n)
+            except Exception:
+                continue
+        if sm:
+            out.update(sm_mhz=statistics.median(sm), sm_max_mhz=max(mx), samples=len(sm))
+        out["reasons"] = sorted(reasons)
+        return out
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(os.path.join(ROOT, "paper_2007_08056_gb300", "csrc"))):
+        with open(os.path.join(ROOT, "paper_2007_08056_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def load_traffic(kernel_key):
+    """DRAM traffic per launch from the committed ncu summary, if it was taken
+    on the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        e = d.get(kernel_key)
+        if e and e.get("source_hash") == kernel_source_hash():
+            return e.get("bytes_per_launch")
+    except Exception:
+        pass
+    return None
+
+
+def peaks():
+    p = {"hbm_gbs": 6692.1, "bf16_tflops": 1925.9, "bf16_tflops_sustained": 1723.2, "src": "fallback"}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        p.update({k: d[k] for k in ("hbm_gbs", "bf16_tflops", "bf16_tflops_sustained") if k in d})
+        p["src"] = "measured"
+    except Exception:
+        pass
+    return p
+
+
+def run_ours(args, rank, world):
+    import torch
+    import paper_2007_08056_gb300 as sc
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+    dev = torch.device("cuda")
+    if args.workload == "mps":
+        name, Eh, Ah = mps_workload()
+        E, A = torch.from_numpy(Eh).to(dev), torch.from_numpy(Ah).to(dev)
+
+        def make(prec):
+            p1 = sc.Plan(WL.MPS_STEP1, (WL.MPS_G,), spec(WL.MPS_E), spec(WL.MPS_A), prec)
+            p2 = sc.Plan(WL.MPS_STEP2, (WL.MPS_G,), p1.sym_w, spec(WL.MPS_A), prec)
+            X = torch.empty(p1.shape_w, dtype=torch.float64, device=dev)
+            out = torch.empty(p2.shape_w, dtype=torch.float64, device=dev)
+
+            def step(e=E, a=A):
+                p1.contract(e, a, out=X)
+                p2.contract(X, a, out=out)
+                return out
+            return [p1, p2], step, out
+        inputs_host = [Eh, Ah]
+    else:
+        name, Uh, Vh = cc_workload()
+        U, V = torch.from_numpy(Uh).to(dev), torch.from_numpy(Vh).to(dev)
+        c = WL.CC_LADDER
+
+        def make(prec):
+            p = sc.Plan(c.einsum, c.moduli, spec(c.u), spec(c.v), prec)
+            out = torch.empty(p.shape_w, dtype=torch.float64, device=dev)
+
+            def step(a=U, b=V):
+                p.contract(a, b, out=out)
+                return out
+            return [p], step, out
+        inputs_host = [Uh, Vh]
+
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    ev_s = torch.cuda.Event(enable_timing=True)
+    ev_e = torch.cuda.Event(enable_timing=True)
+
+    def timed(step, n, warm, per_plan=None):
+        for _ in range(warm):
+            step()
+        torch.cuda.synchronize()
+        times, phases = [], []
+        for _ in range(n):
+            flush.fill_(1)                       # L2 flush, outside the timed window
+            ev_s.record()
+            step()
+            ev_e.record()
+            ev_e.synchronize()
+            times.append(ev_s.elapsed_time(ev_e))
+            if per_plan:
+                phases.append([pl.phase_times() for pl in per_plan])
+        return times, phases
+
+    plans, step, out = make(args.precision)
+    for pl in plans:
+        pl.profile(True)
+    flops = sum(pl.useful_flops for pl in plans)
+
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with Clocks(torch.cuda.current_device()) as clk:
+        times, phases = timed(step, args.steps, args.warmup, plans)
+    torch.cuda.synchronize()
+    for pl in plans:
+        pl.check_device_error()
+    ms = statistics.mean(times)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+        torch.distributed.barrier()
+    value = world * flops / (ms * 1e-3) / 1e12
+
+    # per-kernel phases (averaged over the timed steps)
+    prep = [statistics.mean(ph[i][0] for ph in phases) for i in range(len(plans))]
+    gemm = [statistics.mean(ph[i][1] for ph in phases) for i in range(len(plans))]
+    launches_per_step = sum(phases[-1][i][2] for i in range(len(plans)))
+
+    # accuracy of the forms against the oracle (outside any timed region)
+    res = {}
+    if rank == 0:
+        ref = oracle_step(args.workload, *inputs_host)()
+        got = step().cpu().numpy()
+        res[args.precision] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    # the FP64 form beside it
+    fp64 = None
+    if args.precision != "fp64" and not args.no_fp64:
+        plans64, step64, _ = make("fp64")
+        t64, _ = timed(step64, max(2, min(args.steps, 5)), 1)
+        ms64 = statistics.mean(t64)
+        fp64 = {"value": round(world * flops / (ms64 * 1e-3) / 1e12, 4), "ms_per_step": round(ms64, 4)}
+        if rank == 0:
+            got = step64().cpu().numpy()
+            res["fp64"] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+
+    # end to end through the public API from pinned host buffers
+    hin = [torch.from_numpy(x).pin_memory() for x in inputs_host]
+    dins = [torch.empty(x.shape, dtype=torch.float64, device=dev) for x in inputs_host]
+    hout = torch.empty(tuple(out.shape), dtype=torch.float64).pin_memory()
+
+    def e2e_step():
+        for h, d in zip(hin, dins):
+            d.copy_(h, non_blocking=True)
+        o = step(*dins)
+        hout.copy_(o, non_blocking=True)
+    t_e2e, _ = timed(e2e_step, args.steps, args.warmup)
+    ms_e2e = statistics.mean(t_e2e)
+    if world > 1:
+        t = torch.tensor([ms_e2e], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_e2e = float(t.item())
+
+    pk = peaks()
+    # dominant kernel: the GEMM launch of the heavier contraction
+    gemm_total = sum(gemm)
+    prep_total = sum(prep)
+    i_dom = int(np.argmax(gemm))
+    pl = plans[i_dom]
+    if args.precision == "split_bf16":
+        pairs = pl.info.n_slices * (pl.info.n_slices + 1) // 2
+        per_launch_flops = pl.useful_flops * pairs
+        peak = pk["bf16_tflops"]
+        bound, unit = "tensor", "TFLOP/s"
+        achieved = per_launch_flops / (gemm[i_dom] * 1e-3) / 1e12
+        key = "gemm_split_bf16_" + args.workload
+    elif args.precision == "tf32":
+        per_launch_flops = pl.useful_flops
+        peak = pk["bf16_tflops"] / 2
+        bound, unit = "tensor", "TFLOP/s"
+        achieved = per_launch_flops / (gemm[i_dom] * 1e-3) / 1e12
+        key = "gemm_tf32_" + args.workload
+    else:
+        per_launch_flops = pl.useful_flops
+        peak = 1.25
+        bound, unit = "alu", "TFLOP/s"
+        achieved = per_launch_flops / (gemm[i_dom] * 1e-3) / 1e12
+        key = "gemm_f64_" + args.workload
+    clocks = clk.summary()
+    line = {
+        "metric": "useful TFLOP/s, split-BF16 vs FP64 irrep-aligned contraction at stated rel err",
+        "value": round(value, 4),
+        "unit": "TFLOP/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": {"split_bf16": "bf16 slices x5, fp32 accumulate, int64 combine, f64 out",
+                  "tf32": "tf32, fp32 accumulate, f64 out", "fp64": "f64"}[args.precision],
+        "data": "synthetic (seeded N(0,1) reduced forms)",
+        "config": {"workload": name, "precision": args.precision,
+                   "n_slices": plans[0].info.n_slices, "useful_gflop_per_step": flops / 1e9,
+                   "l2": "flushed (256 MiB write) between timed steps, outside the events",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "rel_err_vs_oracle": {k: float(f"{v:.3e}") for k, v in res.items()},
+        "fp64_form": fp64,
+        "phases_ms": {"prep": [round(x, 4) for x in prep], "gemm": [round(x, 4) for x in gemm]},
+        "roofline": {"bound": bound, "achieved": round(achieved, 3), "peak": peak, "unit": unit,
+                     "frac": round(achieved / peak, 4), "traffic": load_traffic(key),
+                     "kernel": key, "peak_src": pk["src"] if bound != "alu" else
+                     "1.25 TFLOP/s nominal FP64 (measured cuBLAS DGEMM 1.1)"},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks,
+        "e2e": {"value": round(world * flops / (ms_e2e * 1e-3) / 1e12, 4), "unit": "TFLOP/s",
+                "ms_per_step": round(ms_e2e, 4),
+                "h2d_bytes_per_step": int(sum(x.nbytes for x in inputs_host)),
+                "d2h_bytes_per_step": int(out.numel() * 8)},
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        _, t_or, reps = time_oracle(args.workload, *inputs_host, budget_s=args.cpu_budget)
+        line["cpu_baseline"] = {"value": round(flops / t_or / 1e12, 6), "unit": "TFLOP/s",
+                                "cores": _CORES, "kind": "oracle",
+                                "sample": f"whole step (both contractions), block-loop route, "
+                                          f"median of {reps} runs, {t_or * 1e3:.1f} ms each"}
+    return line
+
+
+def run_reference(args, rank, world):
+    """The oracle on the host cores, on the same workload and metric."""
+    if rank != 0:
+        return None
+    if args.workload == "mps":
+        name, a, b = mps_workload()
+        g = WL.MPS_G
+        import oracle as O
+        p1 = O.plan(WL.MPS_STEP1, O.Group((g,)), O.Sym(*spec(WL.MPS_E)), O.Sym(*spec(WL.MPS_A)))
+        p2 = O.plan(WL.MPS_STEP2, O.Group((g,)), p1.sym_w, O.Sym(*spec(WL.MPS_A)))
+        flops = 2.0 * sum(len(O.q_set(p)) * np.prod(O.aligned_dims(p)[1:]) for p in (p1, p2))
+    else:
+        raise SystemExit("reference arm: mps workload only")
+    run = oracle_step(args.workload, a, b)
+    for _ in range(args.warmup):
+        run()
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        run()
+        ts.append(time.perf_counter() - t0)
+    ms = statistics.mean(ts) * 1e3
+    value = flops / (ms * 1e-3) / 1e12
+    return {
+        "impl": "reference",
+        "metric": "useful TFLOP/s, split-BF16 vs FP64 irrep-aligned contraction at stated rel err",
+        "value": round(value, 6), "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": name, "precision": "fp64 (CPU oracle, block loop)"},
+        "cpu_baseline": {"value": round(value, 6), "unit": "TFLOP/s", "cores": _CORES,
+                         "kind": "oracle", "sample": "whole step per timed step"},
+        "e2e": {"value": round(value, 6), "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["mps", "cc_ladder"], default="mps")
+    ap.add_argument("--precision", choices=["split_bf16", "fp64", "tf32"], default="split_bf16")
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+        if line is not None:
+            print(json.dumps(line), flush=True)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        torch.distributed.init_process_group("nccl")
+    line = run_ours(args, rank, world)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

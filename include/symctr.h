@@ -1,0 +1,192 @@
+/*
+ * symctr.h -- C ABI of the irrep-aligned contraction library for tensors with
+ * cyclic-group (Z_G, or product of cyclic groups) symmetry, GB300 / sm_103a.
+ *
+ * The operation (Sec. 2.2, Eq. ctr and Algorithm 2 of "Automatic Transformation
+ * of Irreducible Representations for Efficient Contraction of Tensors with
+ * Cyclic Group Symmetry"):
+ *
+ *   W[i.., j..] = sum_{k..} U[i.., k..] V[k.., j..]
+ *
+ * where each tensor vanishes unless its sector labels obey a conservation law
+ * sum_mu c_mu q_mu == Z (mod G), c_mu = +-1 (Eq. symtsr).  Operands and result
+ * are passed in STANDARD REDUCED FORM: a C-contiguous float64 array of shape
+ * [G]*(N-1) + [D_0, ..., D_{N-1}] whose first N-1 axes are the sector labels of
+ * modes 0..N-2 and whose last N axes are the in-block indices; the sector of
+ * the last mode is implicit, q_{N-1} = c_{N-1} (Z - sum_{mu<N-1} c_mu q_mu)
+ * (Sec. 2.1 and its footnote; API listing of Sec. 3, shape [G,G,G,N,N,N,N]).
+ * For a product group Z_m1 x ... x Z_mr a sector label is the mixed-radix
+ * flattening of its components, first modulus most significant.
+ *
+ * Internally each operand is remapped to an aligned form indexed by an
+ * auxiliary irrep Q (Sec. 2.1 / Alg. 2): U_hat[Q][m][kappa], V_hat[Q][n][kappa],
+ * W_hat[Q][m][n], so that the contraction is one batched GEMM over Q, and the
+ * result is mapped back to W's standard reduced form.  Q is defined as
+ * Q = sum_{k contracted} c^U_k q_k (mod G).  The aligned layouts are:
+ *   m     = (q of free-U modes except the last, b of all free-U modes)
+ *   kappa = (q of contracted modes except the last, b of all contracted modes)
+ *   n     = (q of free-V modes except the last, b of all free-V modes)
+ * sector digits before block digits, C order, modes in the order they appear
+ * in U (free-U, contracted) or V (free-V); only the irreps Q that can carry
+ * nonzero entries are stored (symctr_plan_info.n_q of them, ascending).
+ *
+ * Conventions of every call
+ *   Ownership : the caller owns every device pointer, the workspace and the
+ *               stream.  A plan owns host metadata only; no call allocates
+ *               device memory.
+ *   Errors    : every call returns a status and never throws across the ABI.
+ *               Kernels never trap: a device-side failure (a bounded wait that
+ *               expired, a non-finite input) is recorded in the first word of
+ *               the workspace and reported by symctr_check_device_error.
+ *   Asynchrony: every call that takes a stream is asynchronous on it (the
+ *               stream is a cudaStream_t; NULL = legacy default stream).
+ *   Data      : float64, C-contiguous, device memory, 16-byte aligned; outputs
+ *               are fully overwritten.  Inputs must be finite.
+ */
+#ifndef SYMCTR_H
+#define SYMCTR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define SYMCTR_API __attribute__((visibility("default")))
+#else
+#define SYMCTR_API
+#endif
+
+#define SYMCTR_MAX_ORDER 8      /* modes per tensor */
+#define SYMCTR_MAX_MODULI 4     /* cyclic factors of the group */
+#define SYMCTR_MAX_GROUP 256    /* order of the group */
+
+typedef struct symctr_plan symctr_plan;   /* opaque */
+
+typedef enum {
+  SYMCTR_OK = 0,
+  SYMCTR_ERR_EINSUM = 1,        /* malformed einsum, repeated or trace/batch labels */
+  SYMCTR_ERR_SIGNS = 2,         /* contracted coefficients do not agree up to one sign */
+  SYMCTR_ERR_SHAPE = 3,         /* sector dims of a contracted mode differ; bad modulus */
+  SYMCTR_ERR_CHARGE = 4,        /* a given output law contradicts the derived one */
+  SYMCTR_ERR_UNSUPPORTED = 5,   /* order > 8, group > 256, ... */
+  SYMCTR_ERR_NULLPTR = 6,
+  SYMCTR_ERR_WORKSPACE = 7,     /* workspace smaller than symctr_plan_info.workspace_bytes */
+  SYMCTR_ERR_CUDA = 8,          /* a CUDA runtime/driver call failed */
+  SYMCTR_ERR_DEVICE_TIMEOUT = 9,/* a kernel's bounded wait expired */
+  SYMCTR_ERR_OVERFLOW = 10,     /* an extent or offset exceeds 64-bit / kernel limits */
+  SYMCTR_ERR_NONFINITE = 11,    /* a non-finite input reached the split-precision form */
+  SYMCTR_ERR_ARGUMENT = 12      /* any other invalid argument */
+} symctr_status;
+
+typedef enum {
+  SYMCTR_FP64 = 0,        /* float64 FMA throughout */
+  SYMCTR_SPLIT_BF16 = 1,  /* Ozaki-style BF16 slices on tcgen05, exact FP32 partial
+                             sums, integer recombination, one rounding to float64 */
+  SYMCTR_TF32 = 2         /* operands rounded to TF32 on tcgen05, FP32 accumulation */
+} symctr_precision;
+
+typedef struct {
+  int32_t order_u, order_v, order_w;
+  int32_t s, t, v;              /* free-U, free-V and contracted mode counts (Eq. ctr) */
+  int32_t sigma;                /* c^V_k = sigma c^U_k on contracted modes (+-1) */
+  int32_t n_moduli;
+  int32_t moduli[SYMCTR_MAX_MODULI];
+  int32_t group_order;          /* G = product of moduli */
+  int32_t precision;            /* symctr_precision */
+  int32_t n_slices;             /* BF16 slices per operand (split form), else 0 */
+  int8_t signs_w[SYMCTR_MAX_ORDER];
+  int32_t charge_w[SYMCTR_MAX_MODULI];
+  int64_t dims_w[SYMCTR_MAX_ORDER];
+  int64_t numel_u, numel_v, numel_w;   /* elements of the standard reduced forms */
+  int64_t M, N, K;              /* aligned GEMM extents per irrep Q */
+  int32_t n_q;                  /* irreps Q that carry work (0, 1 or G) */
+  int32_t q_single;             /* the irrep when n_q == 1, else -1 */
+  int64_t aligned_numel_u;      /* n_q * M * K */
+  int64_t aligned_numel_v;      /* n_q * N * K */
+  int64_t aligned_numel_w;      /* n_q * M * N */
+  double useful_flops;          /* 2 * n_q * M * N * K: symmetry-reduced GEMM flops */
+  double transform_bytes;       /* algorithmic bytes of the alignment transforms */
+  uint64_t workspace_bytes;     /* device workspace symctr_contract needs */
+  uint64_t workspace_bytes_backward; /* device workspace symctr_contract_backward needs */
+} symctr_plan_info;
+
+/* Build a plan for W = einsum(spec, U, V).
+ *  einsum   : "u_labels,v_labels->w_labels" (letters; each label at most once per
+ *             operand; the output lists exactly the free labels, in any order).
+ *  moduli   : n_moduli cyclic factors (product G <= 256), e.g. {3} or {2,3}.
+ *  signs_*  : per-mode coefficient +1/-1 of each operand's law (Eq. symtsr).
+ *  charge_* : n_moduli components of each operand's remainder Z.
+ *  dims_*   : per-mode sector (block) dimension D_mu >= 1.
+ *  signs_w_or_null / charge_w_or_null : optional check of the output law; the
+ *             derived law (c^U on free-U modes, -sigma c^V on free-V modes,
+ *             Z_U - sigma Z_V) or its global negation is accepted.
+ *  prec, n_slices : precision form; n_slices = 0 picks the default (5).
+ * Returns SYMCTR_OK and *out, or an error status and *out = NULL.  Host only. */
+SYMCTR_API symctr_status symctr_plan_create(const char* einsum, int n_moduli, const int32_t* moduli,
+                                 const int8_t* signs_u, const int32_t* charge_u,
+                                 const int8_t* signs_v, const int32_t* charge_v,
+                                 const int64_t* dims_u, const int64_t* dims_v,
+                                 const int8_t* signs_w_or_null, const int32_t* charge_w_or_null,
+                                 symctr_precision prec, int n_slices, symctr_plan** out);
+
+/* Fill *out with the plan's derived quantities.  Host only. */
+SYMCTR_API symctr_status symctr_plan_query(const symctr_plan* plan, symctr_plan_info* out);
+
+/* Bit-exact alignment transforms (Alg. 2 input transformations and output step).
+ *  operand   : 0 = U, 1 = V, 2 = W.
+ *  direction : +1 standard reduced form (src) -> aligned form (dst);
+ *              -1 aligned form (src) -> standard reduced form (dst; entries whose
+ *              irrep Q carries no work are written as 0).
+ *  Aligned sizes are aligned_numel_{u,v,w}; reduced sizes numel_{u,v,w}. */
+SYMCTR_API symctr_status symctr_align(const symctr_plan* plan, int operand, int direction,
+                           const double* src, double* dst, void* stream);
+
+/* W = einsum(U, V) in the plan's precision form, from and to standard reduced forms.
+ *  workspace : device scratch of at least workspace_bytes (256-byte aligned); its first
+ *              word receives device-side error codes. */
+SYMCTR_API symctr_status symctr_contract(const symctr_plan* plan, const double* u_red, const double* v_red,
+                              double* w_red, void* workspace, size_t workspace_bytes,
+                              void* stream);
+
+/* Gradients of a scalar loss L through W = einsum(U, V), given gW = dL/dW:
+ *   gU = einsum(w_labels, v_labels -> u_labels)(gW, V)   (written if grad_u_red != NULL)
+ *   gV = einsum(u_labels, w_labels -> v_labels)(U, gW)   (written if grad_v_red != NULL)
+ * Both are irrep-aligned contractions in the plan's precision form; the aligned
+ * operands are recomputed from the standard forms (nothing is saved from the
+ * forward).  gU is in U's layout and gV in V's layout. */
+SYMCTR_API symctr_status symctr_contract_backward(const symctr_plan* plan, const double* grad_w_red,
+                                       const double* u_red, const double* v_red,
+                                       double* grad_u_red, double* grad_v_red,
+                                       void* workspace, size_t workspace_bytes, void* stream);
+
+/* Synchronise `stream`, read the device error word from `workspace` and clear it.
+ * Returns SYMCTR_OK, SYMCTR_ERR_DEVICE_TIMEOUT, SYMCTR_ERR_NONFINITE or SYMCTR_ERR_CUDA. */
+SYMCTR_API symctr_status symctr_check_device_error(const symctr_plan* plan, void* workspace, void* stream);
+
+/* Phase timing for measurement.  enable = 1 creates CUDA events on the plan;
+ * each later symctr_contract on it records them on the call's stream around
+ * the operand preparation (split / TF32 transforms) and the GEMM launch.
+ * enable = 0 destroys them.  Host only; allocates no device memory. */
+SYMCTR_API symctr_status symctr_profile_enable(symctr_plan* plan, int enable);
+
+/* Durations in milliseconds of the two phases of the last symctr_contract on
+ * the plan (prep_ms = 0 for the float64 form) and the number of kernels that
+ * call launched (launches may be NULL).  Waits for the events. */
+SYMCTR_API symctr_status symctr_profile_read(const symctr_plan* plan, float* prep_ms,
+                                             float* gemm_ms, int* launches);
+
+/* Human-readable name of a status. */
+SYMCTR_API const char* symctr_status_string(symctr_status status);
+
+/* Text of the last error raised on the calling host thread (empty if none). */
+SYMCTR_API const char* symctr_last_error_detail(void);
+
+SYMCTR_API void symctr_plan_destroy(symctr_plan* plan);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SYMCTR_H */

@@ -1,0 +1,307 @@
+"""Irrep-aligned contraction of cyclic-group-symmetric tensors on GB300.
+
+Thin Python binding over the C ABI of ``libsymctr.so`` (include/symctr.h):
+argument marshalling only.  Every step of the contraction (alignment
+transforms, the batched GEMM, the map back to the output's reduced form)
+runs in the library's CUDA kernels.  PyTorch provides device memory and
+streams.  There is no CPU fallback: if the library cannot be loaded, every
+entry point raises.
+
+    import paper_2007_08056_gb300 as sc
+    plan = sc.Plan("abkl,klij->abij", moduli=[3],
+                   sym_u=([1, 1, -1, -1], [0], [4, 4, 4, 4]),
+                   sym_v=([1, 1, -1, -1], [0], [4, 4, 4, 4]),
+                   precision="split_bf16")
+    w = plan.contract(u, v)          # u, v: float64 CUDA tensors in reduced form
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional, Sequence, Tuple
+
+import torch
+
+from . import build as _build
+
+MAX_ORDER = 8
+MAX_MODULI = 4
+
+PRECISIONS = {"fp64": 0, "split_bf16": 1, "tf32": 2}
+
+STATUS = {
+    0: "SYMCTR_OK", 1: "SYMCTR_ERR_EINSUM", 2: "SYMCTR_ERR_SIGNS", 3: "SYMCTR_ERR_SHAPE",
+    4: "SYMCTR_ERR_CHARGE", 5: "SYMCTR_ERR_UNSUPPORTED", 6: "SYMCTR_ERR_NULLPTR",
+    7: "SYMCTR_ERR_WORKSPACE", 8: "SYMCTR_ERR_CUDA", 9: "SYMCTR_ERR_DEVICE_TIMEOUT",
+    10: "SYMCTR_ERR_OVERFLOW", 11: "SYMCTR_ERR_NONFINITE", 12: "SYMCTR_ERR_ARGUMENT",
+}
+
+
+class SymctrError(RuntimeError):
+    def __init__(self, status: int, detail: str):
+        super().__init__(f"{STATUS.get(status, status)}: {detail}")
+        self.status = status
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [
+        ("order_u", ctypes.c_int32), ("order_v", ctypes.c_int32), ("order_w", ctypes.c_int32),
+        ("s", ctypes.c_int32), ("t", ctypes.c_int32), ("v", ctypes.c_int32),
+        ("sigma", ctypes.c_int32), ("n_moduli", ctypes.c_int32),
+        ("moduli", ctypes.c_int32 * MAX_MODULI), ("group_order", ctypes.c_int32),
+        ("precision", ctypes.c_int32), ("n_slices", ctypes.c_int32),
+        ("signs_w", ctypes.c_int8 * MAX_ORDER), ("charge_w", ctypes.c_int32 * MAX_MODULI),
+        ("dims_w", ctypes.c_int64 * MAX_ORDER),
+        ("numel_u", ctypes.c_int64), ("numel_v", ctypes.c_int64), ("numel_w", ctypes.c_int64),
+        ("M", ctypes.c_int64), ("N", ctypes.c_int64), ("K", ctypes.c_int64),
+        ("n_q", ctypes.c_int32), ("q_single", ctypes.c_int32),
+        ("aligned_numel_u", ctypes.c_int64), ("aligned_numel_v", ctypes.c_int64),
+        ("aligned_numel_w", ctypes.c_int64),
+        ("useful_flops", ctypes.c_double), ("transform_bytes", ctypes.c_double),
+        ("workspace_bytes", ctypes.c_uint64), ("workspace_bytes_backward", ctypes.c_uint64),
+    ]
+
+
+_LIB = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libsymctr.so (building it in-tree if absent).  Raises on failure."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(_build.LIB):
+        if not build_if_missing:
+            raise ImportError(f"libsymctr.so not built ({_build.LIB})")
+        _build.build()
+    lib = ctypes.CDLL(_build.LIB)
+    P = ctypes.c_void_p
+    i8p, i32p, i64p = (ctypes.POINTER(ctypes.c_int8), ctypes.POINTER(ctypes.c_int32),
+                       ctypes.POINTER(ctypes.c_int64))
+    lib.symctr_plan_create.argtypes = [ctypes.c_char_p, ctypes.c_int, i32p, i8p, i32p, i8p, i32p,
+                                       i64p, i64p, i8p, i32p, ctypes.c_int, ctypes.c_int,
+                                       ctypes.POINTER(P)]
+    lib.symctr_plan_query.argtypes = [P, ctypes.POINTER(PlanInfo)]
+    lib.symctr_align.argtypes = [P, ctypes.c_int, ctypes.c_int, P, P, P]
+    lib.symctr_contract.argtypes = [P, P, P, P, P, ctypes.c_size_t, P]
+    lib.symctr_contract_backward.argtypes = [P, P, P, P, P, P, P, ctypes.c_size_t, P]
+    lib.symctr_check_device_error.argtypes = [P, P, P]
+    lib.symctr_status_string.argtypes = [ctypes.c_int]
+    lib.symctr_status_string.restype = ctypes.c_char_p
+    lib.symctr_last_error_detail.argtypes = []
+    lib.symctr_last_error_detail.restype = ctypes.c_char_p
+    lib.symctr_profile_enable.argtypes = [P, ctypes.c_int]
+    lib.symctr_profile_read.argtypes = [P, ctypes.POINTER(ctypes.c_float),
+                                        ctypes.POINTER(ctypes.c_float),
+                                        ctypes.POINTER(ctypes.c_int)]
+    lib.symctr_plan_destroy.argtypes = [P]
+    lib.symctr_plan_destroy.restype = None
+    for f in ("symctr_plan_create", "symctr_plan_query", "symctr_align", "symctr_contract",
+              "symctr_contract_backward", "symctr_check_device_error", "symctr_profile_enable",
+              "symctr_profile_read"):
+        getattr(lib, f).restype = ctypes.c_int
+    _LIB = lib
+    return lib
+
+
+def _check(status: int):
+    if status != 0:
+        lib = load()
+        raise SymctrError(status, lib.symctr_last_error_detail().decode())
+
+
+def _arr(ctype, vals):
+    vals = list(vals)
+    return (ctype * max(len(vals), 1))(*vals)
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+@dataclass(frozen=True)
+class SymSpec:
+    """Conservation law of one operand: per-mode signs, remainder, sector dims."""
+    signs: Tuple[int, ...]
+    charge: Tuple[int, ...]
+    dims: Tuple[int, ...]
+
+
+def _spec(x) -> SymSpec:
+    if isinstance(x, SymSpec):
+        return x
+    signs, charge, dims = x
+    return SymSpec(tuple(int(s) for s in signs), tuple(int(c) for c in charge),
+                   tuple(int(d) for d in dims))
+
+
+class Plan:
+    """A contraction plan W = einsum(spec, U, V) over Z_m1 x ... x Z_mr."""
+
+    def __init__(self, einsum: str, moduli: Sequence[int], sym_u, sym_v, precision: str = "fp64",
+                 n_slices: int = 0, sym_w=None):
+        lib = load()
+        self.einsum = einsum
+        self.moduli = tuple(int(m) for m in moduli)
+        self.sym_u, self.sym_v = _spec(sym_u), _spec(sym_v)
+        self.precision = precision
+        su, sv = self.sym_u, self.sym_v
+        sw = _spec(sym_w) if sym_w is not None else None
+        handle = ctypes.c_void_p()
+        st = lib.symctr_plan_create(
+            einsum.encode(), len(self.moduli), _arr(ctypes.c_int32, self.moduli),
+            _arr(ctypes.c_int8, su.signs), _arr(ctypes.c_int32, su.charge),
+            _arr(ctypes.c_int8, sv.signs), _arr(ctypes.c_int32, sv.charge),
+            _arr(ctypes.c_int64, su.dims), _arr(ctypes.c_int64, sv.dims),
+            None if sw is None else _arr(ctypes.c_int8, sw.signs),
+            None if sw is None else _arr(ctypes.c_int32, sw.charge),
+            PRECISIONS[precision], int(n_slices), ctypes.byref(handle))
+        _check(st)
+        self._h = handle
+        info = PlanInfo()
+        _check(lib.symctr_plan_query(self._h, ctypes.byref(info)))
+        self.info = info
+        G = info.group_order
+        self.sym_w = SymSpec(tuple(info.signs_w[i] for i in range(info.order_w)),
+                             tuple(info.charge_w[i] for i in range(info.n_moduli)),
+                             tuple(info.dims_w[i] for i in range(info.order_w)))
+
+        def shape(spec: SymSpec):
+            n = len(spec.dims)
+            return tuple([G] * (n - 1) + list(spec.dims)) if n else ()
+        self.shape_u, self.shape_v, self.shape_w = shape(su), shape(sv), shape(self.sym_w)
+        self._ws = None
+
+    def __del__(self):
+        try:
+            if getattr(self, "_h", None) is not None and _LIB is not None:
+                _LIB.symctr_plan_destroy(self._h)
+                self._h = None
+        except Exception:
+            pass
+
+    # -- workspace -----------------------------------------------------------
+    def workspace(self, backward: bool = False, device=None) -> torch.Tensor:
+        need = max(int(self.info.workspace_bytes), int(self.info.workspace_bytes_backward)
+                   if backward else 0, 256)
+        if self._ws is None or self._ws.numel() < need:
+            self._ws = torch.empty(need, dtype=torch.uint8, device=device or "cuda")
+        return self._ws
+
+    # -- checks --------------------------------------------------------------
+    @staticmethod
+    def _dev64(t: torch.Tensor, shape, name):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64):
+            raise TypeError(f"{name} must be a float64 CUDA tensor")
+        if tuple(t.shape) != tuple(shape):
+            raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+
+    # -- operations ------------------------------------------------------------
+    def contract(self, u: torch.Tensor, v: torch.Tensor, out: Optional[torch.Tensor] = None,
+                 workspace: Optional[torch.Tensor] = None) -> torch.Tensor:
+        self._dev64(u, self.shape_u, "u")
+        self._dev64(v, self.shape_v, "v")
+        if out is None:
+            out = torch.empty(self.shape_w, dtype=torch.float64, device=u.device)
+        self._dev64(out, self.shape_w, "out")
+        ws = workspace if workspace is not None else self.workspace(device=u.device)
+        _check(load().symctr_contract(self._h, _ptr(u), _ptr(v), _ptr(out), _ptr(ws),
+                                      ws.numel(), _stream()))
+        return out
+
+    def backward(self, grad_w: torch.Tensor, u: torch.Tensor, v: torch.Tensor,
+                 need_u: bool = True, need_v: bool = True,
+                 workspace: Optional[torch.Tensor] = None):
+        self._dev64(grad_w, self.shape_w, "grad_w")
+        gu = torch.empty(self.shape_u, dtype=torch.float64, device=u.device) if need_u else None
+        gv = torch.empty(self.shape_v, dtype=torch.float64, device=u.device) if need_v else None
+        ws = workspace if workspace is not None else self.workspace(True, u.device)
+        _check(load().symctr_contract_backward(self._h, _ptr(grad_w), _ptr(u), _ptr(v), _ptr(gu),
+                                               _ptr(gv), _ptr(ws), ws.numel(), _stream()))
+        return gu, gv
+
+    def align(self, operand: int, direction: int, src: torch.Tensor) -> torch.Tensor:
+        """Bit-exact alignment transforms (operand 0=U, 1=V, 2=W; direction +1 std->aligned)."""
+        i = self.info
+        red = [self.shape_u, self.shape_v, self.shape_w][operand]
+        al = [(i.n_q, i.M, i.K), (i.n_q, i.N, i.K), (i.n_q, i.M, i.N)][operand]
+        src_shape, dst_shape = (red, al) if direction > 0 else (al, red)
+        self._dev64(src, src_shape, "src")
+        dst = torch.empty(dst_shape, dtype=torch.float64, device=src.device)
+        _check(load().symctr_align(self._h, operand, direction, _ptr(src), _ptr(dst), _stream()))
+        return dst
+
+    def check_device_error(self, workspace: Optional[torch.Tensor] = None):
+        ws = workspace if workspace is not None else self._ws
+        if ws is None:
+            return
+        _check(load().symctr_check_device_error(self._h, _ptr(ws), _stream()))
+
+    def profile(self, enable: bool = True):
+        """Record CUDA events around the operand preparation and the GEMM of
+        each later contract() call (see phase_times)."""
+        _check(load().symctr_profile_enable(self._h, int(enable)))
+
+    def phase_times(self):
+        """(prep_ms, gemm_ms, kernels launched) of the last contract() call."""
+        a, b, n = ctypes.c_float(), ctypes.c_float(), ctypes.c_int()
+        _check(load().symctr_profile_read(self._h, ctypes.byref(a), ctypes.byref(b),
+                                          ctypes.byref(n)))
+        return a.value, b.value, n.value
+
+    @property
+    def useful_flops(self) -> float:
+        return float(self.info.useful_flops)
+
+    def q_values(self):
+        i = self.info
+        if i.n_q == 0:
+            return []
+        if i.n_q == 1:
+            return [i.q_single]
+        return list(range(i.group_order))
+
+
+class SymContract(torch.autograd.Function):
+    """W = plan(U, V) with the hand-written adjoint: gU = gW.V and gV = U.gW
+    as irrep-aligned contractions (aligned operands recomputed, never saved)."""
+
+    @staticmethod
+    def forward(ctx, plan: Plan, u: torch.Tensor, v: torch.Tensor):
+        ctx.plan = plan
+        ctx.save_for_backward(u, v)
+        return plan.contract(u.contiguous(), v.contiguous())
+
+    @staticmethod
+    def backward(ctx, gw):
+        u, v = ctx.saved_tensors
+        plan = ctx.plan
+        gu, gv = plan.backward(gw.contiguous(), u.contiguous(), v.contiguous(),
+                               ctx.needs_input_grad[1], ctx.needs_input_grad[2])
+        return None, gu, gv
+
+
+def contract(plan: Plan, u: torch.Tensor, v: torch.Tensor) -> torch.Tensor:
+    """Differentiable contraction through the plan."""
+    return SymContract.apply(plan, u, v)
+
+
+def einsum(spec: str, u: torch.Tensor, v: torch.Tensor, moduli, sym_u, sym_v,
+           precision: str = "fp64") -> torch.Tensor:
+    """One-shot convenience: plan + differentiable contraction."""
+    return contract(Plan(spec, moduli, sym_u, sym_v, precision), u, v)
+
+
+__all__ = ["Plan", "PlanInfo", "SymSpec", "SymContract", "SymctrError", "contract", "einsum",
+           "load", "library_path", "PRECISIONS"]

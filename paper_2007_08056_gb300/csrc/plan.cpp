@@ -1,0 +1,646 @@
+// Planner and C ABI: einsum parsing, the charge algebra of Algorithm 2,
+// aligned-layout index maps, workspace layout and kernel dispatch.
+//
+// Charge algebra (Sec. 2.2, Alg. 2 coefficient vectors and deltas, with the
+// sign-flip allowance of the remark after Eq. ctr):
+//   sigma      : c^V_k = sigma * c^U_k on every contracted mode k (sigma = -1
+//                when nothing is contracted);
+//   Q          : sum_{k in C} c^U_k q_k                      (mod G)
+//   free U     : sum_{F_U} c^U q == Z_U - Q
+//   contracted : sum_C c^V q == sigma * Q
+//   free V     : sum_{F_V} c^V q == Z_V - sigma * Q
+//   output law : c^W = (c^U on F_U, -sigma c^V on F_V), Z_W = Z_U - sigma Z_V
+// (the last follows by eliminating Q, as in the proof of Sec. 2.3).
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "symctr_internal.h"
+
+using namespace symctr;
+
+thread_local long long symctr::g_kernel_launches = 0;
+
+namespace {
+
+thread_local std::string g_detail;
+
+symctr_status fail(symctr_status st, const std::string& msg) {
+  g_detail = msg;
+  return st;
+}
+
+constexpr int64_t kLimit = (int64_t)1 << 61;
+
+bool mul_ok(int64_t a, int64_t b, int64_t* out) {
+  if (a < 0 || b < 0) return false;
+  if (a != 0 && b > kLimit / a) return false;
+  *out = a * b;
+  return true;
+}
+
+int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+struct Tensor {
+  std::string labels;
+  int sign[SYMCTR_MAX_ORDER];
+  int z;  // flattened remainder
+  int64_t dim[SYMCTR_MAX_ORDER];
+  int order() const { return (int)labels.size(); }
+};
+
+// Reduced-form strides of one tensor: sector axes of modes 0..N-2, then blocks.
+void reduced_strides(const Tensor& t, int G, int64_t* sstride, int64_t* bstride) {
+  int n = t.order();
+  int64_t acc = 1;
+  for (int i = n - 1; i >= 0; --i) {
+    bstride[i] = acc;
+    acc *= t.dim[i];
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    if (i == n - 1) {
+      sstride[i] = 0;
+      continue;
+    }
+    sstride[i] = acc;
+    acc *= G;
+  }
+}
+
+int64_t reduced_numel(const Tensor& t, int G) {
+  int n = t.order();
+  int64_t acc = 1;
+  for (int i = 0; i < n; ++i) mul_ok(acc, t.dim[i], &acc);
+  for (int i = 0; i + 1 < n; ++i) mul_ok(acc, G, &acc);
+  return acc;
+}
+
+}  // namespace
+
+struct symctr_plan {
+  Tensor u, v, w;
+  GroupDesc g;
+  int s = 0, t = 0, vv = 0, sigma = -1;
+  std::vector<int> FU, C, FV;  // mode positions: FU, C in U; FV in V
+  Problem prob;
+  int64_t numel_u = 0, numel_v = 0, numel_w = 0;
+  symctr_precision prec = SYMCTR_FP64;
+  int n_slices = 0;
+  int64_t kpad = 0;
+  // workspace layout (byte offsets)
+  uint64_t ws_bytes = 256, off_a = 0, off_b = 0, off_ea = 0, off_eb = 0, off_acc = 0;
+  int ksplit = 1;
+  bool tensor_core = false;
+  symctr_plan* bwd_u = nullptr;
+  symctr_plan* bwd_v = nullptr;
+  bool prof = false;
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  mutable int last_launches = 0;
+};
+
+namespace {
+
+int g_label(const GroupDesc& g, const int32_t* comps) {
+  int q = 0;
+  for (int i = 0; i < g.n; ++i) {
+    int m = g.mod[i];
+    int c = ((comps[i] % m) + m) % m;
+    q = q * m + c;
+  }
+  return q;
+}
+
+void g_comps(const GroupDesc& g, int q, int32_t* comps) {
+  for (int i = g.n - 1; i >= 0; --i) {
+    comps[i] = q % g.mod[i];
+    q /= g.mod[i];
+  }
+}
+
+AxisMap make_axis(const Tensor& t, const std::vector<int>& modes, const int* law_sign, int G,
+                  int qa, int z) {
+  AxisMap a;
+  std::memset(&a, 0, sizeof(a));
+  int64_t ss[SYMCTR_MAX_ORDER], bs[SYMCTR_MAX_ORDER];
+  reduced_strides(t, G, ss, bs);
+  a.n = (int)modes.size();
+  int64_t size = 1;
+  for (int i = 0; i < a.n; ++i) {
+    int mu = modes[i];
+    a.D[i] = (int)t.dim[mu];
+    a.sign[i] = law_sign[i];
+    a.sstride[i] = ss[mu];
+    a.bstride[i] = bs[mu];
+    size *= t.dim[mu];
+    if (i + 1 < a.n) size *= G;
+  }
+  a.size = size;
+  a.qa = qa;
+  a.z = z;
+  return a;
+}
+
+symctr_status build(const char* einsum, int n_moduli, const int32_t* moduli, const int8_t* su,
+                    const int32_t* zu, const int8_t* sv, const int32_t* zv, const int64_t* du,
+                    const int64_t* dv, const int8_t* sw, const int32_t* zw, symctr_precision prec,
+                    int n_slices, bool with_backward, symctr_plan** out) {
+  if (!out) return fail(SYMCTR_ERR_NULLPTR, "out is NULL");
+  *out = nullptr;
+  if (!einsum || !moduli || !zu || !zv) return fail(SYMCTR_ERR_NULLPTR, "NULL argument");
+  if (n_moduli < 1 || n_moduli > SYMCTR_MAX_MODULI)
+    return fail(SYMCTR_ERR_UNSUPPORTED, "n_moduli must be in [1, 4]");
+  if (prec != SYMCTR_FP64 && prec != SYMCTR_SPLIT_BF16 && prec != SYMCTR_TF32)
+    return fail(SYMCTR_ERR_ARGUMENT, "unknown precision form");
+  if (n_slices < 0 || n_slices > kMaxSlices)
+    return fail(SYMCTR_ERR_ARGUMENT, "n_slices must be in [0, 6]");
+
+  // ---- einsum ----
+  std::string spec;
+  for (const char* c = einsum; *c; ++c)
+    if (*c != ' ') spec.push_back(*c);
+  size_t arrow = spec.find("->");
+  size_t comma = spec.find(',');
+  if (arrow == std::string::npos || comma == std::string::npos || comma > arrow ||
+      spec.find(',', comma + 1) != std::string::npos)
+    return fail(SYMCTR_ERR_EINSUM, "expected 'u,v->w'");
+  std::string lu = spec.substr(0, comma), lv = spec.substr(comma + 1, arrow - comma - 1),
+              lw = spec.substr(arrow + 2);
+  for (const std::string* lab : {&lu, &lv, &lw}) {
+    if ((int)lab->size() > SYMCTR_MAX_ORDER)
+      return fail(SYMCTR_ERR_UNSUPPORTED, "order > 8");
+    for (size_t i = 0; i < lab->size(); ++i) {
+      char c = (*lab)[i];
+      if (!((c >= 'a' && c <= 'z') || (c >= 'A' && c <= 'Z')))
+        return fail(SYMCTR_ERR_EINSUM, "labels must be letters");
+      if (lab->find(c, i + 1) != std::string::npos)
+        return fail(SYMCTR_ERR_EINSUM, "repeated label inside one operand (trace)");
+    }
+  }
+  for (char c : lw) {
+    bool inu = lu.find(c) != std::string::npos, inv = lv.find(c) != std::string::npos;
+    if (inu && inv) return fail(SYMCTR_ERR_EINSUM, "batch label (in U, V and W)");
+    if (!inu && !inv) return fail(SYMCTR_ERR_EINSUM, "output label absent from inputs");
+  }
+  for (char c : lu)
+    if (lv.find(c) == std::string::npos && lw.find(c) == std::string::npos)
+      return fail(SYMCTR_ERR_EINSUM, "free label of U missing from the output");
+  for (char c : lv)
+    if (lu.find(c) == std::string::npos && lw.find(c) == std::string::npos)
+      return fail(SYMCTR_ERR_EINSUM, "free label of V missing from the output");
+  if ((!su || !du) && !lu.empty()) return fail(SYMCTR_ERR_NULLPTR, "signs_u/dims_u NULL");
+  if ((!sv || !dv) && !lv.empty()) return fail(SYMCTR_ERR_NULLPTR, "signs_v/dims_v NULL");
+
+  symctr_plan* P = new (std::nothrow) symctr_plan();
+  if (!P) return fail(SYMCTR_ERR_ARGUMENT, "out of host memory");
+  auto bail = [&](symctr_status st, const std::string& m) {
+    delete P;
+    return fail(st, m);
+  };
+
+  // ---- group ----
+  P->g.n = n_moduli;
+  int64_t G = 1;
+  for (int i = 0; i < n_moduli; ++i) {
+    if (moduli[i] < 1) return bail(SYMCTR_ERR_SHAPE, "moduli must be >= 1");
+    P->g.mod[i] = moduli[i];
+    G *= moduli[i];
+    if (G > SYMCTR_MAX_GROUP) return bail(SYMCTR_ERR_UNSUPPORTED, "group order > 256");
+  }
+  P->g.order = (int)G;
+  const GroupDesc& g = P->g;
+
+  // ---- operands ----
+  P->u.labels = lu;
+  P->v.labels = lv;
+  P->w.labels = lw;
+  for (int i = 0; i < (int)lu.size(); ++i) {
+    if (su[i] != 1 && su[i] != -1) return bail(SYMCTR_ERR_SIGNS, "signs must be +1/-1");
+    if (du[i] < 1 || du[i] > (1 << 30)) return bail(SYMCTR_ERR_SHAPE, "sector dim out of range");
+    P->u.sign[i] = su[i];
+    P->u.dim[i] = du[i];
+  }
+  for (int i = 0; i < (int)lv.size(); ++i) {
+    if (sv[i] != 1 && sv[i] != -1) return bail(SYMCTR_ERR_SIGNS, "signs must be +1/-1");
+    if (dv[i] < 1 || dv[i] > (1 << 30)) return bail(SYMCTR_ERR_SHAPE, "sector dim out of range");
+    P->v.sign[i] = sv[i];
+    P->v.dim[i] = dv[i];
+  }
+  P->u.z = g_label(g, zu);
+  P->v.z = g_label(g, zv);
+
+  // ---- mode classes and sigma ----
+  int sigma = 0;
+  for (int i = 0; i < (int)lu.size(); ++i) {
+    size_t j = lv.find(lu[i]);
+    if (j == std::string::npos) {
+      P->FU.push_back(i);
+      continue;
+    }
+    P->C.push_back(i);
+    if (P->u.dim[i] != P->v.dim[j])
+      return bail(SYMCTR_ERR_SHAPE, std::string("sector dims differ on contracted mode ") + lu[i]);
+    int r = P->u.sign[i] * P->v.sign[j];
+    if (sigma == 0) sigma = r;
+    else if (sigma != r)
+      return bail(SYMCTR_ERR_SIGNS, "contracted coefficients must agree up to one global sign");
+  }
+  for (int j = 0; j < (int)lv.size(); ++j)
+    if (lu.find(lv[j]) == std::string::npos) P->FV.push_back(j);
+  if (sigma == 0) sigma = -1;
+  P->sigma = sigma;
+  P->s = (int)P->FU.size();
+  P->t = (int)P->FV.size();
+  P->vv = (int)P->C.size();
+
+  // ---- output law ----
+  // With nothing contracted (v = 0) both sigma = +1 and sigma = -1 give a valid
+  // law for the outer product, and both reduced forms hold the same numbers
+  // (the two laws agree wherever U's and V's laws both hold); a requested
+  // output law then selects sigma.
+  auto derive = [&](int sg) {
+    for (int i = 0; i < (int)lw.size(); ++i) {
+      size_t a = lu.find(lw[i]);
+      if (a != std::string::npos) {
+        P->w.sign[i] = P->u.sign[a];
+        P->w.dim[i] = P->u.dim[a];
+      } else {
+        size_t b = lv.find(lw[i]);
+        P->w.sign[i] = -sg * P->v.sign[b];
+        P->w.dim[i] = P->v.dim[b];
+      }
+    }
+    P->w.z = g_add(g, P->u.z, g_signed(g, -sg, P->v.z));
+  };
+  auto matches = [&](const int8_t* sw_, const int32_t* zw_) {
+    int zgiven = g_label(g, zw_);
+    bool same = zgiven == P->w.z, neg = zgiven == g_neg(g, P->w.z);
+    for (int i = 0; i < (int)lw.size(); ++i) {
+      same = same && sw_[i] == P->w.sign[i];
+      neg = neg && sw_[i] == -P->w.sign[i];
+    }
+    return same || neg;
+  };
+  derive(sigma);
+  if (sw || zw) {
+    if (!sw || !zw) return bail(SYMCTR_ERR_NULLPTR, "give both signs_w and charge_w, or neither");
+    if (!matches(sw, zw) && P->C.empty()) {
+      sigma = -sigma;
+      P->sigma = sigma;
+      derive(sigma);
+    }
+    if (!matches(sw, zw)) return bail(SYMCTR_ERR_CHARGE, "given output law contradicts the derived law");
+  }
+
+  // ---- sizes ----
+  P->numel_u = reduced_numel(P->u, (int)G);
+  P->numel_v = reduced_numel(P->v, (int)G);
+  P->numel_w = reduced_numel(P->w, (int)G);
+  if (P->numel_u >= kLimit || P->numel_v >= kLimit || P->numel_w >= kLimit)
+    return bail(SYMCTR_ERR_OVERFLOW, "tensor too large");
+
+  // ---- index maps ----
+  std::vector<int> FV_in_V = P->FV, C_in_V, FU_in_W, FV_in_W;
+  int sgn_fu[SYMCTR_MAX_ORDER], sgn_cu[SYMCTR_MAX_ORDER], sgn_cv[SYMCTR_MAX_ORDER],
+      sgn_fv[SYMCTR_MAX_ORDER];
+  for (size_t i = 0; i < P->FU.size(); ++i) {
+    sgn_fu[i] = P->u.sign[P->FU[i]];
+    FU_in_W.push_back((int)lw.find(lu[P->FU[i]]));
+  }
+  for (size_t i = 0; i < P->C.size(); ++i) {
+    sgn_cu[i] = P->u.sign[P->C[i]];
+    int j = (int)lv.find(lu[P->C[i]]);
+    C_in_V.push_back(j);
+    sgn_cv[i] = P->v.sign[j];
+  }
+  for (size_t i = 0; i < P->FV.size(); ++i) {
+    sgn_fv[i] = P->v.sign[P->FV[i]];
+    FV_in_W.push_back((int)lw.find(lv[P->FV[i]]));
+  }
+  Problem& pr = P->prob;
+  pr.g = g;
+  pr.u.rows = make_axis(P->u, P->FU, sgn_fu, (int)G, -1, P->u.z);
+  pr.u.cols = make_axis(P->u, P->C, sgn_cu, (int)G, +1, 0);
+  pr.v.rows = make_axis(P->v, FV_in_V, sgn_fv, (int)G, -sigma, P->v.z);
+  pr.v.cols = make_axis(P->v, C_in_V, sgn_cv, (int)G, sigma, 0);
+  pr.w.rows = make_axis(P->w, FU_in_W, sgn_fu, (int)G, -1, P->u.z);
+  pr.w.cols = make_axis(P->w, FV_in_W, sgn_fv, (int)G, -sigma, P->v.z);
+  pr.M = pr.u.rows.size;
+  pr.N = pr.v.rows.size;
+  pr.K = pr.u.cols.size;
+
+  // ---- irreps carrying work ----
+  int nq = 0, qs = -1;
+  for (int Q = 0; Q < (int)G; ++Q) {
+    bool ok = true;
+    if (P->s == 0) ok = ok && g_add(g, P->u.z, g_neg(g, Q)) == 0;
+    if (P->vv == 0) ok = ok && Q == 0;
+    if (P->t == 0) ok = ok && g_add(g, P->v.z, g_neg(g, g_signed(g, sigma, Q))) == 0;
+    if (ok) {
+      ++nq;
+      qs = Q;
+    }
+  }
+  pr.n_q = nq;
+  pr.q_single = nq == 1 ? qs : -1;
+  if (nq != 0 && nq != 1 && nq != (int)G) return bail(SYMCTR_ERR_ARGUMENT, "internal: Q set");
+
+  // ---- precision form and workspace ----
+  P->prec = prec;
+  P->tensor_core = prec != SYMCTR_FP64 && nq > 0 && tensor_core_shape(pr);
+  P->n_slices = prec == SYMCTR_SPLIT_BF16 ? (n_slices == 0 ? 5 : n_slices) : 0;
+  if (prec == SYMCTR_SPLIT_BF16 && P->n_slices < 2)
+    return bail(SYMCTR_ERR_ARGUMENT, "split form needs at least 2 slices");
+  P->kpad = round_up(pr.K, kKBlock);
+  uint64_t off = 256;
+  auto region = [&](int64_t bytes) {
+    uint64_t at = off;
+    off += (uint64_t)round_up(bytes, 256);
+    return at;
+  };
+  if (P->tensor_core) {
+    int64_t ra = 0, rb = 0;
+    if (!mul_ok((int64_t)nq * pr.M, P->kpad, &ra) || !mul_ok((int64_t)nq * pr.N, P->kpad, &rb))
+      return bail(SYMCTR_ERR_OVERFLOW, "aligned operand too large");
+    if (prec == SYMCTR_SPLIT_BF16) {
+      P->off_a = region(ra * 2 * P->n_slices);
+      P->off_b = region(rb * 2 * P->n_slices);
+      P->off_ea = region((int64_t)nq * pr.M * 4);
+      P->off_eb = region((int64_t)nq * pr.N * 4);
+      P->ksplit = split_k_ranges(pr, P->kpad);
+      if (P->ksplit > 1) P->off_acc = region((int64_t)nq * pr.M * pr.N * 8);
+    } else {
+      P->off_a = region(ra * 4);
+      P->off_b = region(rb * 4);
+    }
+  }
+  P->ws_bytes = off;
+
+  if (with_backward) {
+    // gU = einsum(lw,lv->lu)(gW, V): result carries U's law.
+    int8_t s_w[SYMCTR_MAX_ORDER], s_u[SYMCTR_MAX_ORDER], s_v[SYMCTR_MAX_ORDER];
+    int32_t z_w[SYMCTR_MAX_MODULI], z_u[SYMCTR_MAX_MODULI], z_v[SYMCTR_MAX_MODULI];
+    for (int i = 0; i < (int)lw.size(); ++i) s_w[i] = (int8_t)P->w.sign[i];
+    for (int i = 0; i < (int)lu.size(); ++i) s_u[i] = (int8_t)P->u.sign[i];
+    for (int i = 0; i < (int)lv.size(); ++i) s_v[i] = (int8_t)P->v.sign[i];
+    g_comps(g, P->w.z, z_w);
+    g_comps(g, P->u.z, z_u);
+    g_comps(g, P->v.z, z_v);
+    std::string su_spec = lw + "," + lv + "->" + lu;
+    std::string sv_spec = lu + "," + lw + "->" + lv;
+    symctr_status st = build(su_spec.c_str(), n_moduli, moduli, s_w, z_w, s_v, z_v, P->w.dim,
+                             P->v.dim, s_u, z_u, prec, P->n_slices, false, &P->bwd_u);
+    if (st != SYMCTR_OK) return bail(st, "backward plan (dU): " + g_detail);
+    st = build(sv_spec.c_str(), n_moduli, moduli, s_u, z_u, s_w, z_w, P->u.dim, P->w.dim, s_v,
+               z_v, prec, P->n_slices, false, &P->bwd_v);
+    if (st != SYMCTR_OK) {
+      symctr_plan_destroy(P->bwd_u);
+      P->bwd_u = nullptr;
+      return bail(st, "backward plan (dV): " + g_detail);
+    }
+  }
+  *out = P;
+  g_detail.clear();
+  return SYMCTR_OK;
+}
+
+symctr_status cuda_status(cudaError_t e, const char* where) {
+  if (e == cudaSuccess) return SYMCTR_OK;
+  return fail(SYMCTR_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+symctr_status run_contract_body(const symctr_plan* P, const double* u, const double* v,
+                                double* w, void* ws, size_t ws_bytes, cudaStream_t st);
+
+symctr_status run_contract(const symctr_plan* P, const double* u, const double* v, double* w,
+                           void* ws, size_t ws_bytes, cudaStream_t st) {
+  long long before = g_kernel_launches;
+  symctr_status s = run_contract_body(P, u, v, w, ws, ws_bytes, st);
+  P->last_launches = (int)(g_kernel_launches - before);
+  return s;
+}
+
+symctr_status run_contract_body(const symctr_plan* P, const double* u, const double* v,
+                                double* w, void* ws, size_t ws_bytes, cudaStream_t st) {
+  const Problem& pr = P->prob;
+  if (!w || (!u && P->numel_u) || (!v && P->numel_v))
+    return fail(SYMCTR_ERR_NULLPTR, "NULL tensor pointer");
+  if (!ws || ws_bytes < P->ws_bytes)
+    return fail(SYMCTR_ERR_WORKSPACE, "workspace smaller than workspace_bytes");
+  char* base = (char*)ws;
+  unsigned* err = (unsigned*)base;
+  cudaError_t e = cudaMemsetAsync(err, 0, sizeof(unsigned), st);
+  if (e != cudaSuccess) return cuda_status(e, "clear error word");
+  // Entries of W whose irrep Q carries no work are zero.
+  if ((int64_t)pr.n_q * pr.M * pr.N < P->numel_w) {
+    e = launch_fill_zero(w, P->numel_w, st);
+    if (e != cudaSuccess) return cuda_status(e, "zero fill");
+  }
+  if (pr.n_q == 0) return SYMCTR_OK;
+  if (P->prof) cudaEventRecord(P->ev[0], st);
+  if (!P->tensor_core) {
+    if (P->prof) cudaEventRecord(P->ev[1], st);
+    e = launch_gemm_f64(pr, u, v, w, st);
+    if (P->prof) cudaEventRecord(P->ev[2], st);
+    return cuda_status(e, "gemm_f64");
+  }
+  if (P->prec == SYMCTR_SPLIT_BF16) {
+    uint16_t* as = (uint16_t*)(base + P->off_a);
+    uint16_t* bs = (uint16_t*)(base + P->off_b);
+    int32_t* ea = (int32_t*)(base + P->off_ea);
+    int32_t* eb = (int32_t*)(base + P->off_eb);
+    e = launch_split_operand(pr, 0, P->n_slices, u, as, P->kpad, ea, err, st);
+    if (e != cudaSuccess) return cuda_status(e, "split U");
+    e = launch_split_operand(pr, 1, P->n_slices, v, bs, P->kpad, eb, err, st);
+    if (e != cudaSuccess) return cuda_status(e, "split V");
+    if (P->prof) cudaEventRecord(P->ev[1], st);
+    e = launch_gemm_split(pr, P->n_slices, as, bs, ea, eb, P->kpad, w, err, P->ksplit,
+                          (unsigned long long*)(base + P->off_acc), st);
+    if (P->prof) cudaEventRecord(P->ev[2], st);
+    return cuda_status(e, "gemm_split");
+  }
+  float* a32 = (float*)(base + P->off_a);
+  float* b32 = (float*)(base + P->off_b);
+  e = launch_tf32_operand(pr, 0, u, a32, P->kpad, st);
+  if (e != cudaSuccess) return cuda_status(e, "tf32 U");
+  e = launch_tf32_operand(pr, 1, v, b32, P->kpad, st);
+  if (e != cudaSuccess) return cuda_status(e, "tf32 V");
+  if (P->prof) cudaEventRecord(P->ev[1], st);
+  e = launch_gemm_tf32(pr, a32, b32, P->kpad, w, err, st);
+  if (P->prof) cudaEventRecord(P->ev[2], st);
+  return cuda_status(e, "gemm_tf32");
+}
+
+}  // namespace
+
+extern "C" {
+
+symctr_status symctr_plan_create(const char* einsum, int n_moduli, const int32_t* moduli,
+                                 const int8_t* signs_u, const int32_t* charge_u,
+                                 const int8_t* signs_v, const int32_t* charge_v,
+                                 const int64_t* dims_u, const int64_t* dims_v,
+                                 const int8_t* signs_w_or_null, const int32_t* charge_w_or_null,
+                                 symctr_precision prec, int n_slices, symctr_plan** out) {
+  return build(einsum, n_moduli, moduli, signs_u, charge_u, signs_v, charge_v, dims_u, dims_v,
+               signs_w_or_null, charge_w_or_null, prec, n_slices, true, out);
+}
+
+symctr_status symctr_plan_query(const symctr_plan* P, symctr_plan_info* o) {
+  if (!P || !o) return fail(SYMCTR_ERR_NULLPTR, "NULL argument");
+  std::memset(o, 0, sizeof(*o));
+  const Problem& pr = P->prob;
+  o->order_u = P->u.order();
+  o->order_v = P->v.order();
+  o->order_w = P->w.order();
+  o->s = P->s;
+  o->t = P->t;
+  o->v = P->vv;
+  o->sigma = P->sigma;
+  o->n_moduli = P->g.n;
+  for (int i = 0; i < P->g.n; ++i) o->moduli[i] = P->g.mod[i];
+  o->group_order = P->g.order;
+  o->precision = (int32_t)P->prec;
+  o->n_slices = P->n_slices;
+  for (int i = 0; i < P->w.order(); ++i) {
+    o->signs_w[i] = (int8_t)P->w.sign[i];
+    o->dims_w[i] = P->w.dim[i];
+  }
+  g_comps(P->g, P->w.z, o->charge_w);
+  o->numel_u = P->numel_u;
+  o->numel_v = P->numel_v;
+  o->numel_w = P->numel_w;
+  o->M = pr.M;
+  o->N = pr.N;
+  o->K = pr.K;
+  o->n_q = pr.n_q;
+  o->q_single = pr.q_single;
+  o->aligned_numel_u = (int64_t)pr.n_q * pr.M * pr.K;
+  o->aligned_numel_v = (int64_t)pr.n_q * pr.N * pr.K;
+  o->aligned_numel_w = (int64_t)pr.n_q * pr.M * pr.N;
+  o->useful_flops = 2.0 * (double)pr.n_q * (double)pr.M * (double)pr.N * (double)pr.K;
+  // transforms move each operand element once in and once out (8 B each way)
+  o->transform_bytes = 16.0 * (double)(o->aligned_numel_u + o->aligned_numel_v + o->aligned_numel_w);
+  o->workspace_bytes = P->ws_bytes;
+  uint64_t wb = 256;
+  if (P->bwd_u && P->bwd_u->ws_bytes > wb) wb = P->bwd_u->ws_bytes;
+  if (P->bwd_v && P->bwd_v->ws_bytes > wb) wb = P->bwd_v->ws_bytes;
+  o->workspace_bytes_backward = wb;
+  return SYMCTR_OK;
+}
+
+symctr_status symctr_align(const symctr_plan* P, int operand, int direction, const double* src,
+                           double* dst, void* stream) {
+  if (!P || !src || !dst) return fail(SYMCTR_ERR_NULLPTR, "NULL argument");
+  if (operand < 0 || operand > 2 || (direction != 1 && direction != -1))
+    return fail(SYMCTR_ERR_ARGUMENT, "operand in {0,1,2}, direction in {+1,-1}");
+  const Problem& pr = P->prob;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (direction == -1) {
+    int64_t covered = operand == 0 ? (int64_t)pr.n_q * pr.M * pr.K
+                    : operand == 1 ? (int64_t)pr.n_q * pr.N * pr.K
+                                   : (int64_t)pr.n_q * pr.M * pr.N;
+    int64_t total = operand == 0 ? P->numel_u : operand == 1 ? P->numel_v : P->numel_w;
+    if (covered < total) {
+      cudaError_t e = launch_fill_zero(dst, total, st);
+      if (e != cudaSuccess) return cuda_status(e, "zero fill");
+    }
+  }
+  if (pr.n_q == 0) return SYMCTR_OK;
+  return cuda_status(launch_align_f64(pr, operand, direction, src, dst, st), "align");
+}
+
+symctr_status symctr_contract(const symctr_plan* P, const double* u, const double* v, double* w,
+                              void* ws, size_t ws_bytes, void* stream) {
+  if (!P) return fail(SYMCTR_ERR_NULLPTR, "NULL plan");
+  return run_contract(P, u, v, w, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+symctr_status symctr_contract_backward(const symctr_plan* P, const double* gw, const double* u,
+                                       const double* v, double* gu, double* gv, void* ws,
+                                       size_t ws_bytes, void* stream) {
+  if (!P || !gw) return fail(SYMCTR_ERR_NULLPTR, "NULL argument");
+  if (!P->bwd_u || !P->bwd_v) return fail(SYMCTR_ERR_ARGUMENT, "plan has no backward");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (gu) {
+    symctr_status s = run_contract(P->bwd_u, gw, v, gu, ws, ws_bytes, st);
+    if (s != SYMCTR_OK) return s;
+  }
+  if (gv) {
+    symctr_status s = run_contract(P->bwd_v, u, gw, gv, ws, ws_bytes, st);
+    if (s != SYMCTR_OK) return s;
+  }
+  return SYMCTR_OK;
+}
+
+symctr_status symctr_check_device_error(const symctr_plan* P, void* ws, void* stream) {
+  (void)P;
+  if (!ws) return fail(SYMCTR_ERR_NULLPTR, "NULL workspace");
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, ws, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_status(e, "read device error word");
+  e = cudaMemsetAsync(ws, 0, sizeof(unsigned), st);
+  if (e != cudaSuccess) return cuda_status(e, "clear device error word");
+  if (h & DEVERR_TIMEOUT) return fail(SYMCTR_ERR_DEVICE_TIMEOUT, "a kernel's bounded wait expired");
+  if (h & DEVERR_NONFINITE) return fail(SYMCTR_ERR_NONFINITE, "non-finite input");
+  return SYMCTR_OK;
+}
+
+const char* symctr_status_string(symctr_status s) {
+  switch (s) {
+    case SYMCTR_OK: return "SYMCTR_OK";
+    case SYMCTR_ERR_EINSUM: return "SYMCTR_ERR_EINSUM";
+    case SYMCTR_ERR_SIGNS: return "SYMCTR_ERR_SIGNS";
+    case SYMCTR_ERR_SHAPE: return "SYMCTR_ERR_SHAPE";
+    case SYMCTR_ERR_CHARGE: return "SYMCTR_ERR_CHARGE";
+    case SYMCTR_ERR_UNSUPPORTED: return "SYMCTR_ERR_UNSUPPORTED";
+    case SYMCTR_ERR_NULLPTR: return "SYMCTR_ERR_NULLPTR";
+    case SYMCTR_ERR_WORKSPACE: return "SYMCTR_ERR_WORKSPACE";
+    case SYMCTR_ERR_CUDA: return "SYMCTR_ERR_CUDA";
+    case SYMCTR_ERR_DEVICE_TIMEOUT: return "SYMCTR_ERR_DEVICE_TIMEOUT";
+    case SYMCTR_ERR_OVERFLOW: return "SYMCTR_ERR_OVERFLOW";
+    case SYMCTR_ERR_NONFINITE: return "SYMCTR_ERR_NONFINITE";
+    case SYMCTR_ERR_ARGUMENT: return "SYMCTR_ERR_ARGUMENT";
+  }
+  return "SYMCTR_UNKNOWN";
+}
+
+const char* symctr_last_error_detail(void) { return g_detail.c_str(); }
+
+symctr_status symctr_profile_enable(symctr_plan* P, int enable) {
+  if (!P) return fail(SYMCTR_ERR_NULLPTR, "NULL plan");
+  if (enable && !P->prof) {
+    for (int i = 0; i < 3; ++i) {
+      cudaError_t e = cudaEventCreate(&P->ev[i]);
+      if (e != cudaSuccess) return cuda_status(e, "cudaEventCreate");
+    }
+    P->prof = true;
+  } else if (!enable && P->prof) {
+    for (int i = 0; i < 3; ++i) cudaEventDestroy(P->ev[i]);
+    P->prof = false;
+  }
+  return SYMCTR_OK;
+}
+
+symctr_status symctr_profile_read(const symctr_plan* P, float* prep_ms, float* gemm_ms,
+                                  int* launches) {
+  if (!P || !prep_ms || !gemm_ms) return fail(SYMCTR_ERR_NULLPTR, "NULL argument");
+  if (launches) *launches = P->last_launches;
+  if (!P->prof) return fail(SYMCTR_ERR_ARGUMENT, "profiling not enabled");
+  cudaError_t e = cudaEventSynchronize(P->ev[2]);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(prep_ms, P->ev[0], P->ev[1]);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(gemm_ms, P->ev[1], P->ev[2]);
+  return cuda_status(e, "profile read");
+}
+
+void symctr_plan_destroy(symctr_plan* P) {
+  if (!P) return;
+  symctr_profile_enable(P, 0);
+  symctr_plan_destroy(P->bwd_u);
+  symctr_plan_destroy(P->bwd_v);
+  delete P;
+}
+
+}  // extern "C"

@@ -1,0 +1,156 @@
+// Internal declarations shared by the planner (plan.cpp) and the CUDA kernels.
+//
+// Index maps.  Every transformation of Algorithm 2 (std reduced form <->
+// aligned form, for U, V and W) is a *separable* gather: an aligned element
+// (Q, r, c) lives at reduced-form offset row_off(Q, r) + col_off(Q, c).  This
+// holds because the implicit sector of the row modes depends only on Q and the
+// explicit row sectors, and likewise for the column modes (uniqueness of Q in
+// the proof of Sec. 2.3).  An AxisMap describes one side.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "symctr.h"
+
+#if defined(__CUDACC__)
+#define SC_HD __host__ __device__ __forceinline__
+#else
+#define SC_HD inline
+#endif
+
+namespace symctr {
+
+// Z_m1 x ... x Z_mr, labels flattened mixed-radix, first modulus most significant.
+struct GroupDesc {
+  int n;
+  int mod[SYMCTR_MAX_MODULI];
+  int order;
+};
+
+SC_HD int g_add(const GroupDesc& g, int a, int b) {
+  if (g.n == 1) { int r = a + b; return r >= g.order ? r - g.order : r; }
+  int out = 0, scale = 1;
+  for (int i = g.n - 1; i >= 0; --i) {
+    int m = g.mod[i];
+    int x = (a % m + b % m) % m;
+    out += x * scale;
+    scale *= m;
+    a /= m;
+    b /= m;
+  }
+  return out;
+}
+
+SC_HD int g_neg(const GroupDesc& g, int a) {
+  if (g.n == 1) return a == 0 ? 0 : g.order - a;
+  int out = 0, scale = 1;
+  for (int i = g.n - 1; i >= 0; --i) {
+    int m = g.mod[i];
+    int x = a % m;
+    out += (x == 0 ? 0 : m - x) * scale;
+    scale *= m;
+    a /= m;
+  }
+  return out;
+}
+
+SC_HD int g_signed(const GroupDesc& g, int sign, int a) { return sign > 0 ? a : g_neg(g, a); }
+
+// One side (rows or columns) of an aligned operand.
+struct AxisMap {
+  int n;                                // modes in this group
+  int64_t size;                         // G^(n-1) * prod D  (1 if n == 0)
+  int D[SYMCTR_MAX_ORDER];
+  int sign[SYMCTR_MAX_ORDER];           // law coefficients used to solve the implicit sector
+  int64_t sstride[SYMCTR_MAX_ORDER];    // reduced-form stride of the sector axis (0: not stored)
+  int64_t bstride[SYMCTR_MAX_ORDER];    // reduced-form stride of the block axis
+  int qa;                               // sum_i sign_i q_i == qa*Q + z  (qa = +-1)
+  int z;
+};
+
+// Offset contribution of aligned index r at irrep Q.
+SC_HD int64_t axis_offset(const AxisMap& a, const GroupDesc& g, int Q, int64_t r) {
+  if (a.n == 0) return 0;
+  int64_t off = 0;
+  for (int i = a.n - 1; i >= 0; --i) {
+    int64_t d = a.D[i];
+    int64_t b = r % d;
+    r /= d;
+    off += b * a.bstride[i];
+  }
+  int partial = 0;
+  for (int i = a.n - 2; i >= 0; --i) {
+    int q = (int)(r % g.order);
+    r /= g.order;
+    off += (int64_t)q * a.sstride[i];
+    partial = g_add(g, partial, g_signed(g, a.sign[i], q));
+  }
+  int target = g_add(g, g_signed(g, a.qa, Q), a.z);
+  int last = g_signed(g, a.sign[a.n - 1], g_add(g, target, g_neg(g, partial)));
+  off += (int64_t)last * a.sstride[a.n - 1];
+  return off;
+}
+
+struct OperandMap {
+  AxisMap rows, cols;
+};
+
+// Everything a kernel needs to locate the aligned GEMM problem.
+struct Problem {
+  GroupDesc g;
+  int n_q;            // batches (irreps carrying work)
+  int q_single;       // irrep when n_q == 1
+  int64_t M, N, K;
+  OperandMap u, v, w; // U: rows = free-U, cols = contracted; V: rows = free-V, cols = contracted;
+                      // W: rows = free-U, cols = free-V
+};
+
+SC_HD int batch_irrep(const Problem& p, int b) { return p.n_q == 1 ? p.q_single : b; }
+
+// Device error word codes (first uint32 of the workspace).
+enum : unsigned { DEVERR_NONE = 0, DEVERR_TIMEOUT = 1, DEVERR_NONFINITE = 2 };
+
+// Split-precision constants.
+constexpr int kSliceBits = 8;       // bits per balanced BF16 digit
+constexpr int kMaxSlices = 6;
+constexpr int kKBlock = 32;         // K per pipeline stage (64-byte rows of BF16)
+constexpr int kKChunk = 64;         // K between exact flushes of the top accumulators
+
+// Kernels launched on this host thread (every launcher adds its launches).
+extern thread_local long long g_kernel_launches;
+
+// ---- kernel launchers (return cudaError_t of the launch) ----
+cudaError_t launch_align_f64(const Problem& p, int operand, int direction, const double* src,
+                             double* dst, cudaStream_t st);
+cudaError_t launch_gemm_f64(const Problem& p, const double* u, const double* v, double* w,
+                            cudaStream_t st);
+cudaError_t launch_fill_zero(double* w, int64_t n, cudaStream_t st);
+cudaError_t launch_split_operand(const Problem& p, int operand, int n_slices, const double* src,
+                                 uint16_t* slices, int64_t kpad, int32_t* exps, unsigned* err,
+                                 cudaStream_t st);
+cudaError_t launch_gemm_split(const Problem& p, int n_slices, const uint16_t* us,
+                              const uint16_t* vs, const int32_t* eu, const int32_t* ev,
+                              int64_t kpad, double* w, unsigned* err, int ksplit,
+                              unsigned long long* wacc, cudaStream_t st);
+cudaError_t launch_tf32_operand(const Problem& p, int operand, const double* src, float* dst,
+                                int64_t kpad, cudaStream_t st);
+cudaError_t launch_gemm_tf32(const Problem& p, const float* u, const float* v, int64_t kpad,
+                             double* w, unsigned* err, cudaStream_t st);
+
+// K ranges of the split-BF16 GEMM: enough CTAs to fill the GPU when the
+// problem has few 128x128 tiles (deterministic: independent of the device).
+inline int split_k_ranges(const Problem& p, int64_t kpad) {
+  int64_t tiles = ((p.M + 127) / 128) * ((p.N + 127) / 128) * (int64_t)p.n_q;
+  int64_t chunks = kpad / kKChunk;
+  if (tiles >= 80 || chunks < 4) return 1;
+  int64_t want = (160 + tiles - 1) / tiles;
+  int64_t per = (chunks + want - 1) / want;     // chunks per range
+  if (per < 2) per = 2;
+  return (int)((chunks + per - 1) / per);
+}
+
+// Shape test: the tensor-core forms need a GEMM-shaped problem.
+inline bool tensor_core_shape(const Problem& p) { return p.M >= 32 && p.N >= 32 && p.K >= 16; }
+
+}  // namespace symctr

@@ -1,0 +1,130 @@
+"""C ABI checks that need no GPU: the library loads, exports every entry point
+that include/symctr.h declares, and its host-side planner agrees with the
+oracle's charge algebra (derived output law, aligned GEMM extents, irrep
+set) and reports the documented error statuses."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2007_08056_gb300 as sc
+import workloads as WL
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    with open(os.path.join(ROOT, "include", "symctr.h")) as f:
+        text = f.read()
+    return sorted(set(re.findall(r"SYMCTR_API\s+[\w\s\*]+?\b(symctr_\w+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = sc.load()
+    names = declared_symbols()
+    assert "symctr_contract" in names and "symctr_plan_create" in names
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_status_strings():
+    lib = sc.load()
+    for code, name in sc.STATUS.items():
+        assert lib.symctr_status_string(code).decode() == name
+
+
+def oracle_plan(c):
+    g = O.Group(c.moduli)
+    return O.plan(c.einsum, g, O.Sym(c.u.signs, c.u.charge, c.u.dims),
+                  O.Sym(c.v.signs, c.v.charge, c.v.dims))
+
+
+CASES = WL.small_cases() + [WL.CC_LADDER, WL.cc_ladder(16, 512, 128)]
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: c.name)
+@pytest.mark.parametrize("precision", ["fp64", "split_bf16", "tf32"])
+def test_planner_matches_oracle(case, precision):
+    p = sc.Plan(case.einsum, case.moduli, (case.u.signs, case.u.charge, case.u.dims),
+                (case.v.signs, case.v.charge, case.v.dims), precision)
+    o = oracle_plan(case)
+    G, M, N, K = O.aligned_dims(o)
+    i = p.info
+    assert (i.group_order, i.M, i.N, i.K) == (G, M, N, K)
+    assert (i.s, i.t, i.v, i.sigma) == (o.s, o.t, o.v, o.sigma)
+    assert p.sym_w.signs == o.sym_w.signs
+    assert p.sym_w.charge == o.sym_w.charge
+    assert p.sym_w.dims == o.sym_w.dims
+    qs = O.q_set(o)
+    assert p.q_values() == qs
+    assert i.useful_flops == 2.0 * len(qs) * M * N * K
+    assert p.shape_u == O.reduced_shape(o.group, o.sym_u)
+    assert p.shape_w == O.reduced_shape(o.group, o.sym_w)
+    assert i.workspace_bytes >= 256
+    if precision == "split_bf16":
+        assert i.n_slices == 5
+
+
+def test_config_extents():
+    """Aligned GEMM extents of the paper-shaped workloads."""
+    p = sc.Plan(WL.CC_LADDER.einsum, (8,), (WL.PP, (0,), (32,) * 4), (WL.PP, (0,), (32, 32, 8, 8)))
+    assert (p.info.M, p.info.K, p.info.N, p.info.n_q) == (8192, 8192, 512, 8)
+    assert p.useful_flops == 549_755_813_888
+    s1 = sc.Plan(WL.MPS_STEP1, (8,), (WL.MPS_E.signs, (0,), WL.MPS_E.dims),
+                 (WL.MPS_A.signs, (0,), WL.MPS_A.dims))
+    assert (s1.info.M, s1.info.K, s1.info.N) == (128, 128, 2048)
+    s2 = sc.Plan(WL.MPS_STEP2, (8,), s1.sym_w, (WL.MPS_A.signs, (0,), WL.MPS_A.dims))
+    assert (s2.info.M, s2.info.K, s2.info.N) == (128, 2048, 128)
+    assert s2.sym_w.signs == WL.MPS_E.signs
+    y = sc.Plan(WL.PEPS_Y, WL.PEPS_MODULI, (WL.PEPS_T.signs, (0, 0), WL.PEPS_T.dims),
+                (WL.PEPS_ENV.signs, (0, 0), WL.PEPS_ENV.dims))
+    assert (y.info.M, y.info.N, y.info.K, y.info.n_q) == (2, 1, 6 ** 3 * 16 ** 4, 1)
+
+
+def plan_status(einsum, moduli, su, sv, sw=None):
+    try:
+        sc.Plan(einsum, moduli, su, sv, sym_w=sw)
+        return 0
+    except sc.SymctrError as e:
+        return e.status
+
+
+def test_error_statuses():
+    pp = ((1, 1, -1, -1), (0,), (2, 2, 2, 2))
+    assert plan_status("abkl,klij->abij", (3,), pp, pp) == 0
+    assert plan_status("abkl,klij", (3,), pp, pp) == 1                     # no arrow
+    assert plan_status("aakl,klij->ij", (3,), pp, pp) == 1                  # trace label
+    assert plan_status("abkl,klij->abijk", (3,), pp, pp) == 1               # batch label
+    assert plan_status("abkl,klij->abi", (3,), pp, pp) == 1                 # free label dropped
+    mixed = ((1, -1, 1, -1), (0,), (2, 2, 2, 2))                             # k: sigma=-1, l: +1
+    assert plan_status("abkl,klij->abij", (3,), pp, mixed) == 2
+    assert plan_status("abkl,klij->abij", (3,), pp, ((1, 1, -1, -1), (0,), (3, 2, 2, 2))) == 3
+    assert plan_status("abkl,klij->abij", (300,), pp, pp) == 5               # group too large
+    # an output law that contradicts the derived one; its global negation is accepted
+    assert plan_status("abkl,klij->abij", (3,), pp, pp, ((1, 1, -1, -1), (1,), (2,) * 4)) == 4
+    assert plan_status("abkl,klij->abij", (3,), pp, pp, ((-1, -1, 1, 1), (0,), (2,) * 4)) == 0
+    big = ((1,) * 9, (0,), (1,) * 9)
+    assert plan_status("abcdefghi,a->bcdefghi", (2,), big, ((-1,), (0,), (1,))) == 5
+
+
+def test_null_arguments():
+    lib = sc.load()
+    out = ctypes.c_void_p()
+    st = lib.symctr_plan_create(None, 1, None, None, None, None, None, None, None, None, None, 0,
+                                0, ctypes.byref(out))
+    assert st == 6
+    assert lib.symctr_plan_query(None, None) == 6
+    assert lib.symctr_contract(None, None, None, None, None, 0, None) == 6
+
+
+def test_workspace_too_small_is_rejected_before_any_launch():
+    """The size check happens on the host, so it needs no GPU."""
+    p = sc.Plan(WL.Z3_ORDER4.einsum, (3,), (WL.PP, (0,), (4,) * 4), (WL.PP, (0,), (4,) * 4),
+                "split_bf16")
+    lib = sc.load()
+    fake = ctypes.c_void_p(4096)
+    st = lib.symctr_contract(p._h, fake, fake, fake, fake, 16, None)
+    assert st == 7

@@ -1,0 +1,255 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU float64 oracle.
+
+Tolerances (relative Frobenius error against the oracle's block loop):
+  fp64        <= 1e-12   (float64 FMA; summation order differs)
+  split_bf16  <= 1e-10   (5 BF16 slices of 8 bits: truncation ~2^-39 per
+                          operand entry relative to its row maximum)
+  tf32        <= 1e-2    (operands rounded to 11 significant bits)
+Alignment transforms are compared bit for bit.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import workloads as WL
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "split_bf16": 1e-10, "tf32": 1e-2}
+
+
+@pytest.fixture(scope="module")
+def sc():
+    if not torch.cuda.is_available():
+        pytest.fail("a GPU test ran without a visible GPU")
+    import paper_2007_08056_gb300 as mod
+    mod.load()
+    return mod
+
+
+def dev(a):
+    return torch.from_numpy(np.array(a, dtype=np.float64, order="C", copy=True)).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def rel(a, b):
+    n = np.linalg.norm(b)
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / (n if n > 0 else 1.0))
+
+
+def oplan(einsum, moduli, su, sv):
+    return O.plan(einsum, O.Group(moduli), O.Sym(*su), O.Sym(*sv))
+
+
+def spec(t):
+    return (t.signs, t.charge, t.dims)
+
+
+def run_case(sc, einsum, moduli, su, sv, u, v, precision, check_err=True):
+    p = sc.Plan(einsum, moduli, su, sv, precision)
+    w = p.contract(dev(u), dev(v))
+    torch.cuda.synchronize()
+    if check_err:
+        p.check_device_error()
+    o = oplan(einsum, moduli, su, sv)
+    want = O.contract_blockloop(o, u, v)
+    return rel(host(w), want), p, w, want
+
+
+# ---------------------------------------------------------------------------
+# small contractions spanning (s, t, v), sigma, charges, product groups
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("precision", ["fp64", "split_bf16", "tf32"])
+@pytest.mark.parametrize("case", WL.small_cases(), ids=lambda c: c.name)
+def test_small_cases(sc, case, precision):
+    u, v = WL.draw_pair(case)
+    e, p, _, _ = run_case(sc, case.einsum, case.moduli, spec(case.u), spec(case.v), u, v, precision)
+    assert e <= TOL[precision], (case.name, precision, e)
+
+
+@pytest.mark.parametrize("case", WL.small_cases(), ids=lambda c: c.name)
+def test_alignment_bit_exact(sc, case):
+    """symctr_align against the oracle's delta-tensor transforms, both directions."""
+    u, v = WL.draw_pair(case)
+    p = sc.Plan(case.einsum, case.moduli, spec(case.u), spec(case.v))
+    o = oplan(case.einsum, case.moduli, spec(case.u), spec(case.v))
+    qs = O.q_set(o)
+    w = O.contract_blockloop(o, u, v)
+    for operand, red, al in ((0, u, O.align_u(o, u)), (1, v, O.align_v(o, v)),
+                             (2, w, O.align_w(o, w))):
+        got = host(p.align(operand, +1, dev(red)))
+        assert np.array_equal(got, al[qs]), (case.name, operand)
+        back = host(p.align(operand, -1, dev(al[qs])))
+        # entries whose irrep carries no work come back as zero
+        full = O.mapback_w(o, al) if operand == 2 else None
+        if operand == 2:
+            assert np.array_equal(back, full)
+        elif len(qs) == p.info.group_order or al[[q for q in range(p.info.group_order)
+                                                  if q not in qs]].size == 0:
+            assert np.array_equal(back, red)
+        else:
+            kept = np.isin(red, al[qs])
+            assert np.array_equal(back[kept], red[kept]) and not back[~kept].any()
+
+
+def test_mapback_zero_fill_outer_product(sc):
+    """v = 0: W entries whose irrep carries no work must be written as zeros."""
+    case = [c for c in WL.small_cases() if c.name == "outer_v0_G3"][0]
+    u, v = WL.draw_pair(case)
+    for prec in ("fp64", "split_bf16"):
+        p = sc.Plan(case.einsum, case.moduli, spec(case.u), spec(case.v), prec)
+        w = torch.full(p.shape_w, 7.0, dtype=torch.float64, device="cuda")
+        p.contract(dev(u), dev(v), out=w)
+        want = O.contract_blockloop(oplan(case.einsum, case.moduli, spec(case.u), spec(case.v)), u, v)
+        assert rel(host(w), want) <= 1e-12
+
+
+# ---------------------------------------------------------------------------
+# the paper-shaped workloads
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("precision", ["fp64", "split_bf16", "tf32"])
+def test_config1_order4_z3(sc, precision):
+    c = WL.Z3_ORDER4
+    u, v = WL.draw_pair(c)
+    e, p, _, _ = run_case(sc, c.einsum, c.moduli, spec(c.u), spec(c.v), u, v, precision)
+    assert (p.info.M, p.info.N, p.info.K) == (48, 48, 48)
+    assert e <= TOL[precision], e
+
+
+@pytest.mark.parametrize("precision", ["fp64", "split_bf16"])
+def test_config2_mps_transfer(sc, precision):
+    E = WL.draw(WL.MPS_E, (8,))
+    A = WL.draw(WL.MPS_A, (8,))
+    e1, p1, X, want_x = run_case(sc, WL.MPS_STEP1, (8,), spec(WL.MPS_E), spec(WL.MPS_A), E, A,
+                                 precision)
+    assert e1 <= TOL[precision], e1
+    p2 = sc.Plan(WL.MPS_STEP2, (8,), p1.sym_w, spec(WL.MPS_A), precision)
+    E2 = p2.contract(X, dev(A))
+    o2 = oplan(WL.MPS_STEP2, (8,), (p1.sym_w.signs, p1.sym_w.charge, p1.sym_w.dims), spec(WL.MPS_A))
+    want = O.contract_blockloop(o2, want_x, A)
+    assert rel(host(E2), want) <= 2 * TOL[precision]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "split_bf16", "tf32"])
+def test_cc_ladder_reduced_size(sc, precision):
+    """Config 3's contraction at block size 8/4 (G = 8): M = K = 512, N = 128,
+    several tiles in M, eight exact-flush chunks in K."""
+    c = WL.cc_ladder(8, 64, 32)
+    u, v = WL.draw_pair(c)
+    e, p, _, _ = run_case(sc, c.einsum, c.moduli, spec(c.u), spec(c.v), u, v, precision)
+    assert (p.info.M, p.info.K, p.info.N) == (512, 512, 128)
+    assert e <= TOL[precision], e
+
+
+@pytest.mark.parametrize("precision", ["split_bf16", "tf32", "fp64"])
+def test_ragged_tiles(sc, precision):
+    """M, N not multiples of 128 and K not a multiple of 32 (ragged tails)."""
+    su = ((1, -1, 1), (0,), (5, 9, 7))          # a b k
+    sv = ((-1, 1), (0,), (7, 11))               # k c
+    G = 3
+    u = np.random.default_rng(31).standard_normal((G, G, 5, 9, 7))
+    v = np.random.default_rng(32).standard_normal((G, 7, 11))
+    e, p, _, _ = run_case(sc, "abk,kc->abc", (G,), su, sv, u, v, precision)
+    assert (p.info.M, p.info.N, p.info.K) == (135, 11, 7)
+    assert e <= TOL[precision], e
+    # a tensor-core-sized ragged case
+    su2 = ((1, 1, -1), (1,), (13, 11, 37))
+    sv2 = ((1, -1, 1), (2,), (37, 29, 5))
+    u2 = np.random.default_rng(33).standard_normal((G, G, 13, 11, 37))
+    v2 = np.random.default_rng(34).standard_normal((G, G, 37, 29, 5))
+    e2, p2, _, _ = run_case(sc, "abk,kcd->abcd", (G,), su2, sv2, u2, v2, precision)
+    assert p2.info.M == G * 13 * 11 and p2.info.K == 37
+    assert e2 <= TOL[precision], e2
+
+
+@pytest.mark.parametrize("k_blocks", [1, 3, 64, 257])
+def test_split_exactness_all_positive(sc, k_blocks):
+    """All-positive data makes every slice-pair partial sum grow linearly with K:
+    without exact flushes of the top diagonals the FP32 accumulators would
+    round.  K up to 8224 (257 stages of 32)."""
+    G, Dm, Dn = 2, 130, 70
+    Dk = 32 * k_blocks
+    su = ((1, -1), (0,), (Dm, Dk))
+    sv = ((1, -1), (0,), (Dk, Dn))
+    rng = np.random.default_rng(40 + k_blocks)
+    u = rng.random((G, Dm, Dk))
+    v = rng.random((G, Dk, Dn))
+    e, p, _, _ = run_case(sc, "ij,jk->ik", (G,), su, sv, u, v, "split_bf16")
+    assert e <= 1e-10, e
+
+
+def test_split_extreme_exponents(sc):
+    """Rows scaled by very different powers of two, a zero row and subnormals."""
+    G = 2
+    su = ((1, -1), (0,), (64, 96))
+    sv = ((1, -1), (0,), (96, 48))
+    rng = np.random.default_rng(50)
+    u = rng.standard_normal((G, 64, 96)) * np.exp2(rng.integers(-300, 300, size=(G, 64, 1)))
+    v = rng.standard_normal((G, 96, 48)) * np.exp2(rng.integers(-300, 300, size=(G, 1, 48)))
+    u[0, 5, :] = 0.0
+    u[1, 7, :] = 1e-310 * rng.standard_normal(96)
+    p = sc.Plan("ij,jk->ik", (G,), su, sv, "split_bf16")
+    got = host(p.contract(dev(u), dev(v)))
+    p.check_device_error()
+    want = O.contract_blockloop(oplan("ij,jk->ik", (G,), su, sv), u, v)
+    # the natural error scale of a dot product: sum_j |u_ij| |v_jk| (the same
+    # form as the float64 GEMM bound), evaluated in float64 without overflow
+    scale = np.einsum("qij,qjk->qik", np.abs(u), np.abs(v))
+    assert np.all(got[0, 5] == 0.0)
+    ok = scale > 1e-290
+    assert np.all(np.abs(got - want)[ok] <= 1e-11 * scale[ok])
+
+
+def test_nonfinite_input_is_reported(sc):
+    c = WL.Z3_ORDER4
+    u, v = WL.draw_pair(c)
+    u = u.copy()
+    u[0, 0, 0, 0, 0, 0, 0] = np.inf
+    p = sc.Plan(c.einsum, c.moduli, spec(c.u), spec(c.v), "split_bf16")
+    p.contract(dev(u), dev(v))
+    with pytest.raises(sc.SymctrError) as ei:
+        p.check_device_error()
+    assert ei.value.status == 11
+    p.check_device_error()  # the word was cleared
+
+
+# ---------------------------------------------------------------------------
+# gradients
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("precision", ["fp64", "split_bf16"])
+@pytest.mark.parametrize("case", [WL.Z3_ORDER4] + [c for c in WL.small_cases()
+                                                   if c.name in ("sigma_plus_G5", "z2xz3_order4",
+                                                                 "outer_v0_G3", "s0_G4", "t0_G2")],
+                         ids=lambda c: c.name)
+def test_backward_matches_oracle_gradient(sc, case, precision):
+    u, v = WL.draw_pair(case)
+    p = sc.Plan(case.einsum, case.moduli, spec(case.u), spec(case.v), precision)
+    o = oplan(case.einsum, case.moduli, spec(case.u), spec(case.v))
+    y = np.random.default_rng(77).standard_normal(p.shape_w)
+    gu, gv = p.backward(dev(y), dev(u), dev(v))
+    torch.cuda.synchronize()
+    tol = max(TOL[precision], 1e-12)
+    assert rel(host(gu), O.grad_u(o, y, v)) <= tol
+    assert rel(host(gv), O.grad_v(o, u, y)) <= tol
+
+
+def test_autograd_function(sc):
+    c = WL.Z3_ORDER4
+    u, v = WL.draw_pair(c)
+    p = sc.Plan(c.einsum, c.moduli, spec(c.u), spec(c.v), "fp64")
+    ut = dev(u).requires_grad_(True)
+    vt = dev(v).requires_grad_(True)
+    w = sc.contract(p, ut, vt)
+    loss = (w * w).sum()
+    loss.backward()
+    o = oplan(c.einsum, c.moduli, spec(c.u), spec(c.v))
+    wref = O.contract_blockloop(o, u, v)
+    assert rel(host(ut.grad), O.grad_u(o, 2 * wref, v)) <= 1e-12
+    assert rel(host(vt.grad), O.grad_v(o, u, 2 * wref)) <= 1e-12
