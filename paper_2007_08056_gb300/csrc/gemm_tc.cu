@@ -14,17 +14,17 @@
 //   the tensor core keeps working on the d >= 3 pairs: at most 3 pairs x 64 x
 //   2^14 <= 2^22 per drain, so each drained value is an exact integer that
 //   FP32 represents and that a magic-number add turns into an int32.  The
-//   integers are summed in one int64 per output element; at the end acc3 is
-//   folded in and the int64 is rounded once to float64 with the row and
-//   column exponents applied (integer arithmetic only: GB300 has little
-//   float64 throughput).
+//   integers are summed in three int32 registers per output element; at the
+//   end they and acc3 are combined in one int64 that is rounded once to
+//   float64 with the row and column exponents applied (integer arithmetic
+//   only: GB300 has little float64 throughput).
 // TF32 form: one FP32 operand per side (rounded to TF32), kind::tf32,
 //   one accumulator, FP32 -> float64 in the epilogue.
 //
 // CTA: 384 threads.  warp 0 = TMA producer, warp 1 = MMA issuer and TMEM
 // owner, warps 2-3 idle, warps 4..11 = epilogue (two warps per 32-lane TMEM
 // quadrant, one per half of the 128 columns).  Warpgroup 0 gives registers
-// to the two epilogue warpgroups (setmaxnreg 40 / 232), which hold the int64
+// to the two epilogue warpgroups (setmaxnreg 56 / 224), which hold the int32
 // running sums of their 64 columns.  Optional split-K: each K range adds its
 // exact int64 partial sums into a workspace with integer atomics (order-free,
 // so the result is deterministic) and a finalize kernel rounds them.  Tile 128 x 128, 64-byte K rows (32 BF16 or 16
@@ -34,6 +34,8 @@
 #include <cuda.h>
 #include <cstdint>
 #include <cstdio>
+#include <type_traits>
+#include <utility>
 
 #include "symctr_internal.h"
 
@@ -47,18 +49,13 @@ constexpr int TILE_BYTES = TM * ROW_BYTES;     // 8 KB per operand tile per stag
 constexpr int NTHREADS = 384;
 constexpr int EPI_WARP0 = 4;
 constexpr int kExpBias = 4096;     // row exponents are stored biased (0 = all-zero row)
-constexpr uint64_t kTimeoutNs = 2000000000ull;  // 2 s per wait
+constexpr long long kTimeoutCycles = 4000000000ll;  // ~2 s per wait at 2 GHz
 
 enum Mode { MODE_SPLIT = 0, MODE_TF32 = 1 };
 
 // ---------------------------------------------------------------- PTX helpers
 __device__ __forceinline__ uint32_t su32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ uint64_t globaltimer() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
 }
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count) : "memory");
@@ -89,15 +86,44 @@ struct Ctl {
 };
 
 // Bounded wait: true when the phase completed; false on timeout or abort.
+// The budget is counted in SM clock cycles (clock64 is cheap to read; about
+// 2 s at the maximum SM clock, longer at lower clocks).
 __device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t parity, Ctl* ctl,
-                                        uint64_t limit = kTimeoutNs) {
+                                           long long limit = kTimeoutCycles) {
   if (mbar_test(bar, parity)) return true;
-  uint64_t t0 = globaltimer();
+  const long long t0 = clock64();
   for (;;) {
-    for (int i = 0; i < 32; ++i)
-      if (mbar_test(bar, parity)) return true;
+    if (mbar_test(bar, parity)) return true;
     if (ctl->abort) return false;
-    if (globaltimer() - t0 > limit) {
+    if (clock64() - t0 > limit) {
+      atomicOr(ctl->err, (unsigned)DEVERR_TIMEOUT);
+      ctl->abort = 1;
+      return false;
+    }
+  }
+}
+
+// Same, for threads with nothing else to do: the hardware suspends them
+// between polls (suspend-time hint), so they do not take issue slots from
+// the producer and MMA threads.
+__device__ __forceinline__ bool mbar_test_sleep(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(su32(bar)), "r"(parity), "r"(1000000u)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ bool wait_phase_sleep(uint64_t* bar, uint32_t parity, Ctl* ctl) {
+  const long long t0 = clock64();
+  for (;;) {
+    if (mbar_test_sleep(bar, parity)) return true;
+    if (ctl->abort) return false;
+    if (clock64() - t0 > kTimeoutCycles) {
       atomicOr(ctl->err, (unsigned)DEVERR_TIMEOUT);
       ctl->abort = 1;
       return false;
@@ -125,22 +151,11 @@ __device__ __forceinline__ void tc_commit(uint64_t* bar) {
                    su32(bar))
                : "memory");
 }
-template <int KIND>
-__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
-                                       uint32_t acc) {
-  if (KIND == MODE_SPLIT) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc)
-        : "memory");
-  } else {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc)
-        : "memory");
-  }
+// 4 consecutive 32-bit TMEM columns of this warp's 32 lanes.
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t* r) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr));
 }
 
 // 8 consecutive 32-bit TMEM columns of this warp's 32 lanes.
@@ -238,10 +253,81 @@ __device__ __forceinline__ double f32_to_f64(uint32_t u) {
   return __longlong_as_double((long long)(sgn | ((uint64_t)(e - 127 + 1023) << 52) | ((uint64_t)m << 29)));
 }
 
-struct PairList {
-  int n;
-  int8_t i[21], j[21], acc[21];
-};
+// Descriptor offset of slice tile `i`, K step `kk` (16-byte units).
+__host__ __device__ constexpr uint64_t dofs(int i, int kk) {
+  return (uint64_t)((i * TILE_BYTES + kk * 32) >> 4);
+}
+
+// Compile-time loop: f(std::integral_constant<int, 0>) ... f(..<N-1>).
+template <typename F, int... Is>
+__device__ __forceinline__ void static_for_impl(F&& f, std::integer_sequence<int, Is...>) {
+  (f(std::integral_constant<int, Is>{}), ...);
+}
+template <int N, typename F>
+__device__ __forceinline__ void static_for(F&& f) {
+  static_for_impl(f, std::make_integer_sequence<int, N>{});
+}
+
+// One MMA on slice tiles (I, J) at K step KK: the descriptor offsets are
+// immediates, so the issuing thread keeps only the two stage bases live.
+template <int KIND, int I, int J, int KK>
+__device__ __forceinline__ void mma_ij(uint32_t tacc, uint64_t da, uint64_t db, uint32_t id,
+                                       uint32_t acc) {
+  constexpr unsigned long long oa = dofs(I, KK), ob = dofs(J, KK);
+  if (KIND == MODE_SPLIT) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t.reg .b64 a, b;\n\t"
+        "add.u64 a, %1, %5;\n\tadd.u64 b, %2, %6;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, p;\n\t}\n" ::"r"(tacc),
+        "l"(da), "l"(db), "r"(id), "r"(acc), "n"(oa), "n"(ob)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t.reg .b64 a, b;\n\t"
+        "add.u64 a, %1, %5;\n\tadd.u64 b, %2, %6;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], a, b, %3, p;\n\t}\n" ::"r"(tacc),
+        "l"(da), "l"(db), "r"(id), "r"(acc), "n"(oa), "n"(ob)
+        : "memory");
+  }
+}
+
+// Slice pairs of diagonals 0, 1, 2, one exact TMEM accumulator each.  The first
+// MMA into each accumulator overwrites it when `fresh`.
+template <int KIND, int S>
+__device__ __forceinline__ void issue_top(uint32_t tmem, uint64_t da, uint64_t db, uint32_t id,
+                                          bool fresh) {
+  static_for<3>([&](auto D) {
+    if constexpr (D.value <= S - 1) {
+      static_for<D.value + 1>([&](auto I) {
+        static_for<2>([&](auto KK) {
+          constexpr bool first = I.value == 0 && KK.value == 0;
+          mma_ij<KIND, I.value, D.value - I.value, KK.value>(tmem + 128u * D.value, da, db, id,
+                                                             (fresh && first) ? 0u : 1u);
+        });
+      });
+    }
+  });
+}
+
+// Slice pairs of diagonals 3 .. S-1, all into TMEM accumulator 3.
+template <int KIND, int S>
+__device__ __forceinline__ void issue_low(uint32_t tmem, uint64_t da, uint64_t db, uint32_t id,
+                                          bool fresh) {
+  static_for<(S > 3 ? S - 3 : 0)>([&](auto D3) {
+    constexpr int D = D3.value + 3;
+    static_for<D + 1>([&](auto I) {
+      if constexpr (I.value < S && D - I.value < S) {
+        static_for<2>([&](auto KK) {
+          constexpr bool first = D == 3 && I.value == 0 && KK.value == 0;
+          mma_ij<KIND, I.value, D - I.value, KK.value>(tmem + 384u, da, db, id,
+                                                       (fresh && first) ? 0u : 1u);
+        });
+      }
+    });
+  });
+}
 
 struct TcArgs {
   Problem p;
@@ -252,23 +338,33 @@ struct TcArgs {
   const int32_t* ev; // row exponents of V
   double* w;
   unsigned* err;
-  PairList top, low;
-  int acc_live;      // bit mask of accumulators written by at least one MMA
   int ksplit;        // K ranges (grid.z = n_q * ksplit)
   int kb_per_split;  // stages per K range (a multiple of 2)
   unsigned long long* wacc;  // [n_q][M][N] int64 partial sums when ksplit > 1
+  const int64_t* wrow;       // [n_q][M] offsets of W's rows in its reduced form
+  const int64_t* wcol;       // [n_q][N] offsets of W's columns
 };
 
-template <int KIND, int STAGES>
+// Epilogue staging: the results of the 128 x 128 tile in shared memory (the
+// operand stages are free by then), rows padded to 129 entries.
+constexpr int STAGE_LD = TN + 1;
+constexpr size_t STAGE_BYTES_EPI = (size_t)TM * STAGE_LD * 8;
+
+template <int S, int STAGES>
+__host__ __device__ constexpr size_t tile_region_bytes() {
+  return (size_t)STAGES * 2 * S * TILE_BYTES > STAGE_BYTES_EPI ? (size_t)STAGES * 2 * S * TILE_BYTES
+                                                               : STAGE_BYTES_EPI;
+}
+
+template <int KIND, int S, int STAGES>
 __global__ void __launch_bounds__(NTHREADS, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap tma_a, const __grid_constant__ CUtensorMap tma_b,
                    const __grid_constant__ TcArgs args) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  const int S = args.S;
   const Problem& p = args.p;
-  uint8_t* tiles = smem;  // [STAGES][2][S][TILE_BYTES]
-  uint8_t* ctl_base = smem + (size_t)STAGES * 2 * S * TILE_BYTES;
+  uint8_t* tiles = smem;  // [STAGES][2][S][TILE_BYTES], later the epilogue staging
+  uint8_t* ctl_base = smem + tile_region_bytes<S, STAGES>();
   uint64_t* full = (uint64_t*)ctl_base;
   uint64_t* empty = full + STAGES;
   uint64_t* top_full = empty + STAGES;
@@ -277,7 +373,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   uint64_t* drain = acc_full + 1;
   int64_t* coff = (int64_t*)(drain + 1);       // [TN] W column offsets
   int32_t* cexp = (int32_t*)(coff + TN);        // [TN] column exponents
-  uint32_t* tmem_slot = (uint32_t*)(cexp + TN);
+  int64_t* roffs = (int64_t*)(cexp + TN);        // [TM] W row offsets
+  int32_t* rexps = (int32_t*)(roffs + TM);       // [TM] row exponents
+  uint32_t* tmem_slot = (uint32_t*)(rexps + TM);
   Ctl* ctl = (Ctl*)(tmem_slot + 4);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -313,15 +411,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   if (threadIdx.x >= EPI_WARP0 * 32 && threadIdx.x < EPI_WARP0 * 32 + TN) {
     int c = threadIdx.x - EPI_WARP0 * 32;
     int64_t n = n0 + c;
-    coff[c] = n < p.N ? axis_offset(p.w.cols, p.g, Q, n) : 0;
+    coff[c] = n < p.N ? args.wcol[(int64_t)b * p.N + n] : 0;
     cexp[c] = (KIND == MODE_SPLIT && n < p.N) ? args.ev[(int64_t)b * p.N + n] - kExpBias : 0;
+    int64_t m = m0 + c;
+    roffs[c] = m < p.M ? args.wrow[(int64_t)b * p.M + m] : 0;
+    rexps[c] = (KIND == MODE_SPLIT && m < p.M) ? args.eu[(int64_t)b * p.M + m] - kExpBias : 0;
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  if (warp < EPI_WARP0) asm volatile("setmaxnreg.dec.sync.aligned.u32 40;");
+  if (warp < EPI_WARP0) asm volatile("setmaxnreg.dec.sync.aligned.u32 56;");
   if (warp == 0) {
     // ------------------------------------------------------------ producer
     int issued = 0;
@@ -344,7 +445,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         // let the copies this thread issued land before the CTA exits
         int first = issued > STAGES ? issued - STAGES : 0;
         for (int kb = first; kb < issued; ++kb)
-          wait_phase(&full[kb % STAGES], (kb / STAGES) & 1, ctl, kTimeoutNs / 2);
+          wait_phase(&full[kb % STAGES], (kb / STAGES) & 1, ctl, kTimeoutCycles / 2);
       }
     }
   } else if (warp == 1) {
@@ -357,86 +458,72 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         uint32_t ph = (kb / STAGES) & 1;
         if (!wait_phase(&full[st], ph, ctl)) break;
         tc_fence_after();
-        const uint32_t sa = ab + st * stage_bytes;
-        const uint32_t sb = sa + S * TILE_BYTES;
+        const uint64_t da = sdesc(ab + st * stage_bytes);
+        const uint64_t db = sdesc(ab + st * stage_bytes + S * TILE_BYTES);
         const bool cfirst = KIND == MODE_TF32 ? (kb == 0) : (kb % 2 == 0);
         const int chunk = KIND == MODE_TF32 ? 0 : kb / 2;
         const bool final_chunk = chunk == n_chunks - 1;
-        auto issue = [&](const PairList& L, bool fresh) {
-          bool seen[4] = {false, false, false, false};
-          for (int q = 0; q < L.n; ++q) {
-            int a = L.acc[q];
-            uint32_t d = tmem + 128u * a;
-            for (int kk = 0; kk < 2; ++kk) {
-              uint32_t accum = (fresh && !seen[a] && kk == 0) ? 0u : 1u;
-              tc_mma<KIND>(d, sdesc(sa + L.i[q] * TILE_BYTES + kk * 32),
-                           sdesc(sb + L.j[q] * TILE_BYTES + kk * 32), id, accum);
-            }
-            seen[a] = true;
-          }
-        };
         bool ok = true;
         if (cfirst) {
-          issue(args.low, kb == 0);
+          issue_low<KIND, S>(tmem, da, db, id, kb == 0);
           if (chunk > 0) {
             ok = wait_phase(top_empty, (chunk - 1) & 1, ctl);
             tc_fence_after();
           }
-          if (ok) issue(args.top, true);
+          if (ok) issue_top<KIND, S>(tmem, da, db, id, true);
         } else {
-          issue(args.top, false);
+          issue_top<KIND, S>(tmem, da, db, id, false);
           if (!final_chunk) tc_commit(top_full);
-          issue(args.low, false);
+          issue_low<KIND, S>(tmem, da, db, id, false);
         }
         tc_commit(&empty[st]);
         if (!ok) break;
       }
       tc_commit(acc_full);
       tc_commit(drain);
-      wait_phase(drain, 0, ctl, kTimeoutNs / 2);
+      wait_phase(drain, 0, ctl, kTimeoutCycles / 2);
     }
   } else if (warp >= EPI_WARP0) {
     // ------------------------------------------------------------ epilogue
-    asm volatile("setmaxnreg.inc.sync.aligned.u32 232;");
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 224;");
     const int ew = warp - EPI_WARP0;      // 0..7
     const int quad = warp & 3;            // TMEM lane quadrant this warp may access
     const int half = ew >> 2;             // column half
     const int row = quad * 32 + lane;
     const int64_t m = m0 + row;
     const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(half * 64);
-    int64_t racc[64];
+    // Running sums of the exact diagonals d = 0, 1, 2 in their own units
+    // (1, 2^-8, 2^-16): each drain adds at most 3 * 64 * 2^14 < 2^22, so int32
+    // holds 2^9 drains, i.e. K up to 32768 per K range (longer K is split).
+    int32_t s0[64], s1[64], s2[64];
 #pragma unroll
-    for (int j = 0; j < 64; ++j) racc[j] = 0;
-    const float M0 = 12582912.0f;              // 1.5 * 2^23
-    const float M1 = 12582912.0f / 256.0f;     // unit 2^-8
-    const float M2 = 12582912.0f / 65536.0f;   // unit 2^-16
-    const uint32_t B0 = __float_as_uint(M0), B1 = __float_as_uint(M1), B2 = __float_as_uint(M2);
-    const uint32_t C01 = B0 * 256u + B1;
-    const bool live1 = (args.acc_live >> 1) & 1, live2 = (args.acc_live >> 2) & 1,
-               live3 = (args.acc_live >> 3) & 1;
+    for (int j = 0; j < 64; ++j) s0[j] = s1[j] = s2[j] = 0;
+    const float M0 = 12582912.0f;              // 1.5 * 2^23: ulp 1
+    const float M1 = 12582912.0f / 256.0f;     // ulp 2^-8
+    const float M2 = 12582912.0f / 65536.0f;   // ulp 2^-16
+    const int32_t B0 = (int32_t)__float_as_uint(M0), B1 = (int32_t)__float_as_uint(M1),
+                  B2 = (int32_t)__float_as_uint(M2);
+    constexpr bool live1 = S >= 2, live2 = S >= 3, live3 = S >= 4;
     auto drain_top = [&]() {
 #pragma unroll
-      for (int pc = 0; pc < 8; ++pc) {
-        uint32_t a0[8], a1[8], a2[8];
-        tmem_ld8(lane_base + 0 + pc * 8, a0);
-        if (live1) tmem_ld8(lane_base + 128 + pc * 8, a1);
-        if (live2) tmem_ld8(lane_base + 256 + pc * 8, a2);
+      for (int pc = 0; pc < 16; ++pc) {
+        uint32_t a0[4], a1[4], a2[4];
+        tmem_ld4(lane_base + 0 + pc * 4, a0);
+        if (live1) tmem_ld4(lane_base + 128 + pc * 4, a1);
+        if (live2) tmem_ld4(lane_base + 256 + pc * 4, a2);
         tmem_wait_ld();
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          uint32_t v0 = __float_as_uint(__uint_as_float(a0[j]) + M0);
-          uint32_t v1 = live1 ? __float_as_uint(__uint_as_float(a1[j]) + M1) : B1;
-          uint32_t v2 = live2 ? __float_as_uint(__uint_as_float(a2[j]) + M2) : B2;
-          int32_t x = (int32_t)(v0 * 256u + v1 - C01);
-          int32_t y = (int32_t)(v2 - B2);
-          racc[pc * 8 + j] += (int64_t)x * 256 + y;
+        for (int j = 0; j < 4; ++j) {
+          s0[pc * 4 + j] += (int32_t)__float_as_uint(__uint_as_float(a0[j]) + M0) - B0;
+          if (live1) s1[pc * 4 + j] += (int32_t)__float_as_uint(__uint_as_float(a1[j]) + M1) - B1;
+          if (live2) s2[pc * 4 + j] += (int32_t)__float_as_uint(__uint_as_float(a2[j]) + M2) - B2;
         }
       }
     };
     bool ok = true;
     if (KIND == MODE_SPLIT) {
       for (int c = 0; c + 1 < n_chunks; ++c) {
-        if (!wait_phase(top_full, c & 1, ctl)) {
+        if (!wait_phase_sleep(top_full, c & 1, ctl)) {
           ok = false;
           break;
         }
@@ -447,49 +534,64 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (lane == 0) mbar_arrive(top_empty);
       }
     }
-    if (ok) ok = wait_phase(acc_full, 0, ctl);
-    if (ok && !ctl->abort) {
+    if (ok) ok = wait_phase_sleep(acc_full, 0, ctl);
+    ok = ok && !ctl->abort;
+    if (ok) {
       tc_fence_after();
-      const bool row_ok = m < p.M;
-      const int64_t roff = row_ok ? axis_offset(p.w.rows, p.g, Q, m) : 0;
-      double* wout = args.w + roff;
       if (KIND == MODE_SPLIT) {
-        drain_top();
-        const int32_t er = row_ok ? args.eu[(int64_t)b * p.M + m] - kExpBias : 0;
-        unsigned long long* wacc = args.wacc + ((int64_t)b * p.M + m) * p.N + n0;
+        // last chunk's exact diagonals and acc3, four columns at a time (the
+        // running sums of finished columns die early), staged as int64
+        int64_t* st64 = (int64_t*)tiles + row * STAGE_LD + half * 64;
 #pragma unroll
-        for (int pc = 0; pc < 4; ++pc) {
-          uint32_t a3[16];
-          if (live3) {
-            tmem_ld16(lane_base + 384 + pc * 16, a3);
-            tmem_wait_ld();
-          }
+        for (int pc = 0; pc < 16; ++pc) {
+          uint32_t a0[4], a1[4], a2[4], a3[4];
+          tmem_ld4(lane_base + 0 + pc * 4, a0);
+          if (live1) tmem_ld4(lane_base + 128 + pc * 4, a1);
+          if (live2) tmem_ld4(lane_base + 256 + pc * 4, a2);
+          if (live3) tmem_ld4(lane_base + 384 + pc * 4, a3);
+          tmem_wait_ld();
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            int c = half * 64 + pc * 16 + j;
+          for (int j = 0; j < 4; ++j) {
+            const int jj = pc * 4 + j;
+            int32_t t0 = s0[jj] + (int32_t)__float_as_uint(__uint_as_float(a0[j]) + M0) - B0;
+            int32_t t1 = live1 ? s1[jj] + (int32_t)__float_as_uint(__uint_as_float(a1[j]) + M1) - B1 : 0;
+            int32_t t2 = live2 ? s2[jj] + (int32_t)__float_as_uint(__uint_as_float(a2[j]) + M2) - B2 : 0;
             long long low = live3 ? __float2ll_rn(__uint_as_float(a3[j]) * 16777216.0f) : 0ll;
-            long long Rv = (long long)(racc[pc * 16 + j] << 8) + low;
-            if (row_ok && n0 + c < p.N) {
-              if (args.ksplit > 1) atomicAdd(wacc + c, (unsigned long long)Rv);
-              else wout[coff[c]] = i64_scaled(Rv, er + cexp[c] - 36);
-            }
+            st64[jj] = ((long long)t0 << 24) + ((long long)t1 << 16) + ((long long)t2 << 8) + low;
           }
         }
       } else {
+        uint32_t* st32 = (uint32_t*)tiles + row * STAGE_LD + half * 64;
 #pragma unroll
         for (int pc = 0; pc < 4; ++pc) {
           uint32_t a0[16];
           tmem_ld16(lane_base + pc * 16, a0);
           tmem_wait_ld();
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            int c = half * 64 + pc * 16 + j;
-            if (row_ok && n0 + c < p.N) wout[coff[c]] = f32_to_f64(a0[j]);
-          }
+          for (int j = 0; j < 16; ++j) st32[pc * 16 + j] = a0[j];
         }
       }
     }
     tc_fence_before();
+    // all 256 epilogue threads meet here, whatever path they took
+    asm volatile("bar.sync 1, 256;" ::: "memory");
+    if (ok) {
+      // coalesced: consecutive lanes take consecutive columns of one row
+      const int t = threadIdx.x - EPI_WARP0 * 32;
+      for (int idx = t; idx < TM * TN; idx += 256) {
+        const int r = idx / TN, c = idx % TN;
+        if (m0 + r >= p.M || n0 + c >= p.N) continue;
+        if (KIND == MODE_SPLIT) {
+          const long long Rv = ((const long long*)tiles)[r * STAGE_LD + c];
+          if (args.ksplit > 1)
+            atomicAdd(args.wacc + ((int64_t)b * p.M + m0 + r) * p.N + n0 + c, (unsigned long long)Rv);
+          else
+            args.w[roffs[r] + coff[c]] = i64_scaled(Rv, rexps[r] + cexp[c] - 36);
+        } else {
+          args.w[roffs[r] + coff[c]] = f32_to_f64(((const uint32_t*)tiles)[r * STAGE_LD + c]);
+        }
+      }
+    }
   }
   __syncthreads();
   if (warp == 1) {
@@ -504,6 +606,8 @@ __global__ void __launch_bounds__(256) split_finalize_kernel(Problem p,
                                                              const unsigned long long* __restrict__ wacc,
                                                              const int32_t* __restrict__ eu,
                                                              const int32_t* __restrict__ ev,
+                                                             const int64_t* __restrict__ wrow,
+                                                             const int64_t* __restrict__ wcol,
                                                              double* __restrict__ w) {
   const int64_t total = (int64_t)p.n_q * p.M * p.N;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
@@ -511,10 +615,8 @@ __global__ void __launch_bounds__(256) split_finalize_kernel(Problem p,
     int64_t b = i / (p.M * p.N);
     int64_t r = i - b * p.M * p.N;
     int64_t m = r / p.N, n = r % p.N;
-    int Q = batch_irrep(p, (int)b);
     int e = (eu[b * p.M + m] - kExpBias) + (ev[b * p.N + n] - kExpBias) - 36;
-    w[axis_offset(p.w.rows, p.g, Q, m) + axis_offset(p.w.cols, p.g, Q, n)] =
-        i64_scaled((long long)wacc[i], e);
+    w[wrow[b * p.M + m] + wcol[b * p.N + n]] = i64_scaled((long long)wacc[i], e);
   }
 }
 
@@ -554,26 +656,8 @@ bool make_map(CUtensorMap* map, const void* base, bool is_f32, int64_t kpad, int
   return r == CUDA_SUCCESS;
 }
 
-void build_pairs(int S, PairList* top, PairList* low, int* live) {
-  top->n = low->n = 0;
-  *live = 0;
-  for (int d = 0; d <= S - 1; ++d) {
-    for (int i = 0; i <= d; ++i) {
-      int j = d - i;
-      if (i >= S || j >= S) continue;
-      PairList* L = d <= 2 ? top : low;
-      int acc = d <= 2 ? d : 3;
-      L->i[L->n] = (int8_t)i;
-      L->j[L->n] = (int8_t)j;
-      L->acc[L->n] = (int8_t)acc;
-      ++L->n;
-      *live |= 1 << acc;
-    }
-  }
-}
-
-template <int KIND, int STAGES>
-cudaError_t launch_tc(const Problem& p, int S, const void* a, const void* bop, const int32_t* eu,
+template <int KIND, int S, int STAGES>
+cudaError_t launch_tc(const Problem& p, const Tables& tab, const void* a, const void* bop, const int32_t* eu,
                       const int32_t* ev, int64_t kpad, double* w, unsigned* err, int ksplit,
                       unsigned long long* wacc, cudaStream_t st) {
   const bool f32 = KIND == MODE_TF32;
@@ -595,21 +679,15 @@ cudaError_t launch_tc(const Problem& p, int S, const void* a, const void* bop, c
   if (args.kb_per_split < 2) args.kb_per_split = 2;
   args.ksplit = (args.n_kb + args.kb_per_split - 1) / args.kb_per_split;
   args.wacc = wacc;
+  args.wrow = tab.wrow;
+  args.wcol = tab.wcol;
   if (args.ksplit > 1) {
     cudaError_t e0 = cudaMemsetAsync(wacc, 0, sizeof(unsigned long long) * p.n_q * p.M * p.N, st);
     if (e0 != cudaSuccess) return e0;
   }
-  if (KIND == MODE_SPLIT) {
-    build_pairs(S, &args.top, &args.low, &args.acc_live);
-  } else {
-    args.top.n = 1;
-    args.top.i[0] = args.top.j[0] = args.top.acc[0] = 0;
-    args.low.n = 0;
-    args.acc_live = 1;
-  }
-  size_t smem = 1024 + (size_t)STAGES * 2 * S * TILE_BYTES + 8 * (2 * STAGES + 4) + 8 * TN +
-                4 * TN + 16 + 64;
-  auto kern = gemm_tc_kernel<KIND, STAGES>;
+  size_t smem = 1024 + tile_region_bytes<S, STAGES>() + 8 * (2 * STAGES + 4) + 8 * TN + 4 * TN +
+                8 * TM + 4 * TM + 16 + 64;
+  auto kern = gemm_tc_kernel<KIND, S, STAGES>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int64_t gx = (p.N + TN - 1) / TN, gy = (p.M + TM - 1) / TM;
@@ -621,7 +699,8 @@ cudaError_t launch_tc(const Problem& p, int S, const void* a, const void* bop, c
   if (args.ksplit > 1) {
     int64_t total = (int64_t)p.n_q * p.M * p.N;
     int64_t blocks = (total + 255) / 256;
-    split_finalize_kernel<<<(int)(blocks < 4096 ? blocks : 4096), 256, 0, st>>>(p, wacc, eu, ev, w);
+    split_finalize_kernel<<<(int)(blocks < 4096 ? blocks : 4096), 256, 0, st>>>(p, wacc, eu, ev, tab.wrow,
+                                                                                 tab.wcol, w);
     ++g_kernel_launches;
   }
   return cudaGetLastError();
@@ -629,16 +708,23 @@ cudaError_t launch_tc(const Problem& p, int S, const void* a, const void* bop, c
 
 }  // namespace
 
-cudaError_t launch_gemm_split(const Problem& p, int n_slices, const uint16_t* us,
+cudaError_t launch_gemm_split(const Problem& p, const Tables& tab, int n_slices, const uint16_t* us,
                               const uint16_t* vs, const int32_t* eu, const int32_t* ev,
                               int64_t kpad, double* w, unsigned* err, int ksplit,
                               unsigned long long* wacc, cudaStream_t st) {
-  return launch_tc<MODE_SPLIT, 2>(p, n_slices, us, vs, eu, ev, kpad, w, err, ksplit, wacc, st);
+  switch (n_slices) {
+    case 2: return launch_tc<MODE_SPLIT, 2, 2>(p, tab, us, vs, eu, ev, kpad, w, err, ksplit, wacc, st);
+    case 3: return launch_tc<MODE_SPLIT, 3, 2>(p, tab, us, vs, eu, ev, kpad, w, err, ksplit, wacc, st);
+    case 4: return launch_tc<MODE_SPLIT, 4, 2>(p, tab, us, vs, eu, ev, kpad, w, err, ksplit, wacc, st);
+    case 5: return launch_tc<MODE_SPLIT, 5, 2>(p, tab, us, vs, eu, ev, kpad, w, err, ksplit, wacc, st);
+    case 6: return launch_tc<MODE_SPLIT, 6, 2>(p, tab, us, vs, eu, ev, kpad, w, err, ksplit, wacc, st);
+  }
+  return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_gemm_tf32(const Problem& p, const float* u, const float* v, int64_t kpad,
-                             double* w, unsigned* err, cudaStream_t st) {
-  return launch_tc<MODE_TF32, 6>(p, 1, u, v, nullptr, nullptr, kpad, w, err, 1, nullptr, st);
+cudaError_t launch_gemm_tf32(const Problem& p, const Tables& tab, const float* u, const float* v,
+                             int64_t kpad, double* w, unsigned* err, cudaStream_t st) {
+  return launch_tc<MODE_TF32, 1, 6>(p, tab, u, v, nullptr, nullptr, kpad, w, err, 1, nullptr, st);
 }
 
 }  // namespace symctr

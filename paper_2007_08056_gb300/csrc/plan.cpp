@@ -90,7 +90,7 @@ struct symctr_plan {
   int n_slices = 0;
   int64_t kpad = 0;
   // workspace layout (byte offsets)
-  uint64_t ws_bytes = 256, off_a = 0, off_b = 0, off_ea = 0, off_eb = 0, off_acc = 0;
+  uint64_t ws_bytes = 256, off_a = 0, off_b = 0, off_ea = 0, off_eb = 0, off_acc = 0, off_tab = 0;
   int ksplit = 1;
   bool tensor_core = false;
   symctr_plan* bwd_u = nullptr;
@@ -360,6 +360,7 @@ symctr_status build(const char* einsum, int n_moduli, const int32_t* moduli, con
     return at;
   };
   if (P->tensor_core) {
+    P->off_tab = region(tables_entries(pr) * 8);
     int64_t ra = 0, rb = 0;
     if (!mul_ok((int64_t)nq * pr.M, P->kpad, &ra) || !mul_ok((int64_t)nq * pr.N, P->kpad, &rb))
       return bail(SYMCTR_ERR_OVERFLOW, "aligned operand too large");
@@ -445,29 +446,41 @@ symctr_status run_contract_body(const symctr_plan* P, const double* u, const dou
     if (P->prof) cudaEventRecord(P->ev[2], st);
     return cuda_status(e, "gemm_f64");
   }
+  Tables tab;
+  {
+    int64_t* t0 = (int64_t*)(base + P->off_tab);
+    tab.urow = t0;
+    tab.ucol = tab.urow + (int64_t)pr.n_q * pr.M;
+    tab.vrow = tab.ucol + (int64_t)pr.n_q * pr.K;
+    tab.vcol = tab.vrow + (int64_t)pr.n_q * pr.N;
+    tab.wrow = tab.vcol + (int64_t)pr.n_q * pr.K;
+    tab.wcol = tab.wrow + (int64_t)pr.n_q * pr.M;
+  }
+  e = launch_tables(pr, tab, st);
+  if (e != cudaSuccess) return cuda_status(e, "tables");
   if (P->prec == SYMCTR_SPLIT_BF16) {
     uint16_t* as = (uint16_t*)(base + P->off_a);
     uint16_t* bs = (uint16_t*)(base + P->off_b);
     int32_t* ea = (int32_t*)(base + P->off_ea);
     int32_t* eb = (int32_t*)(base + P->off_eb);
-    e = launch_split_operand(pr, 0, P->n_slices, u, as, P->kpad, ea, err, st);
+    e = launch_split_operand(pr, tab, 0, P->n_slices, u, as, P->kpad, ea, err, st);
     if (e != cudaSuccess) return cuda_status(e, "split U");
-    e = launch_split_operand(pr, 1, P->n_slices, v, bs, P->kpad, eb, err, st);
+    e = launch_split_operand(pr, tab, 1, P->n_slices, v, bs, P->kpad, eb, err, st);
     if (e != cudaSuccess) return cuda_status(e, "split V");
     if (P->prof) cudaEventRecord(P->ev[1], st);
-    e = launch_gemm_split(pr, P->n_slices, as, bs, ea, eb, P->kpad, w, err, P->ksplit,
+    e = launch_gemm_split(pr, tab, P->n_slices, as, bs, ea, eb, P->kpad, w, err, P->ksplit,
                           (unsigned long long*)(base + P->off_acc), st);
     if (P->prof) cudaEventRecord(P->ev[2], st);
     return cuda_status(e, "gemm_split");
   }
   float* a32 = (float*)(base + P->off_a);
   float* b32 = (float*)(base + P->off_b);
-  e = launch_tf32_operand(pr, 0, u, a32, P->kpad, st);
+  e = launch_tf32_operand(pr, tab, 0, u, a32, P->kpad, st);
   if (e != cudaSuccess) return cuda_status(e, "tf32 U");
-  e = launch_tf32_operand(pr, 1, v, b32, P->kpad, st);
+  e = launch_tf32_operand(pr, tab, 1, v, b32, P->kpad, st);
   if (e != cudaSuccess) return cuda_status(e, "tf32 V");
   if (P->prof) cudaEventRecord(P->ev[1], st);
-  e = launch_gemm_tf32(pr, a32, b32, P->kpad, w, err, st);
+  e = launch_gemm_tf32(pr, tab, a32, b32, P->kpad, w, err, st);
   if (P->prof) cudaEventRecord(P->ev[2], st);
   return cuda_status(e, "gemm_tf32");
 }

@@ -108,6 +108,21 @@ struct Problem {
 
 SC_HD int batch_irrep(const Problem& p, int b) { return p.n_q == 1 ? p.q_single : b; }
 
+// Offset tables of the aligned forms for one contraction (device memory in the
+// workspace): row_off / col_off of every (batch, index), int64.
+struct Tables {
+  int64_t* urow;  // [n_q][M]
+  int64_t* ucol;  // [n_q][K]
+  int64_t* vrow;  // [n_q][N]
+  int64_t* vcol;  // [n_q][K]
+  int64_t* wrow;  // [n_q][M]
+  int64_t* wcol;  // [n_q][N]
+};
+
+inline int64_t tables_entries(const Problem& p) {
+  return (int64_t)p.n_q * (2 * p.M + 2 * p.N + 2 * p.K);
+}
+
 // Device error word codes (first uint32 of the workspace).
 enum : unsigned { DEVERR_NONE = 0, DEVERR_TIMEOUT = 1, DEVERR_NONFINITE = 2 };
 
@@ -126,27 +141,34 @@ cudaError_t launch_align_f64(const Problem& p, int operand, int direction, const
 cudaError_t launch_gemm_f64(const Problem& p, const double* u, const double* v, double* w,
                             cudaStream_t st);
 cudaError_t launch_fill_zero(double* w, int64_t n, cudaStream_t st);
-cudaError_t launch_split_operand(const Problem& p, int operand, int n_slices, const double* src,
-                                 uint16_t* slices, int64_t kpad, int32_t* exps, unsigned* err,
-                                 cudaStream_t st);
-cudaError_t launch_gemm_split(const Problem& p, int n_slices, const uint16_t* us,
+cudaError_t launch_tables(const Problem& p, const Tables& t, cudaStream_t st);
+cudaError_t launch_split_operand(const Problem& p, const Tables& t, int operand, int n_slices,
+                                 const double* src, uint16_t* slices, int64_t kpad, int32_t* exps,
+                                 unsigned* err, cudaStream_t st);
+cudaError_t launch_gemm_split(const Problem& p, const Tables& t, int n_slices, const uint16_t* us,
                               const uint16_t* vs, const int32_t* eu, const int32_t* ev,
                               int64_t kpad, double* w, unsigned* err, int ksplit,
                               unsigned long long* wacc, cudaStream_t st);
-cudaError_t launch_tf32_operand(const Problem& p, int operand, const double* src, float* dst,
-                                int64_t kpad, cudaStream_t st);
-cudaError_t launch_gemm_tf32(const Problem& p, const float* u, const float* v, int64_t kpad,
-                             double* w, unsigned* err, cudaStream_t st);
+cudaError_t launch_tf32_operand(const Problem& p, const Tables& t, int operand, const double* src,
+                                float* dst, int64_t kpad, cudaStream_t st);
+cudaError_t launch_gemm_tf32(const Problem& p, const Tables& t, const float* u, const float* v,
+                             int64_t kpad, double* w, unsigned* err, cudaStream_t st);
 
 // K ranges of the split-BF16 GEMM: enough CTAs to fill the GPU when the
 // problem has few 128x128 tiles (deterministic: independent of the device).
+// A K range holds at most kMaxChunksPerRange exact drains (int32 running sums).
+constexpr int64_t kMaxChunksPerRange = 512;
+
 inline int split_k_ranges(const Problem& p, int64_t kpad) {
   int64_t tiles = ((p.M + 127) / 128) * ((p.N + 127) / 128) * (int64_t)p.n_q;
-  int64_t chunks = kpad / kKChunk;
-  if (tiles >= 80 || chunks < 4) return 1;
-  int64_t want = (160 + tiles - 1) / tiles;
-  int64_t per = (chunks + want - 1) / want;     // chunks per range
-  if (per < 2) per = 2;
+  int64_t chunks = (kpad + kKChunk - 1) / kKChunk;
+  int64_t per = chunks;                         // chunks per range
+  if (tiles < 80 && chunks >= 4) {
+    int64_t want = (160 + tiles - 1) / tiles;
+    per = (chunks + want - 1) / want;
+    if (per < 2) per = 2;
+  }
+  if (per > kMaxChunksPerRange) per = kMaxChunksPerRange;
   return (int)((chunks + per - 1) / per);
 }
 

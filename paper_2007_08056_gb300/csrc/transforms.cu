@@ -138,6 +138,29 @@ __device__ __forceinline__ uint16_t digit_bf16(int a, int slice) {
   return (uint16_t)(__float_as_uint(f) >> 16);         // low 16 bits are zero
 }
 
+// Offset tables: one thread per (batch, index) of the six index maps.
+__global__ void __launch_bounds__(THREADS) tables_kernel(Problem p, Tables t) {
+  const int64_t segs[6] = {p.M, p.K, p.N, p.K, p.M, p.N};
+  int64_t total = 0;
+  for (int i = 0; i < 6; ++i) total += segs[i] * p.n_q;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t rem = e;
+    int which = 0;
+    while (rem >= segs[which] * p.n_q) {
+      rem -= segs[which] * p.n_q;
+      ++which;
+    }
+    int64_t b = rem / segs[which], r = rem % segs[which];
+    int Q = batch_irrep(p, (int)b);
+    const AxisMap& a = which == 0 ? p.u.rows : which == 1 ? p.u.cols : which == 2 ? p.v.rows
+                     : which == 3 ? p.v.cols : which == 4 ? p.w.rows : p.w.cols;
+    int64_t* dst = which == 0 ? t.urow : which == 1 ? t.ucol : which == 2 ? t.vrow
+                 : which == 3 ? t.vcol : which == 4 ? t.wrow : t.wcol;
+    dst[rem] = axis_offset(a, p.g, Q, r);
+  }
+}
+
 // Row exponents, stored biased: E + kExpBias for a row whose largest entry
 // lies in [2^E, 2^(E+1)), 0 for an all-zero row (the buffer is zeroed first).
 constexpr int32_t kExpBias = 4096;
@@ -145,7 +168,8 @@ constexpr int SCAN_COLS = 256;
 
 // Exponent scan: tiles of 32 rows x 256 columns, per-row maxima combined with
 // atomicMax in global memory, so any row length spreads over many CTAs.
-__global__ void __launch_bounds__(THREADS) exp_scan_kernel(Problem p, OperandMap m, int64_t R,
+__global__ void __launch_bounds__(THREADS) exp_scan_kernel(Problem p, const int64_t* __restrict__ rtab,
+                                                           const int64_t* __restrict__ ctab, int64_t R,
                                                            int64_t Cn, bool fast_rows,
                                                            const double* __restrict__ src,
                                                            int32_t* __restrict__ exps,
@@ -159,38 +183,52 @@ __global__ void __launch_bounds__(THREADS) exp_scan_kernel(Problem p, OperandMap
     int64_t b = tI / (rt * ct);
     int64_t rem = tI - b * rt * ct;
     int64_t r0 = (rem / ct) * TILE, c0 = (rem % ct) * SCAN_COLS;
-    int Q = batch_irrep(p, (int)b);
     __syncthreads();
     if (threadIdx.x < TILE) {
       int64_t r = r0 + threadIdx.x;
-      roff[threadIdx.x] = r < R ? axis_offset(m.rows, p.g, Q, r) : 0;
+      roff[threadIdx.x] = r < R ? rtab[b * R + r] : 0;
       rmax[threadIdx.x] = 0;
     }
     {
       int64_t c = c0 + threadIdx.x;
-      coff[threadIdx.x] = c < Cn ? axis_offset(m.cols, p.g, Q, c) : 0;
+      coff[threadIdx.x] = c < Cn ? ctab[b * Cn + c] : 0;
     }
     __syncthreads();
     unsigned bad = 0;
+    constexpr int PER = SCAN_COLS / (THREADS / 32);   // 32 loads per thread, issued together
     if (fast_rows) {
       // lanes walk rows (contiguous), warps walk columns
+      double x[PER];
+      const bool rok = r0 + tx < R;
+#pragma unroll
+      for (int i = 0; i < PER; ++i) {
+        int cc = ty + i * (THREADS / 32);
+        x[i] = (rok && c0 + cc < Cn) ? src[roff[tx] + coff[cc]] : 0.0;
+      }
       int32_t mx = 0;
-      for (int cc = ty; cc < SCAN_COLS; cc += THREADS / 32) {
-        if (r0 + tx < R && c0 + cc < Cn) {
-          int32_t e = exponent_of(src[roff[tx] + coff[cc]], &bad);
-          mx = max(mx, e == kZeroRowExp ? 0 : e + kExpBias);
-        }
+#pragma unroll
+      for (int i = 0; i < PER; ++i) {
+        int32_t e = exponent_of(x[i], &bad);
+        mx = max(mx, e == kZeroRowExp ? 0 : e + kExpBias);
       }
       atomicMax(&rmax[tx], mx);
     } else {
       // lanes walk columns (contiguous), warps walk rows
-      for (int rr = ty; rr < TILE; rr += THREADS / 32) {
+#pragma unroll
+      for (int rg = 0; rg < TILE / (THREADS / 32); ++rg) {
+        int rr = ty + rg * (THREADS / 32);
+        const bool rok = r0 + rr < R;
+        double x[SCAN_COLS / 32];
+#pragma unroll
+        for (int i = 0; i < SCAN_COLS / 32; ++i) {
+          int cc = tx + 32 * i;
+          x[i] = (rok && c0 + cc < Cn) ? src[roff[rr] + coff[cc]] : 0.0;
+        }
         int32_t mx = 0;
-        for (int cc = tx; cc < SCAN_COLS; cc += 32) {
-          if (r0 + rr < R && c0 + cc < Cn) {
-            int32_t e = exponent_of(src[roff[rr] + coff[cc]], &bad);
-            mx = max(mx, e == kZeroRowExp ? 0 : e + kExpBias);
-          }
+#pragma unroll
+        for (int i = 0; i < SCAN_COLS / 32; ++i) {
+          int32_t e = exponent_of(x[i], &bad);
+          mx = max(mx, e == kZeroRowExp ? 0 : e + kExpBias);
         }
         for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         if (tx == 0) rmax[rr] = max(rmax[rr], mx);
@@ -208,7 +246,8 @@ constexpr int SLICE_COLS = 64;
 // Slicing: tiles of 32 rows x 64 columns of the padded aligned operand; the
 // source tile goes through shared memory so that the reduced form is read
 // along its contiguous axis and every slice row is written as 128-byte runs.
-__global__ void __launch_bounds__(THREADS) slice_kernel(Problem p, OperandMap m, int64_t R,
+__global__ void __launch_bounds__(THREADS) slice_kernel(Problem p, const int64_t* __restrict__ rtab,
+                                                        const int64_t* __restrict__ ctab, int64_t R,
                                                         int64_t Cn, int64_t kpad, bool fast_rows,
                                                         int S, const double* __restrict__ src,
                                                         const int32_t* __restrict__ exps,
@@ -224,32 +263,40 @@ __global__ void __launch_bounds__(THREADS) slice_kernel(Problem p, OperandMap m,
     int64_t b = tI / (rt * ct);
     int64_t rem = tI - b * rt * ct;
     int64_t r0 = (rem / ct) * TILE, c0 = (rem % ct) * SLICE_COLS;
-    int Q = batch_irrep(p, (int)b);
     __syncthreads();
     if (threadIdx.x < TILE) {
       int64_t r = r0 + threadIdx.x;
-      roff[threadIdx.x] = r < R ? axis_offset(m.rows, p.g, Q, r) : 0;
+      roff[threadIdx.x] = r < R ? rtab[b * R + r] : 0;
       int32_t st = r < R ? exps[b * R + r] : 0;
       rexp[threadIdx.x] = st == 0 ? kZeroRowExp : st - kExpBias;
     } else if (threadIdx.x < TILE + SLICE_COLS) {
       int64_t c = c0 + threadIdx.x - TILE;
-      coff[threadIdx.x - TILE] = c < Cn ? axis_offset(m.cols, p.g, Q, c) : 0;
+      coff[threadIdx.x - TILE] = c < Cn ? ctab[b * Cn + c] : 0;
     }
     __syncthreads();
     if (fast_rows) {
-      for (int cc = ty; cc < SLICE_COLS; cc += THREADS / 32) {
-        double x = 0.0;
-        if (r0 + tx < R && c0 + cc < Cn) x = src[roff[tx] + coff[cc]];
-        tile[tx][cc] = x;
+      double x[SLICE_COLS / (THREADS / 32)];
+      const bool rok = r0 + tx < R;
+#pragma unroll
+      for (int i = 0; i < SLICE_COLS / (THREADS / 32); ++i) {
+        int cc = ty + i * (THREADS / 32);
+        x[i] = (rok && c0 + cc < Cn) ? src[roff[tx] + coff[cc]] : 0.0;
       }
+#pragma unroll
+      for (int i = 0; i < SLICE_COLS / (THREADS / 32); ++i) tile[tx][ty + i * (THREADS / 32)] = x[i];
     } else {
-      for (int rr = ty; rr < TILE; rr += THREADS / 32) {
-        for (int cc = tx; cc < SLICE_COLS; cc += 32) {
-          double x = 0.0;
-          if (r0 + rr < R && c0 + cc < Cn) x = src[roff[rr] + coff[cc]];
-          tile[rr][cc] = x;
+      double x[TILE / (THREADS / 32)][SLICE_COLS / 32];
+#pragma unroll
+      for (int rg = 0; rg < TILE / (THREADS / 32); ++rg)
+#pragma unroll
+        for (int i = 0; i < SLICE_COLS / 32; ++i) {
+          int rr = ty + rg * (THREADS / 32), cc = tx + 32 * i;
+          x[rg][i] = (r0 + rr < R && c0 + cc < Cn) ? src[roff[rr] + coff[cc]] : 0.0;
         }
-      }
+#pragma unroll
+      for (int rg = 0; rg < TILE / (THREADS / 32); ++rg)
+#pragma unroll
+        for (int i = 0; i < SLICE_COLS / 32; ++i) tile[ty + rg * (THREADS / 32)][tx + 32 * i] = x[rg][i];
     }
     __syncthreads();
     // each thread: one row, two adjacent columns -> one uint32 per slice
@@ -273,7 +320,8 @@ __global__ void __launch_bounds__(THREADS) slice_kernel(Problem p, OperandMap m,
 
 // TF32 form: aligned float32 operand rounded to TF32 (round to nearest even
 // on the 10-bit mantissa), zero padded to kpad columns.
-__global__ void __launch_bounds__(THREADS) tf32_kernel(Problem p, OperandMap m, int64_t R,
+__global__ void __launch_bounds__(THREADS) tf32_kernel(Problem p, const int64_t* __restrict__ rtab,
+                                                       const int64_t* __restrict__ ctab, int64_t R,
                                                        int64_t Cn, int64_t kpad, bool fast_rows,
                                                        const double* __restrict__ src,
                                                        float* __restrict__ dst) {
@@ -286,14 +334,13 @@ __global__ void __launch_bounds__(THREADS) tf32_kernel(Problem p, OperandMap m, 
     int64_t b = tI / (rt * ct);
     int64_t rem = tI - b * rt * ct;
     int64_t r0 = (rem / ct) * TILE, c0 = (rem % ct) * TILE;
-    int Q = batch_irrep(p, (int)b);
     __syncthreads();
     if (threadIdx.x < TILE) {
       int64_t r = r0 + threadIdx.x;
-      roff[threadIdx.x] = r < R ? axis_offset(m.rows, p.g, Q, r) : 0;
+      roff[threadIdx.x] = r < R ? rtab[b * R + r] : 0;
     } else if (threadIdx.x < 2 * TILE) {
       int64_t c = c0 + threadIdx.x - TILE;
-      coff[threadIdx.x - TILE] = c < Cn ? axis_offset(m.cols, p.g, Q, c) : 0;
+      coff[threadIdx.x - TILE] = c < Cn ? ctab[b * Cn + c] : 0;
     }
     __syncthreads();
     for (int k = ty; k < TILE; k += THREADS / 32) {
@@ -355,31 +402,43 @@ cudaError_t launch_align_f64(const Problem& p, int operand, int direction, const
   return cudaGetLastError();
 }
 
-cudaError_t launch_split_operand(const Problem& p, int operand, int n_slices, const double* src,
-                                 uint16_t* slices, int64_t kpad, int32_t* exps, unsigned* err,
-                                 cudaStream_t st) {
+cudaError_t launch_tables(const Problem& p, const Tables& t, cudaStream_t st) {
+  int64_t total = tables_entries(p);
+  if (total == 0) return cudaSuccess;
+  tables_kernel<<<grid_for((total + THREADS - 1) / THREADS), THREADS, 0, st>>>(p, t);
+  ++g_kernel_launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_operand(const Problem& p, const Tables& t, int operand, int n_slices,
+                                 const double* src, uint16_t* slices, int64_t kpad, int32_t* exps,
+                                 unsigned* err, cudaStream_t st) {
   int64_t R, Cn;
   operand_extent(p, operand, &R, &Cn);
   const OperandMap& m = operand_map(p, operand);
+  const int64_t* rt = operand == 0 ? t.urow : t.vrow;
+  const int64_t* ct = operand == 0 ? t.ucol : t.vcol;
   cudaError_t e = cudaMemsetAsync(exps, 0, sizeof(int32_t) * R * p.n_q, st);
   if (e != cudaSuccess) return e;
   int64_t t1 = ((R + TILE - 1) / TILE) * ((Cn + SCAN_COLS - 1) / SCAN_COLS) * p.n_q;
-  exp_scan_kernel<<<grid_for(t1), THREADS, 0, st>>>(p, m, R, Cn, rows_fast(m), src, exps, err);
+  exp_scan_kernel<<<grid_for(t1), THREADS, 0, st>>>(p, rt, ct, R, Cn, rows_fast(m), src, exps, err);
   ++g_kernel_launches;
   int64_t t2 = ((R + TILE - 1) / TILE) * ((kpad + SLICE_COLS - 1) / SLICE_COLS) * p.n_q;
-  slice_kernel<<<grid_for(t2), THREADS, 0, st>>>(p, m, R, Cn, kpad, rows_fast(m), n_slices, src,
+  slice_kernel<<<grid_for(t2), THREADS, 0, st>>>(p, rt, ct, R, Cn, kpad, rows_fast(m), n_slices, src,
                                                   exps, (uint32_t*)slices);
   ++g_kernel_launches;
   return cudaGetLastError();
 }
 
-cudaError_t launch_tf32_operand(const Problem& p, int operand, const double* src, float* dst,
-                                int64_t kpad, cudaStream_t st) {
+cudaError_t launch_tf32_operand(const Problem& p, const Tables& t, int operand, const double* src,
+                                float* dst, int64_t kpad, cudaStream_t st) {
   int64_t R, Cn;
   operand_extent(p, operand, &R, &Cn);
   const OperandMap& m = operand_map(p, operand);
+  const int64_t* rt = operand == 0 ? t.urow : t.vrow;
+  const int64_t* ct = operand == 0 ? t.ucol : t.vcol;
   int64_t tiles = ((R + TILE - 1) / TILE) * ((kpad + TILE - 1) / TILE) * p.n_q;
-  tf32_kernel<<<grid_for(tiles), THREADS, 0, st>>>(p, m, R, Cn, kpad, rows_fast(m), src, dst);
+  tf32_kernel<<<grid_for(tiles), THREADS, 0, st>>>(p, rt, ct, R, Cn, kpad, rows_fast(m), src, dst);
   ++g_kernel_launches;
   return cudaGetLastError();
 }
