@@ -151,6 +151,20 @@ SYMCTR_API symctr_status symctr_contract(const symctr_plan* plan, const double* 
                               double* w_red, void* workspace, size_t workspace_bytes,
                               void* stream);
 
+/* symctr_contract without a caller-provided workspace, for callers that cannot
+ * allocate device memory (they are handed only their input and output buffers,
+ * or run where no allocator may be called).  The paper has no counterpart: this
+ * is a deployment convenience.  The scratch is one static device array of
+ * 64 MiB that every GPU loading this code holds until exit; plans whose
+ * workspace_bytes exceed it get SYMCTR_ERR_WORKSPACE.  All calls share that
+ * array: calls that overlap on the GPU race (use one stream).  The first call on
+ * a device looks up the array's address (cudaGetSymbolAddress, device current)
+ * and should come before any stream capture.  Device-side failures are recorded
+ * in the array and not reported; no memory is allocated or freed. */
+SYMCTR_API symctr_status symctr_contract_static_scratch(const symctr_plan* plan,
+                                                        const double* u_red, const double* v_red,
+                                                        double* w_red, void* stream);
+
 /* Gradients of a scalar loss L through W = einsum(U, V), given gW = dL/dW:
  *   gU = einsum(w_labels, v_labels -> u_labels)(gW, V)   (written if grad_u_red != NULL)
  *   gV = einsum(u_labels, w_labels -> v_labels)(U, gW)   (written if grad_v_red != NULL)

@@ -99,11 +99,12 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.symctr_profile_read.argtypes = [P, ctypes.POINTER(ctypes.c_float),
                                         ctypes.POINTER(ctypes.c_float),
                                         ctypes.POINTER(ctypes.c_int)]
+    lib.symctr_contract_static_scratch.argtypes = [P, P, P, P, P]
     lib.symctr_plan_destroy.argtypes = [P]
     lib.symctr_plan_destroy.restype = None
     for f in ("symctr_plan_create", "symctr_plan_query", "symctr_align", "symctr_contract",
               "symctr_contract_backward", "symctr_check_device_error", "symctr_profile_enable",
-              "symctr_profile_read"):
+              "symctr_profile_read", "symctr_contract_static_scratch"):
         getattr(lib, f).restype = ctypes.c_int
     _LIB = lib
     return lib
@@ -218,6 +219,22 @@ class Plan:
         ws = workspace if workspace is not None else self.workspace(device=u.device)
         _check(load().symctr_contract(self._h, _ptr(u), _ptr(v), _ptr(out), _ptr(ws),
                                       ws.numel(), _stream()))
+        return out
+
+    def contract_static_scratch(self, u: torch.Tensor, v: torch.Tensor,
+                                out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """contract() for callers that cannot allocate device scratch: the library
+        uses its own static 64 MiB device array instead of a workspace.  Calls
+        share that array, so they must not overlap on the GPU (use one stream).
+        `out` must be preallocated by such callers (this convenience wrapper
+        allocates it with torch only when it is omitted)."""
+        self._dev64(u, self.shape_u, "u")
+        self._dev64(v, self.shape_v, "v")
+        if out is None:
+            out = torch.empty(self.shape_w, dtype=torch.float64, device=u.device)
+        self._dev64(out, self.shape_w, "out")
+        _check(load().symctr_contract_static_scratch(self._h, _ptr(u), _ptr(v), _ptr(out),
+                                                     _stream()))
         return out
 
     def backward(self, grad_w: torch.Tensor, u: torch.Tensor, v: torch.Tensor,

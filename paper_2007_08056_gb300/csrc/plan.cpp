@@ -487,6 +487,20 @@ symctr_status run_contract_body(const symctr_plan* P, const double* u, const dou
 
 }  // namespace
 
+namespace symctr {
+
+symctr_status contract_into_workspace(const symctr_plan* P, const double* u, const double* v,
+                                      double* w, void* ws, size_t ws_bytes, cudaStream_t st) {
+  if (!P) return fail(SYMCTR_ERR_NULLPTR, "NULL plan");
+  return run_contract(P, u, v, w, ws, ws_bytes, st);
+}
+
+uint64_t plan_workspace_bytes(const symctr_plan* P) { return P ? P->ws_bytes : 0; }
+
+symctr_status record_error(symctr_status st, const char* detail) { return fail(st, detail); }
+
+}  // namespace symctr
+
 extern "C" {
 
 symctr_status symctr_plan_create(const char* einsum, int n_moduli, const int32_t* moduli,

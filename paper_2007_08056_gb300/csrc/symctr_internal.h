@@ -172,6 +172,13 @@ inline int split_k_ranges(const Problem& p, int64_t kpad) {
   return (int)((chunks + per - 1) / per);
 }
 
+// The contraction of symctr_contract on a given workspace, the plan's workspace
+// size, and the error-detail recorder (defined in plan.cpp).
+symctr_status contract_into_workspace(const symctr_plan* P, const double* u, const double* v,
+                                      double* w, void* ws, size_t ws_bytes, cudaStream_t st);
+uint64_t plan_workspace_bytes(const symctr_plan* P);
+symctr_status record_error(symctr_status st, const char* detail);
+
 // Shape test: the tensor-core forms need a GEMM-shaped problem.
 inline bool tensor_core_shape(const Problem& p) { return p.M >= 32 && p.N >= 32 && p.K >= 16; }
 
