@@ -109,8 +109,10 @@ typedef struct {
   int64_t aligned_numel_w;      /* n_q * M * N */
   double useful_flops;          /* 2 * n_q * M * N * K: symmetry-reduced GEMM flops */
   double transform_bytes;       /* algorithmic bytes of the alignment transforms */
-  uint64_t workspace_bytes;     /* device workspace symctr_contract needs */
+  uint64_t workspace_bytes;     /* device workspace for one pass over all irreps Q */
   uint64_t workspace_bytes_backward; /* device workspace symctr_contract_backward needs */
+  uint64_t workspace_bytes_min; /* smallest accepted workspace: the contraction then runs
+                                   one pass per group of irreps that fits (Q-streaming) */
 } symctr_plan_info;
 
 /* Build a plan for W = einsum(spec, U, V).
@@ -145,8 +147,10 @@ SYMCTR_API symctr_status symctr_align(const symctr_plan* plan, int operand, int 
                            const double* src, double* dst, void* stream);
 
 /* W = einsum(U, V) in the plan's precision form, from and to standard reduced forms.
- *  workspace : device scratch of at least workspace_bytes (256-byte aligned); its first
- *              word receives device-side error codes. */
+ *  workspace : device scratch (256-byte aligned) of at least workspace_bytes_min bytes;
+ *              with less than workspace_bytes the irreps Q are processed in several
+ *              passes, each holding the aligned operands of as many irreps as fit.  Its
+ *              first word receives device-side error codes. */
 SYMCTR_API symctr_status symctr_contract(const symctr_plan* plan, const double* u_red, const double* v_red,
                               double* w_red, void* workspace, size_t workspace_bytes,
                               void* stream);

@@ -70,7 +70,7 @@ import numpy as np
 __all__ = [
     "Group", "Sym", "Plan", "parse_einsum", "plan", "reduced_shape",
     "expand", "restrict", "contract_dense_einsum", "contract_dense_loops",
-    "contract_blockloop", "contract_element", "align_u", "align_v",
+    "contract_blockloop", "contract_element", "contract_element_lazy", "align_u", "align_v",
     "mapback_w", "align_w", "q_set", "contract_aligned", "delta", "grad_u", "grad_v",
     "central_difference", "count_stored_blocks", "aligned_dims",
 ]
@@ -408,6 +408,45 @@ def contract_element(p: Plan, u_red, v_red, w_index: Tuple[int, ...]) -> float:
         us, vs = ub[ui], vb[vi]
         cu = [c for c in p.lu if c in p.C]
         cv = [c for c in p.lv if c in p.C]
+        vs = np.transpose(vs, [cv.index(c) for c in cu]) if cv else vs
+        total += float(np.sum(us * vs))
+    return total
+
+
+def contract_element_lazy(p: Plan, u_get, v_get, w_index: Tuple[int, ...]) -> float:
+    """contract_element for operands too large to hold on the host: the same
+    sum (Eq. ctr, over every allowed contracted sector tuple and contracted
+    block index), with the operands read through callbacks.
+    u_get(index) / v_get(index) return the reduced-form sub-array at `index`,
+    a tuple of ints and full slices in the reduced form's axis order."""
+    G = p.group
+    lw = p.lw
+    nw = len(lw)
+    wsig = dict(zip(lw, p.sym_w.signs))
+    usig = dict(zip(p.lu, p.sym_u.signs))
+    vsig = dict(zip(p.lv, p.sym_v.signs))
+    if nw == 0:
+        if not G.conserves((), (), p.sym_w.charge):
+            return 0.0
+        sec, blk = {}, {}
+    else:
+        sec = dict(zip(lw[:-1], w_index[:nw - 1]))
+        blk = dict(zip(lw, w_index[nw - 1:]))
+        sec[lw[-1]] = G.solve(wsig[lw[-1]], [wsig[c] for c in lw[:-1]],
+                              [sec[c] for c in lw[:-1]], p.sym_w.charge)
+    cu = [c for c in p.lu if c in p.C]
+    cv = [c for c in p.lv if c in p.C]
+    total = 0.0
+    for qc in itertools.product(range(G.order), repeat=len(p.C)):
+        sec.update(zip(p.C, qc))
+        if not G.conserves([usig[c] for c in p.lu], [sec[c] for c in p.lu], p.sym_u.charge):
+            continue
+        if not G.conserves([vsig[c] for c in p.lv], [sec[c] for c in p.lv], p.sym_v.charge):
+            continue
+        ui = _red_index(sec, p.lu) + tuple(blk[c] if c in blk else slice(None) for c in p.lu)
+        vi = _red_index(sec, p.lv) + tuple(blk[c] if c in blk else slice(None) for c in p.lv)
+        us = np.asarray(u_get(ui), dtype=np.float64)
+        vs = np.asarray(v_get(vi), dtype=np.float64)
         vs = np.transpose(vs, [cv.index(c) for c in cu]) if cv else vs
         total += float(np.sum(us * vs))
     return total

@@ -60,6 +60,7 @@ class PlanInfo(ctypes.Structure):
         ("aligned_numel_w", ctypes.c_int64),
         ("useful_flops", ctypes.c_double), ("transform_bytes", ctypes.c_double),
         ("workspace_bytes", ctypes.c_uint64), ("workspace_bytes_backward", ctypes.c_uint64),
+        ("workspace_bytes_min", ctypes.c_uint64),
     ]
 
 

@@ -49,6 +49,12 @@ constexpr int TILE_BYTES = TM * ROW_BYTES;     // 8 KB per operand tile per stag
 constexpr int NTHREADS = 384;
 constexpr int EPI_WARP0 = 4;
 constexpr int kExpBias = 4096;     // row exponents are stored biased (0 = all-zero row)
+// Every kFoldChunks exact drains, the rounded accumulator of diagonals >= 3 is
+// folded as well: its part in units of 2^-16 moves into the int32 running sum
+// of diagonal 2 and only the remainder (|r| <= 2^-17) stays in TMEM, so the
+// tensor core keeps accumulating into a small value.  This bounds the drift of
+// its FP32 accumulation over long K.
+constexpr int kFoldChunks = 16;
 constexpr long long kTimeoutCycles = 4000000000ll;  // ~2 s per wait at 2 GHz
 
 enum Mode { MODE_SPLIT = 0, MODE_TF32 = 1 };
@@ -82,6 +88,7 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
 
 struct Ctl {
   volatile int abort;
+  int last;          // this CTA finalizes its tile (split-K)
   unsigned* err;
 };
 
@@ -177,6 +184,14 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
         "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
 }
+__device__ __forceinline__ void tmem_st4(uint32_t taddr, const uint32_t* r) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr),
+               "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3])
+               : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
 __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
@@ -200,8 +215,8 @@ __host__ __device__ constexpr uint32_t idesc() {
 }
 
 // RN(R * 2^e) as float64 using integer operations only (ties to even).
-__device__ __forceinline__ double i64_scaled(long long Rv, int e) {
-  if (Rv == 0) return 0.0;
+// Fast path: |R| < 2^53 and a normal result need no rounding, only a shift.
+__device__ __forceinline__ double i64_scaled_slow(long long Rv, int e) {
   uint64_t sgn = Rv < 0 ? (1ull << 63) : 0ull;
   uint64_t m = Rv < 0 ? (uint64_t)(-Rv) : (uint64_t)Rv;
   int nb = 64 - __clzll((long long)m);
@@ -238,6 +253,21 @@ __device__ __forceinline__ double i64_scaled(long long Rv, int e) {
     q = m << (-shift);
   }
   return __longlong_as_double((long long)(sgn | ((uint64_t)be << 52) | (q & ((1ull << 52) - 1))));
+}
+
+__device__ __forceinline__ double i64_scaled(long long Rv, int e) {
+  if (Rv == 0) return 0.0;
+  const uint64_t m = Rv < 0 ? (uint64_t)(-Rv) : (uint64_t)Rv;
+  if (m < (1ull << 53)) {
+    const int nb = 64 - __clzll((long long)m);
+    const int be = e + nb - 1 + 1023;
+    if (be > 0 && be < 2047) {
+      const uint64_t q = m << (53 - nb);
+      const uint64_t sgn = Rv < 0 ? (1ull << 63) : 0ull;
+      return __longlong_as_double((long long)(sgn | ((uint64_t)be << 52) | (q & ((1ull << 52) - 1))));
+    }
+  }
+  return i64_scaled_slow(Rv, e);
 }
 
 // Exact float32 -> float64 with integer operations.
@@ -340,7 +370,8 @@ struct TcArgs {
   unsigned* err;
   int ksplit;        // K ranges (grid.z = n_q * ksplit)
   int kb_per_split;  // stages per K range (a multiple of 2)
-  unsigned long long* wacc;  // [n_q][M][N] int64 partial sums when ksplit > 1
+  unsigned long long* wacc;  // [n_q][M][N] int64 partial sums when ksplit > 1 (zeroed)
+  unsigned* tile_ctr;        // [n_q][gy][gx] K ranges finished per tile (zeroed)
   const int64_t* wrow;       // [n_q][M] offsets of W's rows in its reduced form
   const int64_t* wcol;       // [n_q][N] offsets of W's columns
 };
@@ -371,7 +402,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   uint64_t* top_empty = top_full + 1;
   uint64_t* acc_full = top_empty + 1;
   uint64_t* drain = acc_full + 1;
-  int64_t* coff = (int64_t*)(drain + 1);       // [TN] W column offsets
+  uint64_t* low_full = drain + 1;
+  uint64_t* low_empty = low_full + 1;
+  int64_t* coff = (int64_t*)(low_empty + 1);   // [TN] W column offsets
   int32_t* cexp = (int32_t*)(coff + TN);        // [TN] column exponents
   int64_t* roffs = (int64_t*)(cexp + TN);        // [TM] W row offsets
   int32_t* rexps = (int32_t*)(roffs + TM);       // [TM] row exponents
@@ -398,6 +431,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     mbar_init(top_empty, 8);
     mbar_init(acc_full, 1);
     mbar_init(drain, 1);
+    mbar_init(low_full, 1);
+    mbar_init(low_empty, 8);
     ctl->abort = 0;
     ctl->err = args.err;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -408,6 +443,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
+  // Launched as a programmatic dependent of the operand preparation: the setup
+  // above overlaps its tail; everything below reads its outputs.
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   if (threadIdx.x >= EPI_WARP0 * 32 && threadIdx.x < EPI_WARP0 * 32 + TN) {
     int c = threadIdx.x - EPI_WARP0 * 32;
     int64_t n = n0 + c;
@@ -464,8 +502,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const int chunk = KIND == MODE_TF32 ? 0 : kb / 2;
         const bool final_chunk = chunk == n_chunks - 1;
         bool ok = true;
+        // fold of accumulator 3 after chunk c: (c + 1) % kFoldChunks == 0, not the last chunk
+        constexpr bool has_low = KIND == MODE_SPLIT && S >= 4;
         if (cfirst) {
-          issue_low<KIND, S>(tmem, da, db, id, kb == 0);
+          if (has_low && chunk > 0 && chunk % kFoldChunks == 0) {
+            ok = wait_phase(low_empty, (uint32_t)(chunk / kFoldChunks - 1) & 1, ctl);
+            tc_fence_after();
+          }
+          if (ok) issue_low<KIND, S>(tmem, da, db, id, kb == 0);
           if (chunk > 0) {
             ok = wait_phase(top_empty, (chunk - 1) & 1, ctl);
             tc_fence_after();
@@ -475,6 +519,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           issue_top<KIND, S>(tmem, da, db, id, false);
           if (!final_chunk) tc_commit(top_full);
           issue_low<KIND, S>(tmem, da, db, id, false);
+          if (has_low && !final_chunk && (chunk + 1) % kFoldChunks == 0) tc_commit(low_full);
         }
         tc_commit(&empty[st]);
         if (!ok) break;
@@ -532,6 +577,32 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(top_empty);
+        if (live3 && (c + 1) % kFoldChunks == 0) {
+          if (!wait_phase_sleep(low_full, (uint32_t)(c / kFoldChunks) & 1, ctl)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+#pragma unroll
+          for (int pc = 0; pc < 16; ++pc) {
+            uint32_t a3[4];
+            tmem_ld4(lane_base + 384 + pc * 4, a3);
+            tmem_wait_ld();
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const float x = __uint_as_float(a3[j]);
+              const float r = __fmaf_rn(x, 65536.0f, M0);        // round(x * 2^16) + 1.5*2^23
+              s2[pc * 4 + j] += (int32_t)__float_as_uint(r) - B0;
+              const float back = (r - M0) * (1.0f / 65536.0f);   // exact
+              a3[j] = __float_as_uint(x - back);                 // exact remainder
+            }
+            tmem_st4(lane_base + 384 + pc * 4, a3);
+          }
+          tmem_wait_st();
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(low_empty);
+        }
       }
     }
     if (ok) ok = wait_phase_sleep(acc_full, 0, ctl);
@@ -575,9 +646,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     tc_fence_before();
     // all 256 epilogue threads meet here, whatever path they took
     asm volatile("bar.sync 1, 256;" ::: "memory");
+    const int t = threadIdx.x - EPI_WARP0 * 32;
     if (ok) {
       // coalesced: consecutive lanes take consecutive columns of one row
-      const int t = threadIdx.x - EPI_WARP0 * 32;
+#pragma unroll 4
       for (int idx = t; idx < TM * TN; idx += 256) {
         const int r = idx / TN, c = idx % TN;
         if (m0 + r >= p.M || n0 + c >= p.N) continue;
@@ -592,31 +664,32 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
       }
     }
+    if (KIND == MODE_SPLIT && args.ksplit > 1) {
+      // the CTA that completes a tile's last K range rounds the summed partials
+      __threadfence();
+      asm volatile("bar.sync 1, 256;" ::: "memory");
+      if (t == 0) {
+        const unsigned tile_id = ((unsigned)b * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+        ctl->last = ok && atomicAdd(args.tile_ctr + tile_id, 1u) == (unsigned)args.ksplit - 1;
+      }
+      asm volatile("bar.sync 1, 256;" ::: "memory");
+      if (ctl->last) {
+        __threadfence();
+        for (int idx = t; idx < TM * TN; idx += 256) {
+          const int r = idx / TN, c = idx % TN;
+          if (m0 + r >= p.M || n0 + c >= p.N) continue;
+          const long long Rv =
+              (long long)__ldcg(args.wacc + ((int64_t)b * p.M + m0 + r) * p.N + n0 + c);
+          args.w[roffs[r] + coff[c]] = i64_scaled(Rv, rexps[r] + cexp[c] - 36);
+        }
+      }
+    }
   }
   __syncthreads();
   if (warp == 1) {
     __syncwarp();
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
-  }
-}
-
-// Split-K finalize: round the summed int64 partials once and map them back.
-__global__ void __launch_bounds__(256) split_finalize_kernel(Problem p,
-                                                             const unsigned long long* __restrict__ wacc,
-                                                             const int32_t* __restrict__ eu,
-                                                             const int32_t* __restrict__ ev,
-                                                             const int64_t* __restrict__ wrow,
-                                                             const int64_t* __restrict__ wcol,
-                                                             double* __restrict__ w) {
-  const int64_t total = (int64_t)p.n_q * p.M * p.N;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    int64_t b = i / (p.M * p.N);
-    int64_t r = i - b * p.M * p.N;
-    int64_t m = r / p.N, n = r % p.N;
-    int e = (eu[b * p.M + m] - kExpBias) + (ev[b * p.N + n] - kExpBias) - 36;
-    w[wrow[b * p.M + m] + wcol[b * p.N + n]] = i64_scaled((long long)wacc[i], e);
   }
 }
 
@@ -659,7 +732,7 @@ bool make_map(CUtensorMap* map, const void* base, bool is_f32, int64_t kpad, int
 template <int KIND, int S, int STAGES>
 cudaError_t launch_tc(const Problem& p, const Tables& tab, const void* a, const void* bop, const int32_t* eu,
                       const int32_t* ev, int64_t kpad, double* w, unsigned* err, int ksplit,
-                      unsigned long long* wacc, cudaStream_t st) {
+                      unsigned long long* wacc, unsigned* tile_ctr, cudaStream_t st) {
   const bool f32 = KIND == MODE_TF32;
   CUtensorMap ma, mb;
   if (!make_map(&ma, a, f32, kpad, p.M, (int64_t)S * p.n_q) ||
@@ -679,31 +752,37 @@ cudaError_t launch_tc(const Problem& p, const Tables& tab, const void* a, const 
   if (args.kb_per_split < 2) args.kb_per_split = 2;
   args.ksplit = (args.n_kb + args.kb_per_split - 1) / args.kb_per_split;
   args.wacc = wacc;
+  args.tile_ctr = tile_ctr;
   args.wrow = tab.wrow;
   args.wcol = tab.wcol;
-  if (args.ksplit > 1) {
-    cudaError_t e0 = cudaMemsetAsync(wacc, 0, sizeof(unsigned long long) * p.n_q * p.M * p.N, st);
-    if (e0 != cudaSuccess) return e0;
-  }
-  size_t smem = 1024 + tile_region_bytes<S, STAGES>() + 8 * (2 * STAGES + 4) + 8 * TN + 4 * TN +
+  size_t smem = 1024 + tile_region_bytes<S, STAGES>() + 8 * (2 * STAGES + 6) + 8 * TN + 4 * TN +
                 8 * TM + 4 * TM + 16 + 64;
   auto kern = gemm_tc_kernel<KIND, S, STAGES>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
+  static bool attr_set[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+  if (!attr_set[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set[dev] = true;
+  }
   int64_t gx = (p.N + TN - 1) / TN, gy = (p.M + TM - 1) / TM;
   if (gx > 0x7FFFFFFF || gy > 65535 || (int64_t)p.n_q * args.ksplit > 65535)
     return cudaErrorInvalidConfiguration;
   dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)(p.n_q * args.ksplit));
-  kern<<<grid, NTHREADS, smem, st>>>(ma, mb, args);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(NTHREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t le = cudaLaunchKernelEx(&cfg, kern, ma, mb, args);
   ++g_kernel_launches;
-  if (args.ksplit > 1) {
-    int64_t total = (int64_t)p.n_q * p.M * p.N;
-    int64_t blocks = (total + 255) / 256;
-    split_finalize_kernel<<<(int)(blocks < 4096 ? blocks : 4096), 256, 0, st>>>(p, wacc, eu, ev, tab.wrow,
-                                                                                 tab.wcol, w);
-    ++g_kernel_launches;
-  }
-  return cudaGetLastError();
+  return le;
 }
 
 }  // namespace
@@ -711,20 +790,21 @@ cudaError_t launch_tc(const Problem& p, const Tables& tab, const void* a, const 
 cudaError_t launch_gemm_split(const Problem& p, const Tables& tab, int n_slices, const uint16_t* us,
                               const uint16_t* vs, const int32_t* eu, const int32_t* ev,
                               int64_t kpad, double* w, unsigned* err, int ksplit,
-                              unsigned long long* wacc, cudaStream_t st) {
+                              unsigned long long* wacc, unsigned* tile_ctr, cudaStream_t st) {
   switch (n_slices) {
-    case 2: return launch_tc<MODE_SPLIT, 2, 2>(p, tab, us, vs, eu, ev, kpad, w, err, ksplit, wacc, st);
-    case 3: return launch_tc<MODE_SPLIT, 3, 2>(p, tab, us, vs, eu, ev, kpad, w, err, ksplit, wacc, st);
-    case 4: return launch_tc<MODE_SPLIT, 4, 2>(p, tab, us, vs, eu, ev, kpad, w, err, ksplit, wacc, st);
-    case 5: return launch_tc<MODE_SPLIT, 5, 2>(p, tab, us, vs, eu, ev, kpad, w, err, ksplit, wacc, st);
-    case 6: return launch_tc<MODE_SPLIT, 6, 2>(p, tab, us, vs, eu, ev, kpad, w, err, ksplit, wacc, st);
+    case 2: return launch_tc<MODE_SPLIT, 2, 2>(p, tab, us, vs, eu, ev, kpad, w, err, ksplit, wacc, tile_ctr, st);
+    case 3: return launch_tc<MODE_SPLIT, 3, 2>(p, tab, us, vs, eu, ev, kpad, w, err, ksplit, wacc, tile_ctr, st);
+    case 4: return launch_tc<MODE_SPLIT, 4, 2>(p, tab, us, vs, eu, ev, kpad, w, err, ksplit, wacc, tile_ctr, st);
+    case 5: return launch_tc<MODE_SPLIT, 5, 2>(p, tab, us, vs, eu, ev, kpad, w, err, ksplit, wacc, tile_ctr, st);
+    case 6: return launch_tc<MODE_SPLIT, 6, 2>(p, tab, us, vs, eu, ev, kpad, w, err, ksplit, wacc, tile_ctr, st);
   }
   return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_gemm_tf32(const Problem& p, const Tables& tab, const float* u, const float* v,
                              int64_t kpad, double* w, unsigned* err, cudaStream_t st) {
-  return launch_tc<MODE_TF32, 1, 6>(p, tab, u, v, nullptr, nullptr, kpad, w, err, 1, nullptr, st);
+  return launch_tc<MODE_TF32, 1, 6>(p, tab, u, v, nullptr, nullptr, kpad, w, err, 1, nullptr, nullptr,
+                                    st);
 }
 
 }  // namespace symctr

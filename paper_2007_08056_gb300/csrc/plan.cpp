@@ -43,6 +43,52 @@ bool mul_ok(int64_t a, int64_t b, int64_t* out) {
 
 int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
+// Byte offsets of one pass's workspace regions (a pass covers n_q irreps).
+struct Layout {
+  uint64_t off_tab = 0, off_a = 0, off_b = 0, off_ea = 0, off_eb = 0, off_acc = 0, off_ctr = 0;
+  uint64_t bytes = 256;
+  int ksplit = 1;
+  int64_t n_tiles = 0;
+  bool ok = true;
+};
+
+Layout make_layout(const Problem& pr, bool tensor_core, symctr_precision prec, int n_slices,
+                   int64_t kpad) {
+  Layout L;
+  uint64_t off = 256;
+  auto region = [&](int64_t bytes) {
+    uint64_t at = off;
+    off += (uint64_t)round_up(bytes, 256);
+    return at;
+  };
+  if (tensor_core) {
+    const int64_t nq = pr.n_q;
+    L.off_tab = region(tables_entries(pr) * 8);
+    int64_t ra = 0, rb = 0;
+    if (!mul_ok(nq * pr.M, kpad, &ra) || !mul_ok(nq * pr.N, kpad, &rb)) {
+      L.ok = false;
+      return L;
+    }
+    if (prec == SYMCTR_SPLIT_BF16) {
+      L.off_a = region(ra * 2 * n_slices);
+      L.off_b = region(rb * 2 * n_slices);
+      L.off_ea = region(nq * pr.M * 4);
+      L.off_eb = region(nq * pr.N * 4);
+      L.ksplit = split_k_ranges(pr, kpad);
+      L.n_tiles = ((pr.M + 127) / 128) * ((pr.N + 127) / 128) * nq;
+      if (L.ksplit > 1) {
+        L.off_acc = region(nq * pr.M * pr.N * 8);
+        L.off_ctr = region(L.n_tiles * 4);
+      }
+    } else {
+      L.off_a = region(ra * 4);
+      L.off_b = region(rb * 4);
+    }
+  }
+  L.bytes = off;
+  return L;
+}
+
 struct Tensor {
   std::string labels;
   int sign[SYMCTR_MAX_ORDER];
@@ -89,9 +135,8 @@ struct symctr_plan {
   symctr_precision prec = SYMCTR_FP64;
   int n_slices = 0;
   int64_t kpad = 0;
-  // workspace layout (byte offsets)
-  uint64_t ws_bytes = 256, off_a = 0, off_b = 0, off_ea = 0, off_eb = 0, off_acc = 0, off_tab = 0;
-  int ksplit = 1;
+  // workspace: all irreps in one pass, or the smallest pass (one irrep)
+  uint64_t ws_bytes = 256, ws_bytes_min = 256;
   bool tensor_core = false;
   symctr_plan* bwd_u = nullptr;
   symctr_plan* bwd_v = nullptr;
@@ -353,30 +398,18 @@ symctr_status build(const char* einsum, int n_moduli, const int32_t* moduli, con
   if (prec == SYMCTR_SPLIT_BF16 && P->n_slices < 2)
     return bail(SYMCTR_ERR_ARGUMENT, "split form needs at least 2 slices");
   P->kpad = round_up(pr.K, kKBlock);
-  uint64_t off = 256;
-  auto region = [&](int64_t bytes) {
-    uint64_t at = off;
-    off += (uint64_t)round_up(bytes, 256);
-    return at;
-  };
-  if (P->tensor_core) {
-    P->off_tab = region(tables_entries(pr) * 8);
-    int64_t ra = 0, rb = 0;
-    if (!mul_ok((int64_t)nq * pr.M, P->kpad, &ra) || !mul_ok((int64_t)nq * pr.N, P->kpad, &rb))
-      return bail(SYMCTR_ERR_OVERFLOW, "aligned operand too large");
-    if (prec == SYMCTR_SPLIT_BF16) {
-      P->off_a = region(ra * 2 * P->n_slices);
-      P->off_b = region(rb * 2 * P->n_slices);
-      P->off_ea = region((int64_t)nq * pr.M * 4);
-      P->off_eb = region((int64_t)nq * pr.N * 4);
-      P->ksplit = split_k_ranges(pr, P->kpad);
-      if (P->ksplit > 1) P->off_acc = region((int64_t)nq * pr.M * pr.N * 8);
-    } else {
-      P->off_a = region(ra * 4);
-      P->off_b = region(rb * 4);
+  pr.q_base = 0;
+  {
+    Layout full = make_layout(pr, P->tensor_core, prec, P->n_slices, P->kpad);
+    if (!full.ok) return bail(SYMCTR_ERR_OVERFLOW, "aligned operand too large");
+    P->ws_bytes = full.bytes;
+    P->ws_bytes_min = full.bytes;
+    if (P->tensor_core && pr.q_single < 0 && pr.n_q > 1) {
+      Problem one = pr;
+      one.n_q = 1;
+      P->ws_bytes_min = make_layout(one, true, prec, P->n_slices, P->kpad).bytes;
     }
   }
-  P->ws_bytes = off;
 
   if (with_backward) {
     // gU = einsum(lw,lv->lu)(gW, V): result carries U's law.
@@ -427,12 +460,13 @@ symctr_status run_contract_body(const symctr_plan* P, const double* u, const dou
   const Problem& pr = P->prob;
   if (!w || (!u && P->numel_u) || (!v && P->numel_v))
     return fail(SYMCTR_ERR_NULLPTR, "NULL tensor pointer");
-  if (!ws || ws_bytes < P->ws_bytes)
-    return fail(SYMCTR_ERR_WORKSPACE, "workspace smaller than workspace_bytes");
+  if (!ws || ws_bytes < P->ws_bytes_min)
+    return fail(SYMCTR_ERR_WORKSPACE, "workspace smaller than workspace_bytes_min");
   char* base = (char*)ws;
   unsigned* err = (unsigned*)base;
-  cudaError_t e = cudaMemsetAsync(err, 0, sizeof(unsigned), st);
-  if (e != cudaSuccess) return cuda_status(e, "clear error word");
+  // header: error word (byte 0) and the prep kernel's grid-barrier counter (byte 64)
+  cudaError_t e = cudaMemsetAsync(err, 0, 128, st);
+  if (e != cudaSuccess) return cuda_status(e, "clear workspace header");
   // Entries of W whose irrep Q carries no work are zero.
   if ((int64_t)pr.n_q * pr.M * pr.N < P->numel_w) {
     e = launch_fill_zero(w, P->numel_w, st);
@@ -446,43 +480,59 @@ symctr_status run_contract_body(const symctr_plan* P, const double* u, const dou
     if (P->prof) cudaEventRecord(P->ev[2], st);
     return cuda_status(e, "gemm_f64");
   }
-  Tables tab;
-  {
-    int64_t* t0 = (int64_t*)(base + P->off_tab);
+  // Q-streaming: as many irreps per pass as the workspace holds.
+  int per_pass = pr.n_q;
+  if (ws_bytes < P->ws_bytes) {
+    per_pass = 0;
+    for (int c = pr.n_q - 1; c >= 1 && per_pass == 0; --c) {
+      Problem pc = pr;
+      pc.n_q = c;
+      if (make_layout(pc, true, P->prec, P->n_slices, P->kpad).bytes <= ws_bytes) per_pass = c;
+    }
+    if (per_pass == 0) return fail(SYMCTR_ERR_WORKSPACE, "workspace smaller than workspace_bytes_min");
+  }
+  unsigned* barrier = (unsigned*)(base + 64);
+  const bool split = P->prec == SYMCTR_SPLIT_BF16;
+  for (int q0 = 0; q0 < pr.n_q; q0 += per_pass) {
+    Problem pc = pr;
+    if (per_pass < pr.n_q) {
+      pc.n_q = per_pass < pr.n_q - q0 ? per_pass : pr.n_q - q0;
+      pc.q_base = q0;
+      if (q0 > 0) {
+        e = cudaMemsetAsync(barrier, 0, 64, st);
+        if (e != cudaSuccess) return cuda_status(e, "clear barrier");
+      }
+    }
+    const Layout L = make_layout(pc, true, P->prec, P->n_slices, P->kpad);
+    Tables tab;
+    int64_t* t0 = (int64_t*)(base + L.off_tab);
     tab.urow = t0;
-    tab.ucol = tab.urow + (int64_t)pr.n_q * pr.M;
-    tab.vrow = tab.ucol + (int64_t)pr.n_q * pr.K;
-    tab.vcol = tab.vrow + (int64_t)pr.n_q * pr.N;
-    tab.wrow = tab.vcol + (int64_t)pr.n_q * pr.K;
-    tab.wcol = tab.wrow + (int64_t)pr.n_q * pr.M;
+    tab.ucol = tab.urow + (int64_t)pc.n_q * pc.M;
+    tab.vrow = tab.ucol + (int64_t)pc.n_q * pc.K;
+    tab.vcol = tab.vrow + (int64_t)pc.n_q * pc.N;
+    tab.wrow = tab.vcol + (int64_t)pc.n_q * pc.K;
+    tab.wcol = tab.wrow + (int64_t)pc.n_q * pc.M;
+    unsigned long long* acc = L.ksplit > 1 ? (unsigned long long*)(base + L.off_acc) : nullptr;
+    unsigned* tile_ctr = L.ksplit > 1 ? (unsigned*)(base + L.off_ctr) : nullptr;
+    const int64_t acc_n = L.ksplit > 1 ? (int64_t)pc.n_q * pc.M * pc.N : 0;
+    const int64_t ctr_n = L.ksplit > 1 ? L.n_tiles : 0;
+    int32_t* ea = split ? (int32_t*)(base + L.off_ea) : nullptr;
+    int32_t* eb = split ? (int32_t*)(base + L.off_eb) : nullptr;
+    e = launch_prep(pc, tab, split, P->n_slices, u, v, base + L.off_a, base + L.off_b, ea, eb,
+                    P->kpad, err, barrier, acc, acc_n, tile_ctr, ctr_n, st);
+    if (e != cudaSuccess) return cuda_status(e, "operand preparation");
+    if (P->prof && q0 == 0) cudaEventRecord(P->ev[1], st);
+    if (split)
+      e = launch_gemm_split(pc, tab, P->n_slices, (const uint16_t*)(base + L.off_a),
+                            (const uint16_t*)(base + L.off_b), ea, eb, P->kpad, w, err, L.ksplit,
+                            acc, tile_ctr, st);
+    else
+      e = launch_gemm_tf32(pc, tab, (const float*)(base + L.off_a),
+                           (const float*)(base + L.off_b), P->kpad, w, err, st);
+    if (e != cudaSuccess) return cuda_status(e, split ? "gemm_split" : "gemm_tf32");
   }
-  e = launch_tables(pr, tab, st);
-  if (e != cudaSuccess) return cuda_status(e, "tables");
-  if (P->prec == SYMCTR_SPLIT_BF16) {
-    uint16_t* as = (uint16_t*)(base + P->off_a);
-    uint16_t* bs = (uint16_t*)(base + P->off_b);
-    int32_t* ea = (int32_t*)(base + P->off_ea);
-    int32_t* eb = (int32_t*)(base + P->off_eb);
-    e = launch_split_operand(pr, tab, 0, P->n_slices, u, as, P->kpad, ea, err, st);
-    if (e != cudaSuccess) return cuda_status(e, "split U");
-    e = launch_split_operand(pr, tab, 1, P->n_slices, v, bs, P->kpad, eb, err, st);
-    if (e != cudaSuccess) return cuda_status(e, "split V");
-    if (P->prof) cudaEventRecord(P->ev[1], st);
-    e = launch_gemm_split(pr, tab, P->n_slices, as, bs, ea, eb, P->kpad, w, err, P->ksplit,
-                          (unsigned long long*)(base + P->off_acc), st);
-    if (P->prof) cudaEventRecord(P->ev[2], st);
-    return cuda_status(e, "gemm_split");
-  }
-  float* a32 = (float*)(base + P->off_a);
-  float* b32 = (float*)(base + P->off_b);
-  e = launch_tf32_operand(pr, tab, 0, u, a32, P->kpad, st);
-  if (e != cudaSuccess) return cuda_status(e, "tf32 U");
-  e = launch_tf32_operand(pr, tab, 1, v, b32, P->kpad, st);
-  if (e != cudaSuccess) return cuda_status(e, "tf32 V");
-  if (P->prof) cudaEventRecord(P->ev[1], st);
-  e = launch_gemm_tf32(pr, tab, a32, b32, P->kpad, w, err, st);
   if (P->prof) cudaEventRecord(P->ev[2], st);
-  return cuda_status(e, "gemm_tf32");
+  return SYMCTR_OK;
 }
 
 }  // namespace
@@ -549,6 +599,7 @@ symctr_status symctr_plan_query(const symctr_plan* P, symctr_plan_info* o) {
   // transforms move each operand element once in and once out (8 B each way)
   o->transform_bytes = 16.0 * (double)(o->aligned_numel_u + o->aligned_numel_v + o->aligned_numel_w);
   o->workspace_bytes = P->ws_bytes;
+  o->workspace_bytes_min = P->ws_bytes_min;
   uint64_t wb = 256;
   if (P->bwd_u && P->bwd_u->ws_bytes > wb) wb = P->bwd_u->ws_bytes;
   if (P->bwd_v && P->bwd_v->ws_bytes > wb) wb = P->bwd_v->ws_bytes;

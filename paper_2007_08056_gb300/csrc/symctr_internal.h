@@ -100,13 +100,14 @@ struct OperandMap {
 struct Problem {
   GroupDesc g;
   int n_q;            // batches (irreps carrying work)
-  int q_single;       // irrep when n_q == 1
+  int q_single;       // the irrep of a single-irrep problem, else -1
+  int q_base;         // first irrep of batch 0 when q_single < 0 (Q-streaming)
   int64_t M, N, K;
   OperandMap u, v, w; // U: rows = free-U, cols = contracted; V: rows = free-V, cols = contracted;
                       // W: rows = free-U, cols = free-V
 };
 
-SC_HD int batch_irrep(const Problem& p, int b) { return p.n_q == 1 ? p.q_single : b; }
+SC_HD int batch_irrep(const Problem& p, int b) { return p.q_single >= 0 ? p.q_single : p.q_base + b; }
 
 // Offset tables of the aligned forms for one contraction (device memory in the
 // workspace): row_off / col_off of every (batch, index), int64.
@@ -141,16 +142,15 @@ cudaError_t launch_align_f64(const Problem& p, int operand, int direction, const
 cudaError_t launch_gemm_f64(const Problem& p, const double* u, const double* v, double* w,
                             cudaStream_t st);
 cudaError_t launch_fill_zero(double* w, int64_t n, cudaStream_t st);
-cudaError_t launch_tables(const Problem& p, const Tables& t, cudaStream_t st);
-cudaError_t launch_split_operand(const Problem& p, const Tables& t, int operand, int n_slices,
-                                 const double* src, uint16_t* slices, int64_t kpad, int32_t* exps,
-                                 unsigned* err, cudaStream_t st);
+cudaError_t launch_prep(const Problem& p, const Tables& t, bool split, int n_slices,
+                        const double* u, const double* v, void* ua, void* va, int32_t* eu,
+                        int32_t* ev, int64_t kpad, unsigned* err, unsigned* barrier,
+                        unsigned long long* zero64, int64_t zero64_n, unsigned* zero32,
+                        int64_t zero32_n, cudaStream_t st);
 cudaError_t launch_gemm_split(const Problem& p, const Tables& t, int n_slices, const uint16_t* us,
                               const uint16_t* vs, const int32_t* eu, const int32_t* ev,
                               int64_t kpad, double* w, unsigned* err, int ksplit,
-                              unsigned long long* wacc, cudaStream_t st);
-cudaError_t launch_tf32_operand(const Problem& p, const Tables& t, int operand, const double* src,
-                                float* dst, int64_t kpad, cudaStream_t st);
+                              unsigned long long* wacc, unsigned* tile_ctr, cudaStream_t st);
 cudaError_t launch_gemm_tf32(const Problem& p, const Tables& t, const float* u, const float* v,
                              int64_t kpad, double* w, unsigned* err, cudaStream_t st);
 

@@ -138,173 +138,200 @@ __device__ __forceinline__ uint16_t digit_bf16(int a, int slice) {
   return (uint16_t)(__float_as_uint(f) >> 16);         // low 16 bits are zero
 }
 
-// Offset tables: one thread per (batch, index) of the six index maps.
-__global__ void __launch_bounds__(THREADS) tables_kernel(Problem p, Tables t) {
-  const int64_t segs[6] = {p.M, p.K, p.N, p.K, p.M, p.N};
-  int64_t total = 0;
-  for (int i = 0; i < 6; ++i) total += segs[i] * p.n_q;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    int64_t rem = e;
-    int which = 0;
-    while (rem >= segs[which] * p.n_q) {
-      rem -= segs[which] * p.n_q;
-      ++which;
-    }
-    int64_t b = rem / segs[which], r = rem % segs[which];
-    int Q = batch_irrep(p, (int)b);
-    const AxisMap& a = which == 0 ? p.u.rows : which == 1 ? p.u.cols : which == 2 ? p.v.rows
-                     : which == 3 ? p.v.cols : which == 4 ? p.w.rows : p.w.cols;
-    int64_t* dst = which == 0 ? t.urow : which == 1 ? t.ucol : which == 2 ? t.vrow
-                 : which == 3 ? t.vcol : which == 4 ? t.wrow : t.wcol;
-    dst[rem] = axis_offset(a, p.g, Q, r);
-  }
-}
-
 // Row exponents, stored biased: E + kExpBias for a row whose largest entry
-// lies in [2^E, 2^(E+1)), 0 for an all-zero row (the buffer is zeroed first).
+// lies in [2^E, 2^(E+1)), 0 for an all-zero row.
 constexpr int32_t kExpBias = 4096;
 constexpr int SCAN_COLS = 256;
+constexpr int SLICE_COLS = 64;
 
-// Exponent scan: tiles of 32 rows x 256 columns, per-row maxima combined with
-// atomicMax in global memory, so any row length spreads over many CTAs.
-__global__ void __launch_bounds__(THREADS) exp_scan_kernel(Problem p, const int64_t* __restrict__ rtab,
-                                                           const int64_t* __restrict__ ctab, int64_t R,
-                                                           int64_t Cn, bool fast_rows,
-                                                           const double* __restrict__ src,
-                                                           int32_t* __restrict__ exps,
-                                                           unsigned* __restrict__ err) {
-  __shared__ int64_t roff[TILE], coff[SCAN_COLS];
-  __shared__ int32_t rmax[TILE];
+// Bounded grid-wide barrier of the cooperative prep launch (all CTAs are
+// co-resident).  `ctr` is zeroed before the launch; barrier number `phase`
+// completes when phase * gridDim.x arrivals have been counted.  On a wait of
+// more than ~2 s the error word gets DEVERR_TIMEOUT and the CTA goes on.
+__device__ __forceinline__ void grid_barrier(unsigned* ctr, unsigned phase, unsigned* err) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(ctr, 1u);
+    const unsigned target = phase * gridDim.x;
+    const long long t0 = clock64();
+    for (;;) {
+      unsigned seen;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(seen) : "l"(ctr) : "memory");
+      if (seen >= target) break;
+      if (clock64() - t0 > 4000000000ll) {
+        atomicOr(err, (unsigned)DEVERR_TIMEOUT);
+        break;
+      }
+      __nanosleep(64);
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+struct PrepArgs {
+  Problem p;
+  Tables t;
+  int split;                 // 1: exponent scan + BF16 slices, 0: TF32 copy
+  int S;
+  int64_t kpad;
+  const double* src[2];      // U, V standard reduced forms
+  void* dst[2];              // slices (split) or float32 operands (TF32)
+  int32_t* exps[2];
+  bool fast_rows[2];
+  unsigned* err;
+  unsigned* barrier;
+  unsigned long long* zero64;  // split-K partial sums, zeroed here
+  int64_t zero64_n;
+  unsigned* zero32;            // split-K tile counters, zeroed here
+  int64_t zero32_n;
+};
+
+__device__ __forceinline__ void operand_dims(const Problem& p, int op, int64_t* R, int64_t* Cn) {
+  *R = op == 0 ? p.M : p.N;
+  *Cn = p.K;
+}
+
+// One 32 x 256 tile of the exponent scan.
+__device__ void scan_tile(const PrepArgs& a, int op, int64_t tile, int64_t* roff, int64_t* coff,
+                          int32_t* rmax) {
+  const Problem& p = a.p;
+  int64_t R, Cn;
+  operand_dims(p, op, &R, &Cn);
+  const int64_t* rtab = op == 0 ? a.t.urow : a.t.vrow;
+  const int64_t* ctab = op == 0 ? a.t.ucol : a.t.vcol;
+  const double* src = a.src[op];
+  int32_t* exps = a.exps[op];
+  const bool fast_rows = a.fast_rows[op];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int64_t rt = (R + TILE - 1) / TILE, ct = (Cn + SCAN_COLS - 1) / SCAN_COLS;
-  const int64_t ntiles = rt * ct * p.n_q;
-  for (int64_t tI = blockIdx.x; tI < ntiles; tI += gridDim.x) {
-    int64_t b = tI / (rt * ct);
-    int64_t rem = tI - b * rt * ct;
-    int64_t r0 = (rem / ct) * TILE, c0 = (rem % ct) * SCAN_COLS;
-    __syncthreads();
-    if (threadIdx.x < TILE) {
-      int64_t r = r0 + threadIdx.x;
-      roff[threadIdx.x] = r < R ? rtab[b * R + r] : 0;
-      rmax[threadIdx.x] = 0;
-    }
-    {
-      int64_t c = c0 + threadIdx.x;
-      coff[threadIdx.x] = c < Cn ? ctab[b * Cn + c] : 0;
-    }
-    __syncthreads();
-    unsigned bad = 0;
-    constexpr int PER = SCAN_COLS / (THREADS / 32);   // 32 loads per thread, issued together
-    if (fast_rows) {
-      // lanes walk rows (contiguous), warps walk columns
-      double x[PER];
-      const bool rok = r0 + tx < R;
+  const int64_t b = tile / (rt * ct);
+  const int64_t rem = tile - b * rt * ct;
+  const int64_t r0 = (rem / ct) * TILE, c0 = (rem % ct) * SCAN_COLS;
+  __syncthreads();
+  if (threadIdx.x < TILE) {
+    int64_t r = r0 + threadIdx.x;
+    roff[threadIdx.x] = r < R ? rtab[b * R + r] : 0;
+    rmax[threadIdx.x] = 0;
+  }
+  {
+    int64_t c = c0 + threadIdx.x;
+    coff[threadIdx.x] = c < Cn ? ctab[b * Cn + c] : 0;
+  }
+  __syncthreads();
+  unsigned bad = 0;
+  constexpr int PER = SCAN_COLS / (THREADS / 32);
+  if (fast_rows) {
+    const bool rok = r0 + tx < R;
+    int32_t mx = 0;
 #pragma unroll
-      for (int i = 0; i < PER; ++i) {
-        int cc = ty + i * (THREADS / 32);
+    for (int h = 0; h < 2; ++h) {
+      double x[PER / 2];
+#pragma unroll
+      for (int i = 0; i < PER / 2; ++i) {
+        int cc = ty + (h * (PER / 2) + i) * (THREADS / 32);
         x[i] = (rok && c0 + cc < Cn) ? src[roff[tx] + coff[cc]] : 0.0;
       }
-      int32_t mx = 0;
 #pragma unroll
-      for (int i = 0; i < PER; ++i) {
+      for (int i = 0; i < PER / 2; ++i) {
         int32_t e = exponent_of(x[i], &bad);
         mx = max(mx, e == kZeroRowExp ? 0 : e + kExpBias);
       }
-      atomicMax(&rmax[tx], mx);
-    } else {
-      // lanes walk columns (contiguous), warps walk rows
-#pragma unroll
-      for (int rg = 0; rg < TILE / (THREADS / 32); ++rg) {
-        int rr = ty + rg * (THREADS / 32);
-        const bool rok = r0 + rr < R;
-        double x[SCAN_COLS / 32];
-#pragma unroll
-        for (int i = 0; i < SCAN_COLS / 32; ++i) {
-          int cc = tx + 32 * i;
-          x[i] = (rok && c0 + cc < Cn) ? src[roff[rr] + coff[cc]] : 0.0;
-        }
-        int32_t mx = 0;
-#pragma unroll
-        for (int i = 0; i < SCAN_COLS / 32; ++i) {
-          int32_t e = exponent_of(x[i], &bad);
-          mx = max(mx, e == kZeroRowExp ? 0 : e + kExpBias);
-        }
-        for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        if (tx == 0) rmax[rr] = max(rmax[rr], mx);
-      }
     }
-    if (bad) atomicOr(err, (unsigned)DEVERR_NONFINITE);
-    __syncthreads();
-    if (threadIdx.x < TILE && r0 + threadIdx.x < R && rmax[threadIdx.x] > 0)
-      atomicMax(&exps[b * R + r0 + threadIdx.x], rmax[threadIdx.x]);
+    atomicMax(&rmax[tx], mx);
+  } else {
+#pragma unroll
+    for (int rg = 0; rg < TILE / (THREADS / 32); ++rg) {
+      int rr = ty + rg * (THREADS / 32);
+      const bool rok = r0 + rr < R;
+      double x[SCAN_COLS / 32];
+#pragma unroll
+      for (int i = 0; i < SCAN_COLS / 32; ++i) {
+        int cc = tx + 32 * i;
+        x[i] = (rok && c0 + cc < Cn) ? src[roff[rr] + coff[cc]] : 0.0;
+      }
+      int32_t mx = 0;
+#pragma unroll
+      for (int i = 0; i < SCAN_COLS / 32; ++i) {
+        int32_t e = exponent_of(x[i], &bad);
+        mx = max(mx, e == kZeroRowExp ? 0 : e + kExpBias);
+      }
+      for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      if (tx == 0) rmax[rr] = max(rmax[rr], mx);
+    }
   }
+  if (bad) atomicOr(a.err, (unsigned)DEVERR_NONFINITE);
+  __syncthreads();
+  if (threadIdx.x < TILE && r0 + threadIdx.x < R && rmax[threadIdx.x] > 0)
+    atomicMax(&exps[b * R + r0 + threadIdx.x], rmax[threadIdx.x]);
 }
 
-constexpr int SLICE_COLS = 64;
-
-// Slicing: tiles of 32 rows x 64 columns of the padded aligned operand; the
-// source tile goes through shared memory so that the reduced form is read
-// along its contiguous axis and every slice row is written as 128-byte runs.
-__global__ void __launch_bounds__(THREADS) slice_kernel(Problem p, const int64_t* __restrict__ rtab,
-                                                        const int64_t* __restrict__ ctab, int64_t R,
-                                                        int64_t Cn, int64_t kpad, bool fast_rows,
-                                                        int S, const double* __restrict__ src,
-                                                        const int32_t* __restrict__ exps,
-                                                        uint32_t* __restrict__ slices) {
-  __shared__ double tile[TILE][SLICE_COLS + 1];
-  __shared__ int64_t roff[TILE], coff[SLICE_COLS];
-  __shared__ int32_t rexp[TILE];
+// One 32 x 64 tile of the padded aligned operand: gather through shared
+// memory, then either BF16 slices (split) or a TF32-rounded float32 copy.
+__device__ void slice_tile(const PrepArgs& a, int op, int64_t tile, int64_t* roff, int64_t* coff,
+                           int32_t* rexp, double (*tilebuf)[SLICE_COLS + 1]) {
+  const Problem& p = a.p;
+  int64_t R, Cn;
+  operand_dims(p, op, &R, &Cn);
+  const int64_t kpad = a.kpad;
+  const int64_t* rtab = op == 0 ? a.t.urow : a.t.vrow;
+  const int64_t* ctab = op == 0 ? a.t.ucol : a.t.vcol;
+  const double* src = a.src[op];
+  const bool fast_rows = a.fast_rows[op];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int64_t rt = (R + TILE - 1) / TILE, ct = (kpad + SLICE_COLS - 1) / SLICE_COLS;
-  const int64_t ntiles = rt * ct * p.n_q;
-  const int64_t slice_stride = (int64_t)p.n_q * R * kpad / 2;  // in uint32 pairs
-  for (int64_t tI = blockIdx.x; tI < ntiles; tI += gridDim.x) {
-    int64_t b = tI / (rt * ct);
-    int64_t rem = tI - b * rt * ct;
-    int64_t r0 = (rem / ct) * TILE, c0 = (rem % ct) * SLICE_COLS;
-    __syncthreads();
-    if (threadIdx.x < TILE) {
-      int64_t r = r0 + threadIdx.x;
-      roff[threadIdx.x] = r < R ? rtab[b * R + r] : 0;
-      int32_t st = r < R ? exps[b * R + r] : 0;
+  const int64_t b = tile / (rt * ct);
+  const int64_t rem = tile - b * rt * ct;
+  const int64_t r0 = (rem / ct) * TILE, c0 = (rem % ct) * SLICE_COLS;
+  __syncthreads();
+  if (threadIdx.x < TILE) {
+    int64_t r = r0 + threadIdx.x;
+    roff[threadIdx.x] = r < R ? rtab[b * R + r] : 0;
+    if (a.split) {
+      int32_t st = r < R ? a.exps[op][b * R + r] : 0;
       rexp[threadIdx.x] = st == 0 ? kZeroRowExp : st - kExpBias;
-    } else if (threadIdx.x < TILE + SLICE_COLS) {
-      int64_t c = c0 + threadIdx.x - TILE;
-      coff[threadIdx.x - TILE] = c < Cn ? ctab[b * Cn + c] : 0;
     }
-    __syncthreads();
-    if (fast_rows) {
-      double x[SLICE_COLS / (THREADS / 32)];
-      const bool rok = r0 + tx < R;
+  } else if (threadIdx.x < TILE + SLICE_COLS) {
+    int64_t c = c0 + threadIdx.x - TILE;
+    coff[threadIdx.x - TILE] = c < Cn ? ctab[b * Cn + c] : 0;
+  }
+  __syncthreads();
+  if (fast_rows) {
+    double x[SLICE_COLS / (THREADS / 32)];
+    const bool rok = r0 + tx < R;
 #pragma unroll
-      for (int i = 0; i < SLICE_COLS / (THREADS / 32); ++i) {
-        int cc = ty + i * (THREADS / 32);
-        x[i] = (rok && c0 + cc < Cn) ? src[roff[tx] + coff[cc]] : 0.0;
+    for (int i = 0; i < SLICE_COLS / (THREADS / 32); ++i) {
+      int cc = ty + i * (THREADS / 32);
+      x[i] = (rok && c0 + cc < Cn) ? src[roff[tx] + coff[cc]] : 0.0;
+    }
+#pragma unroll
+    for (int i = 0; i < SLICE_COLS / (THREADS / 32); ++i) tilebuf[tx][ty + i * (THREADS / 32)] = x[i];
+  } else {
+    double x[TILE / (THREADS / 32)][SLICE_COLS / 32];
+#pragma unroll
+    for (int rg = 0; rg < TILE / (THREADS / 32); ++rg)
+#pragma unroll
+      for (int i = 0; i < SLICE_COLS / 32; ++i) {
+        int rr = ty + rg * (THREADS / 32), cc = tx + 32 * i;
+        x[rg][i] = (r0 + rr < R && c0 + cc < Cn) ? src[roff[rr] + coff[cc]] : 0.0;
       }
 #pragma unroll
-      for (int i = 0; i < SLICE_COLS / (THREADS / 32); ++i) tile[tx][ty + i * (THREADS / 32)] = x[i];
-    } else {
-      double x[TILE / (THREADS / 32)][SLICE_COLS / 32];
+    for (int rg = 0; rg < TILE / (THREADS / 32); ++rg)
 #pragma unroll
-      for (int rg = 0; rg < TILE / (THREADS / 32); ++rg)
-#pragma unroll
-        for (int i = 0; i < SLICE_COLS / 32; ++i) {
-          int rr = ty + rg * (THREADS / 32), cc = tx + 32 * i;
-          x[rg][i] = (r0 + rr < R && c0 + cc < Cn) ? src[roff[rr] + coff[cc]] : 0.0;
-        }
-#pragma unroll
-      for (int rg = 0; rg < TILE / (THREADS / 32); ++rg)
-#pragma unroll
-        for (int i = 0; i < SLICE_COLS / 32; ++i) tile[ty + rg * (THREADS / 32)][tx + 32 * i] = x[rg][i];
-    }
-    __syncthreads();
+      for (int i = 0; i < SLICE_COLS / 32; ++i) tilebuf[ty + rg * (THREADS / 32)][tx + 32 * i] = x[rg][i];
+  }
+  __syncthreads();
+  if (a.split) {
     // each thread: one row, two adjacent columns -> one uint32 per slice
+    const int S = a.S;
+    uint32_t* slices = (uint32_t*)a.dst[op];
+    const int64_t slice_stride = (int64_t)p.n_q * R * kpad / 2;  // in uint32 pairs
     for (int rr = ty; rr < TILE; rr += THREADS / 32) {
       int64_t r = r0 + rr, c = c0 + 2 * tx;
       if (r >= R || c >= kpad) continue;
-      int64_t X0 = fixed_point(tile[rr][2 * tx], rexp[rr], S);
-      int64_t X1 = fixed_point(tile[rr][2 * tx + 1], rexp[rr], S);
+      int64_t X0 = fixed_point(tilebuf[rr][2 * tx], rexp[rr], S);
+      int64_t X1 = fixed_point(tilebuf[rr][2 * tx + 1], rexp[rr], S);
       uint32_t* dst = slices + ((b * R + r) * kpad + c) / 2;
       for (int i = S - 1; i >= 1; --i) {
         int a0 = (int)(((X0 + 128) & 255) - 128);
@@ -315,50 +342,89 @@ __global__ void __launch_bounds__(THREADS) slice_kernel(Problem p, const int64_t
       }
       dst[0] = (uint32_t)digit_bf16((int)X0, 0) | ((uint32_t)digit_bf16((int)X1, 0) << 16);
     }
+  } else {
+    float2* out = (float2*)a.dst[op];
+    for (int rr = ty; rr < TILE; rr += THREADS / 32) {
+      int64_t r = r0 + rr, c = c0 + 2 * tx;
+      if (r >= R || c >= kpad) continue;
+      float2 f;
+      f.x = __double2float_rn(tilebuf[rr][2 * tx]);
+      f.y = __double2float_rn(tilebuf[rr][2 * tx + 1]);
+      uint32_t ux = __float_as_uint(f.x), uy = __float_as_uint(f.y);
+      if ((ux & 0x7F800000u) != 0x7F800000u) ux = (ux + 0xFFFu + ((ux >> 13) & 1u)) & ~0x1FFFu;
+      if ((uy & 0x7F800000u) != 0x7F800000u) uy = (uy + 0xFFFu + ((uy >> 13) & 1u)) & ~0x1FFFu;
+      f.x = __uint_as_float(ux);
+      f.y = __uint_as_float(uy);
+      out[((b * R + r) * kpad + c) / 2] = f;
+    }
   }
 }
 
-// TF32 form: aligned float32 operand rounded to TF32 (round to nearest even
-// on the 10-bit mantissa), zero padded to kpad columns.
-__global__ void __launch_bounds__(THREADS) tf32_kernel(Problem p, const int64_t* __restrict__ rtab,
-                                                       const int64_t* __restrict__ ctab, int64_t R,
-                                                       int64_t Cn, int64_t kpad, bool fast_rows,
-                                                       const double* __restrict__ src,
-                                                       float* __restrict__ dst) {
-  __shared__ float tile[TILE][TILE + 1];
-  __shared__ int64_t roff[TILE], coff[TILE];
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  const int64_t rt = (R + TILE - 1) / TILE, ct = (kpad + TILE - 1) / TILE;
-  const int64_t ntiles = rt * ct * p.n_q;
-  for (int64_t tI = blockIdx.x; tI < ntiles; tI += gridDim.x) {
-    int64_t b = tI / (rt * ct);
-    int64_t rem = tI - b * rt * ct;
-    int64_t r0 = (rem / ct) * TILE, c0 = (rem % ct) * TILE;
-    __syncthreads();
-    if (threadIdx.x < TILE) {
-      int64_t r = r0 + threadIdx.x;
-      roff[threadIdx.x] = r < R ? rtab[b * R + r] : 0;
-    } else if (threadIdx.x < 2 * TILE) {
-      int64_t c = c0 + threadIdx.x - TILE;
-      coff[threadIdx.x - TILE] = c < Cn ? ctab[b * Cn + c] : 0;
-    }
-    __syncthreads();
-    for (int k = ty; k < TILE; k += THREADS / 32) {
-      int rr = fast_rows ? tx : k, cc = fast_rows ? k : tx;
-      float f = 0.f;
-      if (r0 + rr < R && c0 + cc < Cn) {
-        f = __double2float_rn(src[roff[rr] + coff[cc]]);
-        uint32_t u = __float_as_uint(f);
-        if ((u & 0x7F800000u) != 0x7F800000u) {
-          u = (u + 0xFFFu + ((u >> 13) & 1u)) & ~0x1FFFu;
-          f = __uint_as_float(u);
-        }
+// Operand preparation of one contraction in one cooperative launch:
+//   phase 0  offset tables of the six index maps; zero the row exponents and
+//            the split-K accumulators;
+//   phase 1  (split form) per-row exponent maxima of U and V;
+//   phase 2  BF16 slices (split) or TF32 copies of U and V.
+__global__ void __launch_bounds__(THREADS, 4) prep_kernel(PrepArgs a) {
+  __shared__ int64_t roff[TILE], coff[SCAN_COLS];
+  __shared__ int32_t rbuf[TILE];
+  __shared__ double tilebuf[TILE][SLICE_COLS + 1];
+  const Problem& p = a.p;
+  const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
+  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // phase 0
+  {
+    const int64_t segs[6] = {p.M, p.K, p.N, p.K, p.M, p.N};
+    int64_t* dsts[6] = {a.t.urow, a.t.ucol, a.t.vrow, a.t.vcol, a.t.wrow, a.t.wcol};
+    int64_t total = 0;
+    for (int i = 0; i < 6; ++i) total += segs[i] * p.n_q;
+    for (int64_t e = gtid; e < total; e += gthreads) {
+      int64_t rem = e;
+      int which = 0;
+      while (rem >= segs[which] * p.n_q) {
+        rem -= segs[which] * p.n_q;
+        ++which;
       }
-      tile[rr][cc] = f;
+      int64_t b = rem / segs[which], r = rem % segs[which];
+      int Q = batch_irrep(p, (int)b);
+      const AxisMap& m = which == 0 ? p.u.rows : which == 1 ? p.u.cols : which == 2 ? p.v.rows
+                       : which == 3 ? p.v.cols : which == 4 ? p.w.rows : p.w.cols;
+      dsts[which][rem] = axis_offset(m, p.g, Q, r);
     }
-    __syncthreads();
-    for (int k = ty; k < TILE; k += THREADS / 32) {
-      if (r0 + k < R && c0 + tx < kpad) dst[(b * R + r0 + k) * kpad + c0 + tx] = tile[k][tx];
+    if (a.split) {
+      for (int64_t e = gtid; e < (int64_t)p.n_q * p.M; e += gthreads) a.exps[0][e] = 0;
+      for (int64_t e = gtid; e < (int64_t)p.n_q * p.N; e += gthreads) a.exps[1][e] = 0;
+    }
+    for (int64_t e = gtid; e < a.zero64_n; e += gthreads) a.zero64[e] = 0ull;
+    for (int64_t e = gtid; e < a.zero32_n; e += gthreads) a.zero32[e] = 0u;
+  }
+  grid_barrier(a.barrier, 1, a.err);
+  unsigned next = 2;
+  if (a.split) {
+    int64_t tiles[2];
+    for (int op = 0; op < 2; ++op) {
+      int64_t R, Cn;
+      operand_dims(p, op, &R, &Cn);
+      tiles[op] = ((R + TILE - 1) / TILE) * ((Cn + SCAN_COLS - 1) / SCAN_COLS) * p.n_q;
+    }
+    for (int64_t t = blockIdx.x; t < tiles[0] + tiles[1]; t += gridDim.x) {
+      int op = t < tiles[0] ? 0 : 1;
+      scan_tile(a, op, op == 0 ? t : t - tiles[0], roff, coff, rbuf);
+    }
+    grid_barrier(a.barrier, next++, a.err);
+  }
+  // the GEMM that consumes these operands may start its setup now
+  asm volatile("griddepcontrol.launch_dependents;");
+  {
+    int64_t tiles[2];
+    for (int op = 0; op < 2; ++op) {
+      int64_t R, Cn;
+      operand_dims(p, op, &R, &Cn);
+      tiles[op] = ((R + TILE - 1) / TILE) * ((a.kpad + SLICE_COLS - 1) / SLICE_COLS) * p.n_q;
+    }
+    for (int64_t t = blockIdx.x; t < tiles[0] + tiles[1]; t += gridDim.x) {
+      int op = t < tiles[0] ? 0 : 1;
+      slice_tile(a, op, op == 0 ? t : t - tiles[0], roff, coff, rbuf, tilebuf);
     }
   }
 }
@@ -402,45 +468,52 @@ cudaError_t launch_align_f64(const Problem& p, int operand, int direction, const
   return cudaGetLastError();
 }
 
-cudaError_t launch_tables(const Problem& p, const Tables& t, cudaStream_t st) {
-  int64_t total = tables_entries(p);
-  if (total == 0) return cudaSuccess;
-  tables_kernel<<<grid_for((total + THREADS - 1) / THREADS), THREADS, 0, st>>>(p, t);
+cudaError_t launch_prep(const Problem& p, const Tables& t, bool split, int n_slices,
+                        const double* u, const double* v, void* ua, void* va, int32_t* eu,
+                        int32_t* ev, int64_t kpad, unsigned* err, unsigned* barrier,
+                        unsigned long long* zero64, int64_t zero64_n, unsigned* zero32,
+                        int64_t zero32_n, cudaStream_t st) {
+  static int max_blocks = 0;
+  if (max_blocks == 0) {
+    int dev = 0, sms = 0, per = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, prep_kernel, THREADS, 0);
+    if (e != cudaSuccess) return e;
+    max_blocks = sms * (per < 4 ? per : 4);
+  }
+  int64_t work = 0;
+  {
+    int64_t rt_u = (p.M + TILE - 1) / TILE, rt_v = (p.N + TILE - 1) / TILE;
+    int64_t ct = (kpad + SLICE_COLS - 1) / SLICE_COLS;
+    work = (rt_u + rt_v) * ct * p.n_q;
+  }
+  int grid = (int)(work < max_blocks ? (work > 0 ? work : 1) : max_blocks);
+  PrepArgs a;
+  a.p = p;
+  a.t = t;
+  a.split = split ? 1 : 0;
+  a.S = n_slices;
+  a.kpad = kpad;
+  a.src[0] = u;
+  a.src[1] = v;
+  a.dst[0] = ua;
+  a.dst[1] = va;
+  a.exps[0] = eu;
+  a.exps[1] = ev;
+  a.fast_rows[0] = rows_fast(p.u);
+  a.fast_rows[1] = rows_fast(p.v);
+  a.err = err;
+  a.barrier = barrier;
+  a.zero64 = zero64;
+  a.zero64_n = zero64_n;
+  a.zero32 = zero32;
+  a.zero32_n = zero32_n;
+  void* params[] = {&a};
+  cudaError_t e = cudaLaunchCooperativeKernel((const void*)prep_kernel, dim3(grid), dim3(THREADS),
+                                              params, 0, st);
   ++g_kernel_launches;
-  return cudaGetLastError();
-}
-
-cudaError_t launch_split_operand(const Problem& p, const Tables& t, int operand, int n_slices,
-                                 const double* src, uint16_t* slices, int64_t kpad, int32_t* exps,
-                                 unsigned* err, cudaStream_t st) {
-  int64_t R, Cn;
-  operand_extent(p, operand, &R, &Cn);
-  const OperandMap& m = operand_map(p, operand);
-  const int64_t* rt = operand == 0 ? t.urow : t.vrow;
-  const int64_t* ct = operand == 0 ? t.ucol : t.vcol;
-  cudaError_t e = cudaMemsetAsync(exps, 0, sizeof(int32_t) * R * p.n_q, st);
-  if (e != cudaSuccess) return e;
-  int64_t t1 = ((R + TILE - 1) / TILE) * ((Cn + SCAN_COLS - 1) / SCAN_COLS) * p.n_q;
-  exp_scan_kernel<<<grid_for(t1), THREADS, 0, st>>>(p, rt, ct, R, Cn, rows_fast(m), src, exps, err);
-  ++g_kernel_launches;
-  int64_t t2 = ((R + TILE - 1) / TILE) * ((kpad + SLICE_COLS - 1) / SLICE_COLS) * p.n_q;
-  slice_kernel<<<grid_for(t2), THREADS, 0, st>>>(p, rt, ct, R, Cn, kpad, rows_fast(m), n_slices, src,
-                                                  exps, (uint32_t*)slices);
-  ++g_kernel_launches;
-  return cudaGetLastError();
-}
-
-cudaError_t launch_tf32_operand(const Problem& p, const Tables& t, int operand, const double* src,
-                                float* dst, int64_t kpad, cudaStream_t st) {
-  int64_t R, Cn;
-  operand_extent(p, operand, &R, &Cn);
-  const OperandMap& m = operand_map(p, operand);
-  const int64_t* rt = operand == 0 ? t.urow : t.vrow;
-  const int64_t* ct = operand == 0 ? t.ucol : t.vcol;
-  int64_t tiles = ((R + TILE - 1) / TILE) * ((kpad + TILE - 1) / TILE) * p.n_q;
-  tf32_kernel<<<grid_for(tiles), THREADS, 0, st>>>(p, rt, ct, R, Cn, kpad, rows_fast(m), src, dst);
-  ++g_kernel_launches;
-  return cudaGetLastError();
+  return e;
 }
 
 }  // namespace symctr

@@ -222,6 +222,20 @@ def test_small_workloads_all_routes(case):
         assert abs(O.contract_element(p, u, v, idx) - w4[idx]) <= 1e-12 * (1 + abs(w4[idx]))
 
 
+@pytest.mark.parametrize("case", WL.small_cases(), ids=lambda c: c.name)
+def test_lazy_element_matches_block_loop(case):
+    """The callback form used for operands that only live on a device sums the
+    same terms as the block loop."""
+    p = mk(case)
+    u, v = WL.draw_pair(case)
+    w4 = O.contract_blockloop(p, u, v)
+    rng = np.random.default_rng(4)
+    for _ in range(5):
+        idx = tuple(int(rng.integers(0, n)) for n in w4.shape)
+        got = O.contract_element_lazy(p, lambda i: u[i], lambda i: v[i], idx)
+        assert abs(got - w4[idx]) <= 1e-12 * (1 + abs(w4[idx]))
+
+
 def test_g1_is_plain_dense():
     """G = 1: the reduced form is the dense tensor; the contraction is np.einsum."""
     rng = np.random.default_rng(5)
