@@ -23,6 +23,21 @@ __host__ inline bool rows_fast(const OperandMap& m) {
   return m.rows.n > 0 && m.rows.bstride[m.rows.n - 1] == 1;
 }
 
+// True when columns 2j and 2j+1 of every row are adjacent in memory and the
+// even one sits at an even offset: the innermost column digit has stride 1 and
+// an even extent, and every other stride of rows and columns is even.
+__host__ inline bool pairs_aligned(const OperandMap& m) {
+  const AxisMap& c = m.cols;
+  if (c.n == 0 || c.bstride[c.n - 1] != 1 || (c.D[c.n - 1] & 1)) return false;
+  for (int i = 0; i < c.n; ++i) {
+    if (i < c.n - 1 && (c.bstride[i] & 1)) return false;
+    if (c.sstride[i] & 1) return false;
+  }
+  for (int i = 0; i < m.rows.n; ++i)
+    if ((m.rows.bstride[i] & 1) || (m.rows.sstride[i] & 1)) return false;
+  return true;
+}
+
 __global__ void fill_zero_kernel(double* __restrict__ w, int64_t n) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -131,6 +146,24 @@ __device__ __forceinline__ int64_t fixed_point(double x, int32_t E, int S) {
   return (bits >> 63) ? -v : v;
 }
 
+// Balanced base-256 digits by byte extraction: with B = 0x80 * (256^S - 1)/255,
+// Y = X + B has bytes (a_k + 128) for the low S-1 digits and (a_top + 128) in
+// [0, 256] above them (no carries: every shifted digit lies in [0, 255]).
+__host__ __device__ constexpr uint64_t digit_bias(int S) {
+  uint64_t b = 0;
+  for (int k = 0; k < S; ++k) b |= (uint64_t)0x80 << (8 * k);
+  return b;
+}
+
+// BF16 bits of (u - 128) * 2^(-8 i) for a biased digit u in [0, 256], with
+// full-rate operations only: 0x4B000000 | u is the float 2^23 + u, so one
+// subtraction gives u - 128 exactly; the scale is an exponent decrement.
+__device__ __forceinline__ uint32_t bf16_of_biased(uint32_t u, int i) {
+  const float f = __uint_as_float(0x4B000000u | u) - 8388736.0f;
+  const uint32_t b = __float_as_uint(f) >> 16;
+  return b ? b - ((uint32_t)i << 10) : 0u;
+}
+
 __device__ __forceinline__ uint16_t digit_bf16(int a, int slice) {
   if (a == 0) return 0;
   float f = (float)a;                                  // exact, |a| <= 128
@@ -180,6 +213,7 @@ struct PrepArgs {
   void* dst[2];              // slices (split) or float32 operands (TF32)
   int32_t* exps[2];
   bool fast_rows[2];
+  bool pair_ok[2];           // column-contiguous with every offset of an even column even
   unsigned* err;
   unsigned* barrier;
   unsigned long long* zero64;  // split-K partial sums, zeroed here
@@ -267,8 +301,43 @@ __device__ void scan_tile(const PrepArgs& a, int op, int64_t tile, int64_t* roff
     atomicMax(&exps[b * R + r0 + threadIdx.x], rmax[threadIdx.x]);
 }
 
-// One 32 x 64 tile of the padded aligned operand: gather through shared
-// memory, then either BF16 slices (split) or a TF32-rounded float32 copy.
+// Writes the S slices of two adjacent columns (c, c+1) of one row.
+template <int S>
+__device__ __forceinline__ void put_slices_pair(double x0, double x1, int32_t E, uint32_t* dst,
+                                                int64_t stride) {
+  const uint64_t y0 = (uint64_t)(fixed_point(x0, E, S) + (int64_t)digit_bias(S));
+  const uint64_t y1 = (uint64_t)(fixed_point(x1, E, S) + (int64_t)digit_bias(S));
+#pragma unroll
+  for (int i = 0; i < S; ++i) {
+    const int k = S - 1 - i;  // byte position of slice i's digit
+    const uint32_t u0 = i == 0 ? (uint32_t)(y0 >> (8 * k)) : (uint32_t)(y0 >> (8 * k)) & 255u;
+    const uint32_t u1 = i == 0 ? (uint32_t)(y1 >> (8 * k)) : (uint32_t)(y1 >> (8 * k)) & 255u;
+    dst[(int64_t)i * stride] = bf16_of_biased(u0, i) | (bf16_of_biased(u1, i) << 16);
+  }
+}
+
+template <int S>
+__device__ __forceinline__ void put_slices_one(double x, int32_t E, uint16_t* dst, int64_t stride) {
+  const uint64_t y = (uint64_t)(fixed_point(x, E, S) + (int64_t)digit_bias(S));
+#pragma unroll
+  for (int i = 0; i < S; ++i) {
+    const int k = S - 1 - i;
+    const uint32_t u = i == 0 ? (uint32_t)(y >> (8 * k)) : (uint32_t)(y >> (8 * k)) & 255u;
+    dst[(int64_t)i * stride] = (uint16_t)bf16_of_biased(u, i);
+  }
+}
+
+__device__ __forceinline__ float tf32_round(double x) {
+  uint32_t u = __float_as_uint(__double2float_rn(x));
+  if ((u & 0x7F800000u) != 0x7F800000u) u = (u + 0xFFFu + ((u >> 13) & 1u)) & ~0x1FFFu;
+  return __uint_as_float(u);
+}
+
+// One 32 x 64 tile of the padded aligned operand.  Column-contiguous operands
+// are read along the columns straight from global memory (16-byte loads when
+// every offset is even), row-contiguous ones go through shared memory so that
+// both the gather and the slice stores are coalesced.
+template <int S>
 __device__ void slice_tile(const PrepArgs& a, int op, int64_t tile, int64_t* roff, int64_t* coff,
                            int32_t* rexp, double (*tilebuf)[SLICE_COLS + 1]) {
   const Problem& p = a.p;
@@ -284,11 +353,50 @@ __device__ void slice_tile(const PrepArgs& a, int op, int64_t tile, int64_t* rof
   const int64_t b = tile / (rt * ct);
   const int64_t rem = tile - b * rt * ct;
   const int64_t r0 = (rem / ct) * TILE, c0 = (rem % ct) * SLICE_COLS;
+  const bool split = a.split;
+  const int64_t slice_stride = (int64_t)p.n_q * R * kpad;   // elements
+  if (!fast_rows) {
+    // lanes walk column pairs; warps walk rows; no shared memory
+    const int64_t c = c0 + 2 * tx;
+    const bool pair = a.pair_ok[op];
+    int64_t co0 = 0, co1 = 0;
+    if (c < Cn) co0 = ctab[b * Cn + c];
+    if (!pair && c + 1 < Cn) co1 = ctab[b * Cn + c + 1];
+#pragma unroll
+    for (int rg = 0; rg < TILE / (THREADS / 32); ++rg) {
+      const int64_t r = r0 + ty + rg * (THREADS / 32);
+      if (r >= R || c >= kpad) continue;
+      const int64_t ro = rtab[b * R + r];
+      double x0 = 0.0, x1 = 0.0;
+      if (pair) {
+        if (c < Cn) {
+          const double2 v2 = *reinterpret_cast<const double2*>(src + ro + co0);
+          x0 = v2.x;
+          x1 = v2.y;
+        }
+      } else {
+        if (c < Cn) x0 = src[ro + co0];
+        if (c + 1 < Cn) x1 = src[ro + co1];
+      }
+      const int64_t e_at = (b * R + r) * kpad + c;
+      if (split) {
+        const int32_t st = a.exps[op][b * R + r];
+        const int32_t E = st == 0 ? kZeroRowExp : st - kExpBias;
+        put_slices_pair<S>(x0, x1, E, (uint32_t*)a.dst[op] + e_at / 2, slice_stride / 2);
+      } else {
+        float2 f;
+        f.x = tf32_round(x0);
+        f.y = tf32_round(x1);
+        reinterpret_cast<float2*>(a.dst[op])[e_at / 2] = f;
+      }
+    }
+    return;
+  }
   __syncthreads();
   if (threadIdx.x < TILE) {
     int64_t r = r0 + threadIdx.x;
     roff[threadIdx.x] = r < R ? rtab[b * R + r] : 0;
-    if (a.split) {
+    if (split) {
       int32_t st = r < R ? a.exps[op][b * R + r] : 0;
       rexp[threadIdx.x] = st == 0 ? kZeroRowExp : st - kExpBias;
     }
@@ -297,7 +405,7 @@ __device__ void slice_tile(const PrepArgs& a, int op, int64_t tile, int64_t* rof
     coff[threadIdx.x - TILE] = c < Cn ? ctab[b * Cn + c] : 0;
   }
   __syncthreads();
-  if (fast_rows) {
+  {
     double x[SLICE_COLS / (THREADS / 32)];
     const bool rok = r0 + tx < R;
 #pragma unroll
@@ -307,55 +415,21 @@ __device__ void slice_tile(const PrepArgs& a, int op, int64_t tile, int64_t* rof
     }
 #pragma unroll
     for (int i = 0; i < SLICE_COLS / (THREADS / 32); ++i) tilebuf[tx][ty + i * (THREADS / 32)] = x[i];
-  } else {
-    double x[TILE / (THREADS / 32)][SLICE_COLS / 32];
-#pragma unroll
-    for (int rg = 0; rg < TILE / (THREADS / 32); ++rg)
-#pragma unroll
-      for (int i = 0; i < SLICE_COLS / 32; ++i) {
-        int rr = ty + rg * (THREADS / 32), cc = tx + 32 * i;
-        x[rg][i] = (r0 + rr < R && c0 + cc < Cn) ? src[roff[rr] + coff[cc]] : 0.0;
-      }
-#pragma unroll
-    for (int rg = 0; rg < TILE / (THREADS / 32); ++rg)
-#pragma unroll
-      for (int i = 0; i < SLICE_COLS / 32; ++i) tilebuf[ty + rg * (THREADS / 32)][tx + 32 * i] = x[rg][i];
   }
   __syncthreads();
-  if (a.split) {
-    // each thread: one row, two adjacent columns -> one uint32 per slice
-    const int S = a.S;
-    uint32_t* slices = (uint32_t*)a.dst[op];
-    const int64_t slice_stride = (int64_t)p.n_q * R * kpad / 2;  // in uint32 pairs
-    for (int rr = ty; rr < TILE; rr += THREADS / 32) {
-      int64_t r = r0 + rr, c = c0 + 2 * tx;
-      if (r >= R || c >= kpad) continue;
-      int64_t X0 = fixed_point(tilebuf[rr][2 * tx], rexp[rr], S);
-      int64_t X1 = fixed_point(tilebuf[rr][2 * tx + 1], rexp[rr], S);
-      uint32_t* dst = slices + ((b * R + r) * kpad + c) / 2;
-      for (int i = S - 1; i >= 1; --i) {
-        int a0 = (int)(((X0 + 128) & 255) - 128);
-        int a1 = (int)(((X1 + 128) & 255) - 128);
-        X0 = (X0 - a0) >> 8;
-        X1 = (X1 - a1) >> 8;
-        dst[(int64_t)i * slice_stride] = (uint32_t)digit_bf16(a0, i) | ((uint32_t)digit_bf16(a1, i) << 16);
-      }
-      dst[0] = (uint32_t)digit_bf16((int)X0, 0) | ((uint32_t)digit_bf16((int)X1, 0) << 16);
-    }
-  } else {
-    float2* out = (float2*)a.dst[op];
-    for (int rr = ty; rr < TILE; rr += THREADS / 32) {
-      int64_t r = r0 + rr, c = c0 + 2 * tx;
-      if (r >= R || c >= kpad) continue;
+  // each thread: one row, two adjacent columns -> one uint32 per slice
+  for (int rr = ty; rr < TILE; rr += THREADS / 32) {
+    int64_t r = r0 + rr, c = c0 + 2 * tx;
+    if (r >= R || c >= kpad) continue;
+    const int64_t e_at = (b * R + r) * kpad + c;
+    if (split) {
+      put_slices_pair<S>(tilebuf[rr][2 * tx], tilebuf[rr][2 * tx + 1], rexp[rr],
+                         (uint32_t*)a.dst[op] + e_at / 2, slice_stride / 2);
+    } else {
       float2 f;
-      f.x = __double2float_rn(tilebuf[rr][2 * tx]);
-      f.y = __double2float_rn(tilebuf[rr][2 * tx + 1]);
-      uint32_t ux = __float_as_uint(f.x), uy = __float_as_uint(f.y);
-      if ((ux & 0x7F800000u) != 0x7F800000u) ux = (ux + 0xFFFu + ((ux >> 13) & 1u)) & ~0x1FFFu;
-      if ((uy & 0x7F800000u) != 0x7F800000u) uy = (uy + 0xFFFu + ((uy >> 13) & 1u)) & ~0x1FFFu;
-      f.x = __uint_as_float(ux);
-      f.y = __uint_as_float(uy);
-      out[((b * R + r) * kpad + c) / 2] = f;
+      f.x = tf32_round(tilebuf[rr][2 * tx]);
+      f.y = tf32_round(tilebuf[rr][2 * tx + 1]);
+      reinterpret_cast<float2*>(a.dst[op])[e_at / 2] = f;
     }
   }
 }
@@ -424,7 +498,15 @@ __global__ void __launch_bounds__(THREADS, 4) prep_kernel(PrepArgs a) {
     }
     for (int64_t t = blockIdx.x; t < tiles[0] + tiles[1]; t += gridDim.x) {
       int op = t < tiles[0] ? 0 : 1;
-      slice_tile(a, op, op == 0 ? t : t - tiles[0], roff, coff, rbuf, tilebuf);
+      int64_t tt = op == 0 ? t : t - tiles[0];
+      switch (a.split ? a.S : 1) {
+        case 1: slice_tile<1>(a, op, tt, roff, coff, rbuf, tilebuf); break;
+        case 2: slice_tile<2>(a, op, tt, roff, coff, rbuf, tilebuf); break;
+        case 3: slice_tile<3>(a, op, tt, roff, coff, rbuf, tilebuf); break;
+        case 4: slice_tile<4>(a, op, tt, roff, coff, rbuf, tilebuf); break;
+        case 5: slice_tile<5>(a, op, tt, roff, coff, rbuf, tilebuf); break;
+        default: slice_tile<6>(a, op, tt, roff, coff, rbuf, tilebuf); break;
+      }
     }
   }
 }
@@ -503,6 +585,8 @@ cudaError_t launch_prep(const Problem& p, const Tables& t, bool split, int n_sli
   a.exps[1] = ev;
   a.fast_rows[0] = rows_fast(p.u);
   a.fast_rows[1] = rows_fast(p.v);
+  a.pair_ok[0] = !a.fast_rows[0] && pairs_aligned(p.u);
+  a.pair_ok[1] = !a.fast_rows[1] && pairs_aligned(p.v);
   a.err = err;
   a.barrier = barrier;
   a.zero64 = zero64;
