@@ -57,16 +57,25 @@ def mps_workload():
     return name, E, A
 
 
-def cc_workload():
-    c = WL.CC_LADDER
-    return "cc_ladder_Z8_virt8x32_occ8x8 (w=v.t)", WL.draw(c.u, c.moduli), WL.draw(c.v, c.moduli)
+def cc_contraction(args):
+    if args.cc_dims:
+        virt, occ = (int(x) for x in args.cc_dims.split(","))
+        return WL.cc_ladder(8, virt, occ)
+    return WL.CC_LADDER
+
+
+def cc_workload(args):
+    c = cc_contraction(args)
+    g = c.moduli[0]
+    name = f"cc_ladder_Z{g}_virt{g}x{c.u.dims[0]}_occ{g}x{c.u.dims[-1]} (w=v.t)"
+    return name, WL.draw(c.u, c.moduli), WL.draw(c.v, c.moduli)
 
 
 # ---------------------------------------------------------------------------
 # oracle (CPU float64) -- cpu_baseline leg and the reference arm only
 # ---------------------------------------------------------------------------
 
-def oracle_step(workload, a, b):
+def oracle_step(workload, a, b, c=None):
     import oracle as O
     if workload == "mps":
         g = O.Group((WL.MPS_G,))
@@ -77,14 +86,14 @@ def oracle_step(workload, a, b):
             x = O.contract_blockloop(p1, a, b)
             return O.contract_blockloop(p2, x, b)
         return run
-    c = WL.CC_LADDER
+    c = c or WL.CC_LADDER
     p = O.plan(c.einsum, O.Group(c.moduli), O.Sym(*spec(c.u)), O.Sym(*spec(c.v)))
-    # bounded sample: one irrep Q of the block loop (1/G of the flops)
+    # the whole block loop (its G^(s+t+v-2) block products are NumPy matmuls)
     return lambda: O.contract_blockloop(p, a, b)
 
 
-def time_oracle(workload, a, b, budget_s=12.0, max_reps=50):
-    run = oracle_step(workload, a, b)
+def time_oracle(workload, a, b, budget_s=12.0, max_reps=50, c=None):
+    run = oracle_step(workload, a, b, c)
     out = run()
     ts = []
     t_end = time.perf_counter() + budget_s
@@ -157,23 +166,30 @@ class Clocks:
 # our arm
 # ---------------------------------------------------------------------------
 
-def kernel_source_hash():
+# the sources that decide each kernel's code and launch shape
+KERNEL_SOURCES = {
+    "prep_kernel": ("transforms.cu", "symctr_internal.h", "plan.cpp"),
+    "gemm_tc_kernel": ("gemm_tc.cu", "symctr_internal.h", "plan.cpp"),
+    "gemm_f64": ("gemm_f64.cu", "symctr_internal.h", "plan.cpp"),
+}
+
+
+def kernel_source_hash(kernel):
     h = hashlib.sha256()
-    for f in sorted(os.listdir(os.path.join(ROOT, "paper_2007_08056_gb300", "csrc"))):
+    for f in KERNEL_SOURCES[kernel]:
         with open(os.path.join(ROOT, "paper_2007_08056_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def load_traffic(kernel_key):
-    """DRAM traffic per launch from the committed ncu summary, if it was taken
-    on the current kernel sources."""
+def load_traffic(kernel, key):
+    """DRAM bytes per launch (read + write) from the committed ncu summary
+    profiles/traffic.json, if it was taken on the current kernel sources."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
-            d = json.load(f)
-        e = d.get(kernel_key)
-        if e and e.get("source_hash") == kernel_source_hash():
+            e = json.load(f).get(key)
+        if e and e.get("source_hash") == kernel_source_hash(kernel):
             return e.get("bytes_per_launch")
     except Exception:
         pass
@@ -192,12 +208,62 @@ def peaks():
     return p
 
 
+def prep_bytes(pl):
+    """Algorithmic bytes of one operand-prep launch: every aligned operand
+    element read once as float64 and written once in the GEMM's operand format
+    (S BF16 slices, or one TF32 word), plus one int32 exponent per row."""
+    i = pl.info
+    elems = i.aligned_numel_u + i.aligned_numel_v
+    if i.precision == 1:
+        return elems * (8 + 2 * i.n_slices) + 4 * i.n_q * (i.M + i.N)
+    return elems * (8 + 4)
+
+
+def rooflines(args, plans, prep, gemm, pk):
+    """One roofline per kernel kind of the step: achieved = algorithmic work of
+    its launches in one step / their CUDA-event time in that step."""
+    out = []
+    gemm_ms = sum(gemm)
+    if args.precision == "split_bf16":
+        pairs = [pl.info.n_slices * (pl.info.n_slices + 1) // 2 for pl in plans]
+        work = sum(pl.useful_flops * k for pl, k in zip(plans, pairs))
+        kernel, bound, unit, peak = "gemm_tc_kernel", "tensor", "TFLOP/s", pk["bf16_tflops"]
+        peak_src = f"{pk['src']} bf16 burst"
+    elif args.precision == "tf32":
+        work = sum(pl.useful_flops for pl in plans)
+        kernel, bound, unit, peak = "gemm_tc_kernel", "tensor", "TFLOP/s", pk["bf16_tflops"] / 2
+        peak_src = f"{pk['src']} bf16 burst x 1/2 (nominal tf32:bf16 ratio)"
+    else:
+        work = sum(pl.useful_flops for pl in plans)
+        kernel, bound, unit, peak = "gemm_f64", "alu", "TFLOP/s", 1.25
+        peak_src = "1.25 TFLOP/s nominal FP64 (152 SMs x FP64 units x clock; cuBLAS DGEMM measured 1.1)"
+    achieved = work / (gemm_ms * 1e-3) / 1e12
+    key = f"{kernel}/{args.precision}/{args.workload}"
+    out.append({"kernel": kernel, "bound": bound, "achieved": round(achieved, 3), "peak": peak,
+                "unit": unit, "frac": round(achieved / peak, 4),
+                "traffic": load_traffic(kernel, key), "peak_src": peak_src,
+                "launches_per_step": len(plans), "ms_per_step": round(gemm_ms, 4),
+                "work_per_launch": work / len(plans)})
+    prep_ms = sum(prep)
+    if args.precision != "fp64" and prep_ms > 0:
+        nbytes = sum(prep_bytes(pl) for pl in plans)
+        achieved = nbytes / (prep_ms * 1e-3) / 1e9
+        key = f"prep_kernel/{args.precision}/{args.workload}"
+        out.append({"kernel": "prep_kernel", "bound": "hbm", "achieved": round(achieved, 1),
+                    "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": round(achieved / pk["hbm_gbs"], 4),
+                    "traffic": load_traffic("prep_kernel", key), "peak_src": f"{pk['src']} hbm copy",
+                    "launches_per_step": len(plans), "ms_per_step": round(prep_ms, 4),
+                    "work_per_launch": nbytes / len(plans)})
+    return out
+
+
 def run_ours(args, rank, world):
     import torch
     import paper_2007_08056_gb300 as sc
 
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
     dev = torch.device("cuda")
+    ctr = None
     if args.workload == "mps":
         name, Eh, Ah = mps_workload()
         E, A = torch.from_numpy(Eh).to(dev), torch.from_numpy(Ah).to(dev)
@@ -215,9 +281,9 @@ def run_ours(args, rank, world):
             return [p1, p2], step, out
         inputs_host = [Eh, Ah]
     else:
-        name, Uh, Vh = cc_workload()
+        name, Uh, Vh = cc_workload(args)
         U, V = torch.from_numpy(Uh).to(dev), torch.from_numpy(Vh).to(dev)
-        c = WL.CC_LADDER
+        c = ctr = cc_contraction(args)
 
         def make(prec):
             p = sc.Plan(c.einsum, c.moduli, spec(c.u), spec(c.v), prec)
@@ -278,7 +344,7 @@ def run_ours(args, rank, world):
     # accuracy of the forms against the oracle (outside any timed region)
     res = {}
     if rank == 0:
-        ref = oracle_step(args.workload, *inputs_host)()
+        ref = oracle_step(args.workload, *inputs_host, c=ctr)()
         got = step().cpu().numpy()
         res[args.precision] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
     # the FP64 form beside it
@@ -310,30 +376,9 @@ def run_ours(args, rank, world):
         ms_e2e = float(t.item())
 
     pk = peaks()
-    # dominant kernel: the GEMM launch of the heavier contraction
-    gemm_total = sum(gemm)
-    prep_total = sum(prep)
-    i_dom = int(np.argmax(gemm))
-    pl = plans[i_dom]
-    if args.precision == "split_bf16":
-        pairs = pl.info.n_slices * (pl.info.n_slices + 1) // 2
-        per_launch_flops = pl.useful_flops * pairs
-        peak = pk["bf16_tflops"]
-        bound, unit = "tensor", "TFLOP/s"
-        achieved = per_launch_flops / (gemm[i_dom] * 1e-3) / 1e12
-        key = "gemm_split_bf16_" + args.workload
-    elif args.precision == "tf32":
-        per_launch_flops = pl.useful_flops
-        peak = pk["bf16_tflops"] / 2
-        bound, unit = "tensor", "TFLOP/s"
-        achieved = per_launch_flops / (gemm[i_dom] * 1e-3) / 1e12
-        key = "gemm_tf32_" + args.workload
-    else:
-        per_launch_flops = pl.useful_flops
-        peak = 1.25
-        bound, unit = "alu", "TFLOP/s"
-        achieved = per_launch_flops / (gemm[i_dom] * 1e-3) / 1e12
-        key = "gemm_f64_" + args.workload
+    roofs = rooflines(args, plans, prep, gemm, pk)
+    dominant = max(roofs, key=lambda r: r["ms_per_step"])
+    other = [r for r in roofs if r is not dominant]
     clocks = clk.summary()
     line = {
         "metric": "useful TFLOP/s, split-BF16 vs FP64 irrep-aligned contraction at stated rel err",
@@ -356,10 +401,8 @@ def run_ours(args, rank, world):
         "rel_err_vs_oracle": {k: float(f"{v:.3e}") for k, v in res.items()},
         "fp64_form": fp64,
         "phases_ms": {"prep": [round(x, 4) for x in prep], "gemm": [round(x, 4) for x in gemm]},
-        "roofline": {"bound": bound, "achieved": round(achieved, 3), "peak": peak, "unit": unit,
-                     "frac": round(achieved / peak, 4), "traffic": load_traffic(key),
-                     "kernel": key, "peak_src": pk["src"] if bound != "alu" else
-                     "1.25 TFLOP/s nominal FP64 (measured cuBLAS DGEMM 1.1)"},
+        "roofline": dominant,
+        "roofline_other": other[0] if other else None,
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
         "e2e": {"value": round(world * flops / (ms_e2e * 1e-3) / 1e12, 4), "unit": "TFLOP/s",
@@ -368,7 +411,7 @@ def run_ours(args, rank, world):
                 "d2h_bytes_per_step": int(out.numel() * 8)},
     }
     if rank == 0 and not args.no_cpu_baseline:
-        _, t_or, reps = time_oracle(args.workload, *inputs_host, budget_s=args.cpu_budget)
+        _, t_or, reps = time_oracle(args.workload, *inputs_host, budget_s=args.cpu_budget, c=ctr)
         line["cpu_baseline"] = {"value": round(flops / t_or / 1e12, 6), "unit": "TFLOP/s",
                                 "cores": _CORES, "kind": "oracle",
                                 "sample": f"whole step (both contractions), block-loop route, "
@@ -424,6 +467,9 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--cc-dims", default=None,
+                    help="VIRT,OCC for the cc_ladder workload (default 256,64); smaller cases are "
+                         "for profiling captures")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 

@@ -270,6 +270,46 @@ __device__ __forceinline__ double i64_scaled(long long Rv, int e) {
   return i64_scaled_slow(Rv, e);
 }
 
+// Out-of-line copies for the rare entries of a batch (keeps the batch code small).
+__device__ __noinline__ double i64_scaled_rare(long long Rv, int e) { return i64_scaled_slow(Rv, e); }
+
+// The common case of i64_scaled without branches (selects only), so that a
+// batch of conversions interleaves: exact for Rv = 0, or |Rv| < 2^53 with a
+// normal result; `slow` is set for every other Rv.
+__device__ __forceinline__ double i64_scaled_common(long long Rv, int e, bool& slow) {
+  const uint64_t sm = (uint64_t)(Rv >> 63);   // all ones for Rv < 0
+  const uint64_t m = ((uint64_t)Rv ^ sm) - sm;
+  const int nb = 64 - __clzll((long long)m);
+  const int be = e + nb - 1 + 1023;
+  const uint64_t q = m << ((53 - nb) & 63);
+  const uint64_t bits = (sm << 63) | ((uint64_t)(unsigned)be << 52) | (q & ((1ull << 52) - 1));
+  slow = Rv != 0 && ((m >> 53) != 0 || (unsigned)(be - 1) >= 2046u);
+  return Rv == 0 ? 0.0 : __longlong_as_double((long long)bits);
+}
+
+// RN(Rv[j] * 2^e[j]) for a batch: the common case for all, the general routine
+// only for the entries that need it.
+template <int B>
+__device__ __forceinline__ void i64_scaled_batch(const long long (&Rv)[B], const int (&e)[B], double (&d)[B]) {
+  unsigned slow_mask = 0;
+#pragma unroll
+  for (int j = 0; j < B; ++j) {
+    bool sl;
+    d[j] = i64_scaled_common(Rv[j], e[j], sl);
+    slow_mask |= (unsigned)sl << j;
+  }
+  if (slow_mask) {
+#pragma unroll
+    for (int j = 0; j < B; ++j)
+      if ((slow_mask >> j) & 1u) d[j] = i64_scaled_rare(Rv[j], e[j]);
+  }
+}
+
+// Fire-and-forget 64-bit integer add in L2 (no value returned).
+__device__ __forceinline__ void red_add_u64(unsigned long long* a, unsigned long long v) {
+  asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(a), "l"(v) : "memory");
+}
+
 // Exact float32 -> float64 with integer operations.
 __device__ __forceinline__ double f32_to_f64(uint32_t u) {
   uint64_t sgn = (uint64_t)(u >> 31) << 63;
@@ -281,6 +321,29 @@ __device__ __forceinline__ double f32_to_f64(uint32_t u) {
   }
   if (e == 255) return __longlong_as_double((long long)(sgn | 0x7FF0000000000000ull | ((uint64_t)m << 29)));
   return __longlong_as_double((long long)(sgn | ((uint64_t)(e - 127 + 1023) << 52) | ((uint64_t)m << 29)));
+}
+
+__device__ __noinline__ double f32_to_f64_rare(uint32_t u) { return f32_to_f64(u); }
+
+// f32_to_f64 for a batch: normal numbers and zeros without branches, the
+// general routine for subnormals, infinities and NaNs.
+template <int B>
+__device__ __forceinline__ void f32_to_f64_batch(const uint32_t (&u)[B], double (&d)[B]) {
+  unsigned slow_mask = 0;
+#pragma unroll
+  for (int j = 0; j < B; ++j) {
+    const uint32_t e = (u[j] >> 23) & 0xFFu;
+    const uint64_t sgn = (uint64_t)(u[j] >> 31) << 63;
+    const uint64_t bits = sgn | ((uint64_t)(e + 896u) << 52) | ((uint64_t)(u[j] & 0x7FFFFFu) << 29);
+    const bool zero = (u[j] << 1) == 0;
+    slow_mask |= (unsigned)(!zero && (e == 0 || e == 255)) << j;
+    d[j] = __longlong_as_double((long long)(zero ? sgn : bits));
+  }
+  if (slow_mask) {
+#pragma unroll
+    for (int j = 0; j < B; ++j)
+      if ((slow_mask >> j) & 1u) d[j] = f32_to_f64_rare(u[j]);
+  }
 }
 
 // Descriptor offset of slice tile `i`, K step `kk` (16-byte units).
@@ -647,20 +710,58 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     // all 256 epilogue threads meet here, whatever path they took
     asm volatile("bar.sync 1, 256;" ::: "memory");
     const int t = threadIdx.x - EPI_WARP0 * 32;
-    if (ok) {
-      // coalesced: consecutive lanes take consecutive columns of one row
-#pragma unroll 4
-      for (int idx = t; idx < TM * TN; idx += 256) {
-        const int r = idx / TN, c = idx % TN;
-        if (m0 + r >= p.M || n0 + c >= p.N) continue;
+    // Thread t writes column c = t % TN of rows t / TN, t / TN + 2, ...: the
+    // column's offset and exponent stay in registers, and each batch issues
+    // all of its shared-memory (or L2) loads before any global store, so the
+    // loads of a batch overlap instead of waiting behind the stores.
+    constexpr int RSTEP = 256 / TN;
+    constexpr int BATCH = 8;
+    static_assert(TM % (RSTEP * BATCH) == 0 && 256 % TN == 0, "epilogue row walk");
+    const int c = t % TN;
+    const bool col_ok = n0 + c < p.N;
+    const int64_t co = coff[c];
+    const int ce = cexp[c] - 36;
+    const int64_t acc_col = ((int64_t)b * p.M + m0) * p.N + n0 + c;   // wacc index of row 0
+    if (ok && col_ok) {
+#pragma unroll 1
+      for (int rb = t / TN; rb < TM; rb += RSTEP * BATCH) {
         if (KIND == MODE_SPLIT) {
-          const long long Rv = ((const long long*)tiles)[r * STAGE_LD + c];
-          if (args.ksplit > 1)
-            atomicAdd(args.wacc + ((int64_t)b * p.M + m0 + r) * p.N + n0 + c, (unsigned long long)Rv);
-          else
-            args.w[roffs[r] + coff[c]] = i64_scaled(Rv, rexps[r] + cexp[c] - 36);
+          long long Rv[BATCH];
+#pragma unroll
+          for (int j = 0; j < BATCH; ++j) Rv[j] = ((const long long*)tiles)[(rb + RSTEP * j) * STAGE_LD + c];
+          if (args.ksplit > 1) {
+#pragma unroll
+            for (int j = 0; j < BATCH; ++j) {
+              const int r = rb + RSTEP * j;
+              if (m0 + r < p.M) red_add_u64(args.wacc + acc_col + (int64_t)r * p.N, (unsigned long long)Rv[j]);
+            }
+          } else {
+            int64_t ro[BATCH];
+            int ex[BATCH];
+#pragma unroll
+            for (int j = 0; j < BATCH; ++j) {
+              ro[j] = roffs[rb + RSTEP * j];
+              ex[j] = rexps[rb + RSTEP * j] + ce;
+            }
+            double d[BATCH];
+            i64_scaled_batch<BATCH>(Rv, ex, d);
+#pragma unroll
+            for (int j = 0; j < BATCH; ++j)
+              if (m0 + rb + RSTEP * j < p.M) args.w[ro[j] + co] = d[j];
+          }
         } else {
-          args.w[roffs[r] + coff[c]] = f32_to_f64(((const uint32_t*)tiles)[r * STAGE_LD + c]);
+          uint32_t a[BATCH];
+          int64_t ro[BATCH];
+#pragma unroll
+          for (int j = 0; j < BATCH; ++j) {
+            a[j] = ((const uint32_t*)tiles)[(rb + RSTEP * j) * STAGE_LD + c];
+            ro[j] = roffs[rb + RSTEP * j];
+          }
+          double d[BATCH];
+          f32_to_f64_batch<BATCH>(a, d);
+#pragma unroll
+          for (int j = 0; j < BATCH; ++j)
+            if (m0 + rb + RSTEP * j < p.M) args.w[ro[j] + co] = d[j];
         }
       }
     }
@@ -673,14 +774,25 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         ctl->last = ok && atomicAdd(args.tile_ctr + tile_id, 1u) == (unsigned)args.ksplit - 1;
       }
       asm volatile("bar.sync 1, 256;" ::: "memory");
-      if (ctl->last) {
+      if (ctl->last && col_ok) {
         __threadfence();
-        for (int idx = t; idx < TM * TN; idx += 256) {
-          const int r = idx / TN, c = idx % TN;
-          if (m0 + r >= p.M || n0 + c >= p.N) continue;
-          const long long Rv =
-              (long long)__ldcg(args.wacc + ((int64_t)b * p.M + m0 + r) * p.N + n0 + c);
-          args.w[roffs[r] + coff[c]] = i64_scaled(Rv, rexps[r] + cexp[c] - 36);
+#pragma unroll 1
+        for (int rb = t / TN; rb < TM; rb += RSTEP * BATCH) {
+          long long Rv[BATCH];
+          int64_t ro[BATCH];
+          int ex[BATCH];
+#pragma unroll
+          for (int j = 0; j < BATCH; ++j) {
+            const int r = rb + RSTEP * j;
+            Rv[j] = m0 + r < p.M ? (long long)__ldcg(args.wacc + acc_col + (int64_t)r * p.N) : 0ll;
+            ro[j] = roffs[r];
+            ex[j] = rexps[r] + ce;
+          }
+          double d[BATCH];
+          i64_scaled_batch<BATCH>(Rv, ex, d);
+#pragma unroll
+          for (int j = 0; j < BATCH; ++j)
+            if (m0 + rb + RSTEP * j < p.M) args.w[ro[j] + co] = d[j];
         }
       }
     }

@@ -69,27 +69,35 @@ struct AxisMap {
   int z;
 };
 
-// Offset contribution of aligned index r at irrep Q.
-SC_HD int64_t axis_offset(const AxisMap& a, const GroupDesc& g, int Q, int64_t r) {
-  if (a.n == 0) return 0;
+// Offset contribution of aligned index r at irrep Q.  Axes below 2^31
+// entries (all practical ones) take 32-bit divisions.
+template <typename I>
+SC_HD int64_t axis_offset_t(const AxisMap& a, const GroupDesc& g, int Q, I r) {
   int64_t off = 0;
   for (int i = a.n - 1; i >= 0; --i) {
-    int64_t d = a.D[i];
-    int64_t b = r % d;
-    r /= d;
-    off += b * a.bstride[i];
+    const I d = (I)a.D[i];
+    const I q = r / d;
+    off += (int64_t)(r - q * d) * a.bstride[i];
+    r = q;
   }
   int partial = 0;
   for (int i = a.n - 2; i >= 0; --i) {
-    int q = (int)(r % g.order);
-    r /= g.order;
-    off += (int64_t)q * a.sstride[i];
-    partial = g_add(g, partial, g_signed(g, a.sign[i], q));
+    const I q = r / (I)g.order;
+    const int s = (int)(r - q * (I)g.order);
+    r = q;
+    off += (int64_t)s * a.sstride[i];
+    partial = g_add(g, partial, g_signed(g, a.sign[i], s));
   }
   int target = g_add(g, g_signed(g, a.qa, Q), a.z);
   int last = g_signed(g, a.sign[a.n - 1], g_add(g, target, g_neg(g, partial)));
   off += (int64_t)last * a.sstride[a.n - 1];
   return off;
+}
+
+SC_HD int64_t axis_offset(const AxisMap& a, const GroupDesc& g, int Q, int64_t r) {
+  if (a.n == 0) return 0;
+  if (a.size <= 0x7FFFFFFF) return axis_offset_t<uint32_t>(a, g, Q, (uint32_t)r);
+  return axis_offset_t<int64_t>(a, g, Q, r);
 }
 
 struct OperandMap {
@@ -120,8 +128,30 @@ struct Tables {
   int64_t* wcol;  // [n_q][N]
 };
 
-inline int64_t tables_entries(const Problem& p) {
+SC_HD int64_t tables_entries(const Problem& p) {
   return (int64_t)p.n_q * (2 * p.M + 2 * p.N + 2 * p.K);
+}
+
+// Exponent scan of the operand preparation: aligned rows are scanned in
+// tiles of 32 rows by at most kScanWidth columns, the K range cut into
+// `prep_scan_parts` column blocks (also enough of them to give the GPU some
+// 8192 tiles); each block writes its own partial row maxima ([parts][n_q *
+// (M + N)] int32 in the workspace, when parts > 1).
+constexpr int kScanWidth = 1024;
+inline int prep_scan_parts(const Problem& p) {
+  const int64_t row_tiles = ((p.M + 31) / 32 + (p.N + 31) / 32) * (int64_t)p.n_q;
+  const int64_t col_blocks = (p.K + 255) / 256;
+  int64_t parts = row_tiles > 0 ? (8192 + row_tiles - 1) / row_tiles : 1;
+  const int64_t by_width = (p.K + kScanWidth - 1) / kScanWidth;
+  if (parts < by_width) parts = by_width;
+  if (parts > col_blocks) parts = col_blocks;
+  if (parts > 64) parts = 64;
+  return parts < 1 ? 1 : (int)parts;
+}
+
+inline int64_t prep_partials_entries(const Problem& p) {
+  const int parts = prep_scan_parts(p);
+  return parts > 1 ? (int64_t)parts * p.n_q * (p.M + p.N) : 0;
 }
 
 // Device error word codes (first uint32 of the workspace).
@@ -144,7 +174,7 @@ cudaError_t launch_gemm_f64(const Problem& p, const double* u, const double* v, 
 cudaError_t launch_fill_zero(double* w, int64_t n, cudaStream_t st);
 cudaError_t launch_prep(const Problem& p, const Tables& t, bool split, int n_slices,
                         const double* u, const double* v, void* ua, void* va, int32_t* eu,
-                        int32_t* ev, int64_t kpad, unsigned* err, unsigned* barrier,
+                        int32_t* ev, int32_t* partials, int64_t kpad, unsigned* err, unsigned* barrier,
                         unsigned long long* zero64, int64_t zero64_n, unsigned* zero32,
                         int64_t zero32_n, cudaStream_t st);
 cudaError_t launch_gemm_split(const Problem& p, const Tables& t, int n_slices, const uint16_t* us,

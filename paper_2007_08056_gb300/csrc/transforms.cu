@@ -9,6 +9,8 @@
 // col_off(Q, c): constant work per element, pure data movement, bit-exact.
 #include <cstdint>
 
+#include <cuda_bf16.h>
+
 #include "symctr_internal.h"
 
 namespace symctr {
@@ -108,42 +110,53 @@ __global__ void __launch_bounds__(THREADS) align_kernel(Problem p, OperandMap m,
 
 constexpr int32_t kZeroRowExp = -2000;
 
-__device__ __forceinline__ int32_t exponent_of(double x, unsigned* bad) {
-  uint64_t bits = (uint64_t)__double_as_longlong(x);
-  int ef = (int)((bits >> 52) & 0x7FF);
-  uint64_t mant = bits & ((1ull << 52) - 1);
-  if (ef == 0x7FF) {
-    *bad = 1;
-    return kZeroRowExp;
-  }
-  if (ef != 0) return ef - 1023;
-  if (mant == 0) return kZeroRowExp;
-  return (63 - __clzll((long long)mant)) - 1074;
+// Row exponents, stored biased: E + kExpBias for a row whose largest entry
+// lies in [2^E, 2^(E+1)) (E clamped below at 8S - 1076, see row_key), 0 for an
+// all-zero row.
+constexpr int32_t kExpBias = 4096;
+constexpr int SCAN_COLS = 256;
+constexpr int SLICE_COLS = 64;
+constexpr int SLICE_GROUP = 4;   // 64-column sub-tiles per slice work unit
+
+// |x| as its IEEE bit pattern: the order of these integers is the order of
+// the magnitudes, so a row maximum needs only integer max operations.
+__device__ __forceinline__ uint64_t abs_bits(double x) {
+  return (uint64_t)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
 }
 
-// X = round(x * 2^(8S - 2 - E)), |X| <= 2^(8S-1).  Round half away from zero.
-__device__ __forceinline__ int64_t fixed_point(double x, int32_t E, int S) {
-  uint64_t bits = (uint64_t)__double_as_longlong(x);
-  int ef = (int)((bits >> 52) & 0x7FF);
-  uint64_t mant = bits & ((1ull << 52) - 1);
-  int ex;
-  if (ef != 0) {
-    mant |= 1ull << 52;
-    ex = ef - 1075;
-  } else {
-    ex = -1074;
+// Biased row exponent key from the largest |x| bit pattern of a row: 0 for an
+// all-zero row; nonfinite entries set `bad`.  E is clamped below at 8S - 1076:
+// a row whose largest entry is smaller holds only subnormals, which are exact
+// integers at that scale (multiples of 2^-1074), so nothing is lost, and every
+// entry then needs a right shift only (fixed_point).
+template <int S>
+__device__ __forceinline__ int32_t row_key(uint64_t ab, unsigned& bad) {
+  if (ab == 0) return 0;
+  if (ab >= 0x7FF0000000000000ull) {
+    bad = 1;
+    return 0;
   }
-  if (mant == 0 || E == kZeroRowExp) return 0;
-  int sh = ex + 8 * S - 2 - E;
-  uint64_t X;
-  if (sh >= 0) {
-    X = sh >= 63 ? 0 : (mant << sh);  // subnormal rows: |X| <= 2^(8S-1) still holds
-  } else {
-    int k = -sh;
-    X = k > 54 ? 0 : ((mant + (1ull << (k - 1))) >> k);
-  }
-  int64_t v = (int64_t)X;
-  return (bits >> 63) ? -v : v;
+  const int ef = (int)(ab >> 52);
+  const int e = ef != 0 ? ef - 1023 : (63 - __clzll((long long)ab)) - 1074;
+  return max(e, 8 * S - 1076) + kExpBias;
+}
+
+// X = round(x * 2^(8S - 2 - E)), |X| <= 2^(8S-1), round half away from zero,
+// given k0 = E + 1077 - 8S for the row (so that X = round(m * 2^-k) with
+// k = k0 - max(e_f, 1) >= 0 for the integer mantissa m and exponent field
+// e_f).  A zero row passes k0 >= 64 + 2047.  Selects only, no branches.
+__device__ __forceinline__ int64_t fixed_point(double x, int k0) {
+  const uint64_t bits = (uint64_t)__double_as_longlong(x);
+  const int ef = (int)((bits >> 52) & 0x7FF);
+  const uint64_t mant = (bits & ((1ull << 52) - 1)) | ((uint64_t)(ef != 0) << 52);
+  const int k = min(k0 - max(ef, 1), 63);
+  const uint64_t X = (mant + ((1ull << k) >> 1)) >> k;   // 0 once k >= 54
+  const uint64_t sm = 0ull - (bits >> 63);               // all ones for a negative entry
+  return (int64_t)((X ^ sm) - sm);
+}
+
+__device__ __forceinline__ int row_k0(int32_t key, int S) {
+  return key == 0 ? 4096 : key - kExpBias + 1077 - 8 * S;
 }
 
 // Balanced base-256 digits by byte extraction: with B = 0x80 * (256^S - 1)/255,
@@ -155,27 +168,26 @@ __host__ __device__ constexpr uint64_t digit_bias(int S) {
   return b;
 }
 
-// BF16 bits of (u - 128) * 2^(-8 i) for a biased digit u in [0, 256], with
-// full-rate operations only: 0x4B000000 | u is the float 2^23 + u, so one
-// subtraction gives u - 128 exactly; the scale is an exponent decrement.
-__device__ __forceinline__ uint32_t bf16_of_biased(uint32_t u, int i) {
-  const float f = __uint_as_float(0x4B000000u | u) - 8388736.0f;
-  const uint32_t b = __float_as_uint(f) >> 16;
-  return b ? b - ((uint32_t)i << 10) : 0u;
+// Slice i's value (a - 128) * 2^(-8 i) as a float, for the biased digit
+// a + 128 held in byte k = S-1-i of y (the top digit, which may be 256, is
+// everything above the low S-1 bytes).  The byte is moved under the exponent of
+// 2^23 by one byte permute, giving the float 2^23 + u; one FMA then scales by
+// 2^(-8 i) and subtracts (2^23 + 128) 2^(-8 i).  Product and sum are exact, so
+// the result is exact (and +0 for a zero digit).
+template <int S, int I>
+__device__ __forceinline__ float digit_value(uint64_t y) {
+  constexpr int k = S - 1 - I;
+  uint32_t w;
+  if (I == 0) {
+    w = 0x4B000000u | (uint32_t)(y >> (8 * k));
+  } else if (k < 4) {
+    w = __byte_perm((uint32_t)y, 0x4B000000u, 0x7540 | k);
+  } else {
+    w = __byte_perm((uint32_t)(y >> 32), 0x4B000000u, 0x7540 | (k - 4));
+  }
+  const float scale = __int_as_float((127 - 8 * I) << 23);
+  return __fmaf_rn(__uint_as_float(w), scale, -8388736.0f * scale);
 }
-
-__device__ __forceinline__ uint16_t digit_bf16(int a, int slice) {
-  if (a == 0) return 0;
-  float f = (float)a;                                  // exact, |a| <= 128
-  f = __fmul_rn(f, __int_as_float((127 - 8 * slice) << 23));  // * 2^(-8 slice), exact
-  return (uint16_t)(__float_as_uint(f) >> 16);         // low 16 bits are zero
-}
-
-// Row exponents, stored biased: E + kExpBias for a row whose largest entry
-// lies in [2^E, 2^(E+1)), 0 for an all-zero row.
-constexpr int32_t kExpBias = 4096;
-constexpr int SCAN_COLS = 256;
-constexpr int SLICE_COLS = 64;
 
 // Bounded grid-wide barrier of the cooperative prep launch (all CTAs are
 // co-resident).  `ctr` is zeroed before the launch; barrier number `phase`
@@ -206,12 +218,12 @@ __device__ __forceinline__ void grid_barrier(unsigned* ctr, unsigned phase, unsi
 struct PrepArgs {
   Problem p;
   Tables t;
-  int split;                 // 1: exponent scan + BF16 slices, 0: TF32 copy
-  int S;
   int64_t kpad;
+  int parts;                 // column blocks of the exponent scan (prep_scan_parts)
   const double* src[2];      // U, V standard reduced forms
   void* dst[2];              // slices (split) or float32 operands (TF32)
-  int32_t* exps[2];
+  int32_t* exps[2];          // biased row exponents read by the GEMM
+  int32_t* part[2];          // [parts][n_q * R] partial row maxima (parts > 1)
   bool fast_rows[2];
   bool pair_ok[2];           // column-contiguous with every offset of an even column even
   unsigned* err;
@@ -227,104 +239,113 @@ __device__ __forceinline__ void operand_dims(const Problem& p, int op, int64_t* 
   *Cn = p.K;
 }
 
-// One 32 x 256 tile of the exponent scan.
-__device__ void scan_tile(const PrepArgs& a, int op, int64_t tile, int64_t* roff, int64_t* coff,
-                          int32_t* rmax) {
+// Exponent scan of 32 rows over one column block, offsets computed in place
+// (the tables are not built yet): the offsets of up to kScanWidth columns at
+// once (independent computations, one exposed latency), then the loads.
+template <int S>
+__device__ void scan_tile(const PrepArgs& a, const OperandMap* maps, const GroupDesc& g, int op,
+                          uint32_t tile, int64_t* roff, int64_t* coff, unsigned long long* rmax) {
   const Problem& p = a.p;
   int64_t R, Cn;
   operand_dims(p, op, &R, &Cn);
-  const int64_t* rtab = op == 0 ? a.t.urow : a.t.vrow;
-  const int64_t* ctab = op == 0 ? a.t.ucol : a.t.vcol;
+  const OperandMap& m = maps[op];
   const double* src = a.src[op];
-  int32_t* exps = a.exps[op];
   const bool fast_rows = a.fast_rows[op];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  const int64_t rt = (R + TILE - 1) / TILE, ct = (Cn + SCAN_COLS - 1) / SCAN_COLS;
-  const int64_t b = tile / (rt * ct);
-  const int64_t rem = tile - b * rt * ct;
-  const int64_t r0 = (rem / ct) * TILE, c0 = (rem % ct) * SCAN_COLS;
+  const uint32_t P = (uint32_t)a.parts;
+  const int64_t width = (Cn + P - 1) / P;
+  const uint32_t rt = (uint32_t)((R + TILE - 1) / TILE);
+  const uint32_t b = tile / (rt * P);
+  const uint32_t rem = tile - b * rt * P;
+  const int64_t r0 = (int64_t)(rem / P) * TILE;
+  const uint32_t j = rem % P;
+  const int64_t cb = j * width, ce = min(Cn, cb + width);
+  const int Q = batch_irrep(p, (int)b);
   __syncthreads();
   if (threadIdx.x < TILE) {
-    int64_t r = r0 + threadIdx.x;
-    roff[threadIdx.x] = r < R ? rtab[b * R + r] : 0;
+    const int64_t r = r0 + threadIdx.x;
+    roff[threadIdx.x] = r < R ? axis_offset(m.rows, g, Q, r) : 0;
     rmax[threadIdx.x] = 0;
   }
-  {
-    int64_t c = c0 + threadIdx.x;
-    coff[threadIdx.x] = c < Cn ? ctab[b * Cn + c] : 0;
-  }
-  __syncthreads();
-  unsigned bad = 0;
   constexpr int PER = SCAN_COLS / (THREADS / 32);
-  if (fast_rows) {
-    const bool rok = r0 + tx < R;
-    int32_t mx = 0;
+  uint64_t mx = 0;   // fast rows: this thread's row (tx)
+  for (int64_t sb = cb; sb < ce; sb += kScanWidth) {
+    const int64_t se = min(ce, sb + kScanWidth);
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      double x[PER / 2];
+    for (int i = 0; i < kScanWidth / THREADS; ++i) {
+      const int64_t c = sb + threadIdx.x + i * THREADS;
+      coff[threadIdx.x + i * THREADS] = c < se ? axis_offset(m.cols, g, Q, c) : 0;
+    }
+    __syncthreads();
+    for (int64_t c0 = sb; c0 < se; c0 += SCAN_COLS) {
+      const int64_t* co = coff + (c0 - sb);
+      if (fast_rows) {
+        // lanes walk rows (contiguous), warps walk columns
+        const bool rok = r0 + tx < R;
+        const double* rowp = src + roff[tx];
 #pragma unroll
-      for (int i = 0; i < PER / 2; ++i) {
-        int cc = ty + (h * (PER / 2) + i) * (THREADS / 32);
-        x[i] = (rok && c0 + cc < Cn) ? src[roff[tx] + coff[cc]] : 0.0;
-      }
+        for (int h = 0; h < 2; ++h) {
+          double x[PER / 2];
 #pragma unroll
-      for (int i = 0; i < PER / 2; ++i) {
-        int32_t e = exponent_of(x[i], &bad);
-        mx = max(mx, e == kZeroRowExp ? 0 : e + kExpBias);
+          for (int i = 0; i < PER / 2; ++i) {
+            const int cc = ty + (h * (PER / 2) + i) * (THREADS / 32);
+            x[i] = (rok && c0 + cc < se) ? rowp[co[cc]] : 0.0;
+          }
+#pragma unroll
+          for (int i = 0; i < PER / 2; ++i) mx = max(mx, abs_bits(x[i]));
+        }
+      } else {
+        // lanes walk columns (contiguous), warps walk rows
+#pragma unroll
+        for (int h = 0; h < TILE / (THREADS / 32); ++h) {
+          const int rr = ty + h * (THREADS / 32);
+          const bool rok = r0 + rr < R;
+          const double* rowp = src + roff[rr];
+          double x[SCAN_COLS / 32];
+#pragma unroll
+          for (int i = 0; i < SCAN_COLS / 32; ++i) {
+            const int cc = tx + 32 * i;
+            x[i] = (rok && c0 + cc < se) ? rowp[co[cc]] : 0.0;
+          }
+          uint64_t v = 0;
+#pragma unroll
+          for (int i = 0; i < SCAN_COLS / 32; ++i) v = max(v, abs_bits(x[i]));
+          for (int o = 16; o > 0; o >>= 1) v = max(v, (uint64_t)__shfl_xor_sync(0xffffffffu, (unsigned long long)v, o));
+          if (tx == 0) rmax[rr] = max((uint64_t)rmax[rr], v);   // row rr belongs to this warp alone
+        }
       }
     }
-    atomicMax(&rmax[tx], mx);
-  } else {
-#pragma unroll
-    for (int rg = 0; rg < TILE / (THREADS / 32); ++rg) {
-      int rr = ty + rg * (THREADS / 32);
-      const bool rok = r0 + rr < R;
-      double x[SCAN_COLS / 32];
-#pragma unroll
-      for (int i = 0; i < SCAN_COLS / 32; ++i) {
-        int cc = tx + 32 * i;
-        x[i] = (rok && c0 + cc < Cn) ? src[roff[rr] + coff[cc]] : 0.0;
-      }
-      int32_t mx = 0;
-#pragma unroll
-      for (int i = 0; i < SCAN_COLS / 32; ++i) {
-        int32_t e = exponent_of(x[i], &bad);
-        mx = max(mx, e == kZeroRowExp ? 0 : e + kExpBias);
-      }
-      for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-      if (tx == 0) rmax[rr] = max(rmax[rr], mx);
-    }
+    __syncthreads();
   }
-  if (bad) atomicOr(a.err, (unsigned)DEVERR_NONFINITE);
+  if (fast_rows) atomicMax(&rmax[tx], (unsigned long long)mx);
   __syncthreads();
-  if (threadIdx.x < TILE && r0 + threadIdx.x < R && rmax[threadIdx.x] > 0)
-    atomicMax(&exps[b * R + r0 + threadIdx.x], rmax[threadIdx.x]);
+  if (threadIdx.x < TILE && r0 + threadIdx.x < R) {
+    unsigned bad = 0;
+    const int32_t key = row_key<S>(rmax[threadIdx.x], bad);
+    if (bad) atomicOr(a.err, (unsigned)DEVERR_NONFINITE);
+    int32_t* out = P > 1 ? a.part[op] + (int64_t)j * p.n_q * R : a.exps[op];
+    out[(int64_t)b * R + r0 + threadIdx.x] = key;
+  }
 }
 
-// Writes the S slices of two adjacent columns (c, c+1) of one row.
+// Writes the S slices of two adjacent columns (c, c+1) of one row: one
+// packed BF16 pair per slice (the conversion is exact, every digit value has
+// at most 8 significant bits).
+template <int S, int I = 0>
+__device__ __forceinline__ void put_digits(uint64_t y0, uint64_t y1, uint32_t* dst, int64_t stride) {
+  if constexpr (I < S) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(digit_value<S, I>(y0), digit_value<S, I>(y1));
+    dst[(int64_t)I * stride] = *reinterpret_cast<const uint32_t*>(&h);
+    put_digits<S, I + 1>(y0, y1, dst, stride);
+  }
+}
+
 template <int S>
-__device__ __forceinline__ void put_slices_pair(double x0, double x1, int32_t E, uint32_t* dst,
+__device__ __forceinline__ void put_slices_pair(double x0, double x1, int k0, uint32_t* dst,
                                                 int64_t stride) {
-  const uint64_t y0 = (uint64_t)(fixed_point(x0, E, S) + (int64_t)digit_bias(S));
-  const uint64_t y1 = (uint64_t)(fixed_point(x1, E, S) + (int64_t)digit_bias(S));
-#pragma unroll
-  for (int i = 0; i < S; ++i) {
-    const int k = S - 1 - i;  // byte position of slice i's digit
-    const uint32_t u0 = i == 0 ? (uint32_t)(y0 >> (8 * k)) : (uint32_t)(y0 >> (8 * k)) & 255u;
-    const uint32_t u1 = i == 0 ? (uint32_t)(y1 >> (8 * k)) : (uint32_t)(y1 >> (8 * k)) & 255u;
-    dst[(int64_t)i * stride] = bf16_of_biased(u0, i) | (bf16_of_biased(u1, i) << 16);
-  }
-}
-
-template <int S>
-__device__ __forceinline__ void put_slices_one(double x, int32_t E, uint16_t* dst, int64_t stride) {
-  const uint64_t y = (uint64_t)(fixed_point(x, E, S) + (int64_t)digit_bias(S));
-#pragma unroll
-  for (int i = 0; i < S; ++i) {
-    const int k = S - 1 - i;
-    const uint32_t u = i == 0 ? (uint32_t)(y >> (8 * k)) : (uint32_t)(y >> (8 * k)) & 255u;
-    dst[(int64_t)i * stride] = (uint16_t)bf16_of_biased(u, i);
-  }
+  const uint64_t y0 = (uint64_t)(fixed_point(x0, k0) + (int64_t)digit_bias(S));
+  const uint64_t y1 = (uint64_t)(fixed_point(x1, k0) + (int64_t)digit_bias(S));
+  put_digits<S>(y0, y1, dst, stride);
 }
 
 __device__ __forceinline__ float tf32_round(double x) {
@@ -333,13 +354,30 @@ __device__ __forceinline__ float tf32_round(double x) {
   return __uint_as_float(u);
 }
 
-// One 32 x 64 tile of the padded aligned operand.  Column-contiguous operands
-// are read along the columns straight from global memory (16-byte loads when
-// every offset is even), row-contiguous ones go through shared memory so that
-// both the gather and the slice stores are coalesced.
 template <int S>
-__device__ void slice_tile(const PrepArgs& a, int op, int64_t tile, int64_t* roff, int64_t* coff,
-                           int32_t* rexp, double (*tilebuf)[SLICE_COLS + 1]) {
+__device__ __forceinline__ void put_pair(const PrepArgs& a, int op, double x0, double x1, int k0,
+                                         int64_t e_at, int64_t slice_stride) {
+  if constexpr (S > 0) {
+    put_slices_pair<S>(x0, x1, k0, (uint32_t*)a.dst[op] + e_at / 2, slice_stride / 2);
+  } else {
+    float2 f;
+    f.x = tf32_round(x0);
+    f.y = tf32_round(x1);
+    reinterpret_cast<float2*>(a.dst[op])[e_at / 2] = f;
+  }
+}
+
+// One work unit of the padded aligned operand: 32 rows by SLICE_GROUP x 64
+// columns (S slices; S = 0: the TF32 copy).  Column-contiguous operands are
+// read along the columns straight from global memory (16-byte loads when every
+// offset is even), row-contiguous ones go through shared memory, 64 columns at
+// a time, so that both the gather and the slice stores are coalesced.  The row
+// exponents are the maxima over the scan's column blocks; the units of the
+// first column group store them for the GEMM.
+template <int S>
+__device__ void slice_unit(const PrepArgs& a, int op, uint32_t unit, int64_t* roff, int64_t* coff,
+                           int32_t* rk0, double (*tilebuf)[SLICE_COLS + 1]) {
+  constexpr int UCOLS = SLICE_GROUP * SLICE_COLS;
   const Problem& p = a.p;
   int64_t R, Cn;
   operand_dims(p, op, &R, &Cn);
@@ -349,164 +387,171 @@ __device__ void slice_tile(const PrepArgs& a, int op, int64_t tile, int64_t* rof
   const double* src = a.src[op];
   const bool fast_rows = a.fast_rows[op];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  const int64_t rt = (R + TILE - 1) / TILE, ct = (kpad + SLICE_COLS - 1) / SLICE_COLS;
-  const int64_t b = tile / (rt * ct);
-  const int64_t rem = tile - b * rt * ct;
-  const int64_t r0 = (rem / ct) * TILE, c0 = (rem % ct) * SLICE_COLS;
-  const bool split = a.split;
+  const uint32_t rt = (uint32_t)((R + TILE - 1) / TILE), ct = (uint32_t)((kpad + UCOLS - 1) / UCOLS);
+  const uint32_t b = unit / (rt * ct);
+  const uint32_t rem = unit - b * rt * ct;
+  const int64_t r0 = (int64_t)(rem / ct) * TILE, cu = (int64_t)(rem % ct) * UCOLS;
   const int64_t slice_stride = (int64_t)p.n_q * R * kpad;   // elements
-  if (!fast_rows) {
-    // lanes walk column pairs; warps walk rows; no shared memory
-    const int64_t c = c0 + 2 * tx;
-    const bool pair = a.pair_ok[op];
-    int64_t co0 = 0, co1 = 0;
-    if (c < Cn) co0 = ctab[b * Cn + c];
-    if (!pair && c + 1 < Cn) co1 = ctab[b * Cn + c + 1];
-#pragma unroll
-    for (int rg = 0; rg < TILE / (THREADS / 32); ++rg) {
-      const int64_t r = r0 + ty + rg * (THREADS / 32);
-      if (r >= R || c >= kpad) continue;
-      const int64_t ro = rtab[b * R + r];
-      double x0 = 0.0, x1 = 0.0;
-      if (pair) {
-        if (c < Cn) {
-          const double2 v2 = *reinterpret_cast<const double2*>(src + ro + co0);
-          x0 = v2.x;
-          x1 = v2.y;
+  const int64_t brow = (int64_t)b * R;
+  __syncthreads();
+  if (threadIdx.x < TILE) {
+    const int64_t r = r0 + threadIdx.x;
+    roff[threadIdx.x] = r < R ? rtab[brow + r] : 0;
+    if constexpr (S > 0) {
+      int32_t key = 0;
+      if (r < R) {
+        if (a.parts > 1) {
+          const int64_t nR = (int64_t)p.n_q * R;
+          for (int j = 0; j < a.parts; ++j) key = max(key, a.part[op][j * nR + brow + r]);
+          if (cu == 0) a.exps[op][brow + r] = key;
+        } else {
+          key = a.exps[op][brow + r];
         }
-      } else {
-        if (c < Cn) x0 = src[ro + co0];
-        if (c + 1 < Cn) x1 = src[ro + co1];
       }
-      const int64_t e_at = (b * R + r) * kpad + c;
-      if (split) {
-        const int32_t st = a.exps[op][b * R + r];
-        const int32_t E = st == 0 ? kZeroRowExp : st - kExpBias;
-        put_slices_pair<S>(x0, x1, E, (uint32_t*)a.dst[op] + e_at / 2, slice_stride / 2);
-      } else {
-        float2 f;
-        f.x = tf32_round(x0);
-        f.y = tf32_round(x1);
-        reinterpret_cast<float2*>(a.dst[op])[e_at / 2] = f;
+      rk0[threadIdx.x] = row_k0(key, S);
+    }
+  } else if (fast_rows) {
+    for (int i = threadIdx.x - TILE; i < UCOLS; i += THREADS - TILE) {
+      const int64_t c = cu + i;
+      coff[i] = c < Cn ? ctab[(int64_t)b * Cn + c] : 0;
+    }
+  }
+  __syncthreads();
+  if (!fast_rows) {
+    // lanes walk column pairs, warps walk rows; no shared-memory transpose
+    const bool pair = a.pair_ok[op];
+#pragma unroll 1
+    for (int sub = 0; sub < SLICE_GROUP; ++sub) {
+      const int64_t c = cu + sub * SLICE_COLS + 2 * tx;
+      if (c >= kpad) break;
+      int64_t co0 = 0, co1 = 0;
+      if (c < Cn) co0 = ctab[(int64_t)b * Cn + c];
+      if (!pair && c + 1 < Cn) co1 = ctab[(int64_t)b * Cn + c + 1];
+#pragma unroll
+      for (int rg = 0; rg < TILE / (THREADS / 32); ++rg) {
+        const int rr = ty + rg * (THREADS / 32);
+        const int64_t r = r0 + rr;
+        if (r >= R) continue;
+        const double* rowp = src + roff[rr];
+        double x0 = 0.0, x1 = 0.0;
+        if (pair) {
+          if (c < Cn) {
+            const double2 v2 = *reinterpret_cast<const double2*>(rowp + co0);
+            x0 = v2.x;
+            x1 = v2.y;
+          }
+        } else {
+          if (c < Cn) x0 = rowp[co0];
+          if (c + 1 < Cn) x1 = rowp[co1];
+        }
+        put_pair<S>(a, op, x0, x1, S > 0 ? rk0[rr] : 0, (brow + r) * kpad + c, slice_stride);
       }
     }
     return;
   }
-  __syncthreads();
-  if (threadIdx.x < TILE) {
-    int64_t r = r0 + threadIdx.x;
-    roff[threadIdx.x] = r < R ? rtab[b * R + r] : 0;
-    if (split) {
-      int32_t st = r < R ? a.exps[op][b * R + r] : 0;
-      rexp[threadIdx.x] = st == 0 ? kZeroRowExp : st - kExpBias;
-    }
-  } else if (threadIdx.x < TILE + SLICE_COLS) {
-    int64_t c = c0 + threadIdx.x - TILE;
-    coff[threadIdx.x - TILE] = c < Cn ? ctab[b * Cn + c] : 0;
-  }
-  __syncthreads();
-  {
-    double x[SLICE_COLS / (THREADS / 32)];
-    const bool rok = r0 + tx < R;
+  const bool rok = r0 + tx < R;
+  const double* rowp = src + roff[tx];
+#pragma unroll 1
+  for (int sub = 0; sub < SLICE_GROUP; ++sub) {
+    const int64_t c0 = cu + sub * SLICE_COLS;
+    if (c0 >= kpad) break;
+    if (sub > 0) __syncthreads();   // the previous sub-tile's reads of tilebuf are done
+    {
+      double x[SLICE_COLS / (THREADS / 32)];
 #pragma unroll
-    for (int i = 0; i < SLICE_COLS / (THREADS / 32); ++i) {
-      int cc = ty + i * (THREADS / 32);
-      x[i] = (rok && c0 + cc < Cn) ? src[roff[tx] + coff[cc]] : 0.0;
-    }
+      for (int i = 0; i < SLICE_COLS / (THREADS / 32); ++i) {
+        const int cc = ty + i * (THREADS / 32);
+        x[i] = (rok && c0 + cc < Cn) ? rowp[coff[sub * SLICE_COLS + cc]] : 0.0;
+      }
 #pragma unroll
-    for (int i = 0; i < SLICE_COLS / (THREADS / 32); ++i) tilebuf[tx][ty + i * (THREADS / 32)] = x[i];
-  }
-  __syncthreads();
-  // each thread: one row, two adjacent columns -> one uint32 per slice
-  for (int rr = ty; rr < TILE; rr += THREADS / 32) {
-    int64_t r = r0 + rr, c = c0 + 2 * tx;
-    if (r >= R || c >= kpad) continue;
-    const int64_t e_at = (b * R + r) * kpad + c;
-    if (split) {
-      put_slices_pair<S>(tilebuf[rr][2 * tx], tilebuf[rr][2 * tx + 1], rexp[rr],
-                         (uint32_t*)a.dst[op] + e_at / 2, slice_stride / 2);
-    } else {
-      float2 f;
-      f.x = tf32_round(tilebuf[rr][2 * tx]);
-      f.y = tf32_round(tilebuf[rr][2 * tx + 1]);
-      reinterpret_cast<float2*>(a.dst[op])[e_at / 2] = f;
+      for (int i = 0; i < SLICE_COLS / (THREADS / 32); ++i) tilebuf[tx][ty + i * (THREADS / 32)] = x[i];
+    }
+    __syncthreads();
+    // each thread: one row, two adjacent columns -> one uint32 per slice
+#pragma unroll
+    for (int rg = 0; rg < TILE / (THREADS / 32); ++rg) {
+      const int rr = ty + rg * (THREADS / 32);
+      const int64_t r = r0 + rr, c = c0 + 2 * tx;
+      if (r >= R || c >= kpad) continue;
+      put_pair<S>(a, op, tilebuf[rr][2 * tx], tilebuf[rr][2 * tx + 1], S > 0 ? rk0[rr] : 0,
+                  (brow + r) * kpad + c, slice_stride);
     }
   }
 }
 
 // Operand preparation of one contraction in one cooperative launch:
-//   phase 0  offset tables of the six index maps; zero the row exponents and
-//            the split-K accumulators;
-//   phase 1  (split form) per-row exponent maxima of U and V;
+//   phase 1  offset tables of the six index maps, zeroed split-K accumulators,
+//            and (split form) the per-row exponent maxima of U and V;
 //   phase 2  BF16 slices (split) or TF32 copies of U and V.
+template <int S>
 __global__ void __launch_bounds__(THREADS, 4) prep_kernel(PrepArgs a) {
-  __shared__ int64_t roff[TILE], coff[SCAN_COLS];
-  __shared__ int32_t rbuf[TILE];
+  __shared__ int64_t roff[TILE], coff[kScanWidth];
+  __shared__ unsigned long long rmax[TILE];
+  __shared__ int32_t rk0[TILE];
   __shared__ double tilebuf[TILE][SLICE_COLS + 1];
+  // the index maps and the group in shared memory: the offset computations
+  // index them with run-time subscripts
+  __shared__ OperandMap maps[3];
+  __shared__ GroupDesc g;
   const Problem& p = a.p;
+  {
+    static_assert(sizeof(OperandMap) % 4 == 0 && sizeof(GroupDesc) % 4 == 0, "word copy");
+    constexpr int nw = (int)(sizeof(OperandMap) / 4);
+    for (int i = threadIdx.x; i < 3 * nw + (int)(sizeof(GroupDesc) / 4); i += THREADS) {
+      uint32_t v;
+      if (i < nw) v = reinterpret_cast<const uint32_t*>(&p.u)[i];
+      else if (i < 2 * nw) v = reinterpret_cast<const uint32_t*>(&p.v)[i - nw];
+      else if (i < 3 * nw) v = reinterpret_cast<const uint32_t*>(&p.w)[i - 2 * nw];
+      else v = reinterpret_cast<const uint32_t*>(&p.g)[i - 3 * nw];
+      if (i < 3 * nw) reinterpret_cast<uint32_t*>(maps)[i] = v;
+      else reinterpret_cast<uint32_t*>(&g)[i - 3 * nw] = v;
+    }
+  }
+  __syncthreads();
   const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
   const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  // phase 0
   {
-    const int64_t segs[6] = {p.M, p.K, p.N, p.K, p.M, p.N};
-    int64_t* dsts[6] = {a.t.urow, a.t.ucol, a.t.vrow, a.t.vcol, a.t.wrow, a.t.wcol};
-    int64_t total = 0;
-    for (int i = 0; i < 6; ++i) total += segs[i] * p.n_q;
+    // one grid-stride walk over the six tables, which lie end to end in the
+    // order U rows, U cols, V rows, V cols, W rows, W cols
+    const int64_t nq = p.n_q;
+    const int64_t total = tables_entries(p);
     for (int64_t e = gtid; e < total; e += gthreads) {
-      int64_t rem = e;
+      int64_t r = e, len = 0;
       int which = 0;
-      while (rem >= segs[which] * p.n_q) {
-        rem -= segs[which] * p.n_q;
-        ++which;
+      for (; which < 6; ++which) {
+        len = which == 0 || which == 4 ? p.M : which == 2 || which == 5 ? p.N : p.K;
+        if (r < nq * len) break;
+        r -= nq * len;
       }
-      int64_t b = rem / segs[which], r = rem % segs[which];
-      int Q = batch_irrep(p, (int)b);
-      const AxisMap& m = which == 0 ? p.u.rows : which == 1 ? p.u.cols : which == 2 ? p.v.rows
-                       : which == 3 ? p.v.cols : which == 4 ? p.w.rows : p.w.cols;
-      dsts[which][rem] = axis_offset(m, p.g, Q, r);
+      const AxisMap& m = (which & 1) ? maps[which >> 1].cols : maps[which >> 1].rows;
+      const int64_t b = r / len;
+      a.t.urow[e] = axis_offset(m, g, batch_irrep(p, (int)b), r - b * len);
     }
-    if (a.split) {
-      for (int64_t e = gtid; e < (int64_t)p.n_q * p.M; e += gthreads) a.exps[0][e] = 0;
-      for (int64_t e = gtid; e < (int64_t)p.n_q * p.N; e += gthreads) a.exps[1][e] = 0;
+    for (int64_t i = gtid; i < a.zero64_n; i += gthreads) a.zero64[i] = 0ull;
+    for (int64_t i = gtid; i < a.zero32_n; i += gthreads) a.zero32[i] = 0u;
+  }
+  if (S > 0) {
+    const uint32_t tiles0 = (uint32_t)(((p.M + TILE - 1) / TILE) * a.parts * p.n_q);
+    const uint32_t tiles1 = (uint32_t)(((p.N + TILE - 1) / TILE) * a.parts * p.n_q);
+    for (uint32_t t = blockIdx.x; t < tiles0 + tiles1; t += gridDim.x) {
+      const int op = t < tiles0 ? 0 : 1;
+      scan_tile<S>(a, maps, g, op, op == 0 ? t : t - tiles0, roff, coff, rmax);
     }
-    for (int64_t e = gtid; e < a.zero64_n; e += gthreads) a.zero64[e] = 0ull;
-    for (int64_t e = gtid; e < a.zero32_n; e += gthreads) a.zero32[e] = 0u;
   }
   grid_barrier(a.barrier, 1, a.err);
-  unsigned next = 2;
-  if (a.split) {
-    int64_t tiles[2];
-    for (int op = 0; op < 2; ++op) {
-      int64_t R, Cn;
-      operand_dims(p, op, &R, &Cn);
-      tiles[op] = ((R + TILE - 1) / TILE) * ((Cn + SCAN_COLS - 1) / SCAN_COLS) * p.n_q;
-    }
-    for (int64_t t = blockIdx.x; t < tiles[0] + tiles[1]; t += gridDim.x) {
-      int op = t < tiles[0] ? 0 : 1;
-      scan_tile(a, op, op == 0 ? t : t - tiles[0], roff, coff, rbuf);
-    }
-    grid_barrier(a.barrier, next++, a.err);
-  }
   // the GEMM that consumes these operands may start its setup now
   asm volatile("griddepcontrol.launch_dependents;");
   {
-    int64_t tiles[2];
+    constexpr int UCOLS = SLICE_GROUP * SLICE_COLS;
+    uint32_t units[2];
     for (int op = 0; op < 2; ++op) {
       int64_t R, Cn;
       operand_dims(p, op, &R, &Cn);
-      tiles[op] = ((R + TILE - 1) / TILE) * ((a.kpad + SLICE_COLS - 1) / SLICE_COLS) * p.n_q;
+      units[op] = (uint32_t)(((R + TILE - 1) / TILE) * ((a.kpad + UCOLS - 1) / UCOLS) * p.n_q);
     }
-    for (int64_t t = blockIdx.x; t < tiles[0] + tiles[1]; t += gridDim.x) {
-      int op = t < tiles[0] ? 0 : 1;
-      int64_t tt = op == 0 ? t : t - tiles[0];
-      switch (a.split ? a.S : 1) {
-        case 1: slice_tile<1>(a, op, tt, roff, coff, rbuf, tilebuf); break;
-        case 2: slice_tile<2>(a, op, tt, roff, coff, rbuf, tilebuf); break;
-        case 3: slice_tile<3>(a, op, tt, roff, coff, rbuf, tilebuf); break;
-        case 4: slice_tile<4>(a, op, tt, roff, coff, rbuf, tilebuf); break;
-        case 5: slice_tile<5>(a, op, tt, roff, coff, rbuf, tilebuf); break;
-        default: slice_tile<6>(a, op, tt, roff, coff, rbuf, tilebuf); break;
-      }
+    for (uint32_t t = blockIdx.x; t < units[0] + units[1]; t += gridDim.x) {
+      const int op = t < units[0] ? 0 : 1;
+      slice_unit<S>(a, op, op == 0 ? t : t - units[0], roff, coff, rk0, tilebuf);
     }
   }
 }
@@ -552,37 +597,53 @@ cudaError_t launch_align_f64(const Problem& p, int operand, int direction, const
 
 cudaError_t launch_prep(const Problem& p, const Tables& t, bool split, int n_slices,
                         const double* u, const double* v, void* ua, void* va, int32_t* eu,
-                        int32_t* ev, int64_t kpad, unsigned* err, unsigned* barrier,
+                        int32_t* ev, int32_t* partials, int64_t kpad, unsigned* err, unsigned* barrier,
                         unsigned long long* zero64, int64_t zero64_n, unsigned* zero32,
                         int64_t zero32_n, cudaStream_t st) {
-  static int max_blocks = 0;
-  if (max_blocks == 0) {
+  const int S = split ? n_slices : 0;
+  if (S < 0 || S > kMaxSlices) return cudaErrorInvalidValue;
+  void (*kern)(PrepArgs) = nullptr;
+  switch (S) {
+    case 0: kern = prep_kernel<0>; break;
+    case 1: kern = prep_kernel<1>; break;
+    case 2: kern = prep_kernel<2>; break;
+    case 3: kern = prep_kernel<3>; break;
+    case 4: kern = prep_kernel<4>; break;
+    case 5: kern = prep_kernel<5>; break;
+    default: kern = prep_kernel<6>; break;
+  }
+  static int max_blocks[kMaxSlices + 1] = {};
+  if (max_blocks[S] == 0) {
     int dev = 0, sms = 0, per = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, prep_kernel, THREADS, 0);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, THREADS, 0);
     if (e != cudaSuccess) return e;
-    max_blocks = sms * (per < 4 ? per : 4);
+    max_blocks[S] = sms * (per < 4 ? per : 4);
   }
   int64_t work = 0;
   {
     int64_t rt_u = (p.M + TILE - 1) / TILE, rt_v = (p.N + TILE - 1) / TILE;
-    int64_t ct = (kpad + SLICE_COLS - 1) / SLICE_COLS;
+    int64_t ct = (kpad + SLICE_GROUP * SLICE_COLS - 1) / (SLICE_GROUP * SLICE_COLS);
     work = (rt_u + rt_v) * ct * p.n_q;
+    if (work > 0xFFFFFFFFll / 2 || (rt_u + rt_v) * (int64_t)prep_scan_parts(p) * p.n_q > 0xFFFFFFFFll / 2)
+      return cudaErrorInvalidValue;
   }
-  int grid = (int)(work < max_blocks ? (work > 0 ? work : 1) : max_blocks);
+  int grid = (int)(work < max_blocks[S] ? (work > 0 ? work : 1) : max_blocks[S]);
   PrepArgs a;
   a.p = p;
   a.t = t;
-  a.split = split ? 1 : 0;
-  a.S = n_slices;
   a.kpad = kpad;
+  a.parts = S > 0 ? prep_scan_parts(p) : 1;
+  if (a.parts > 1 && !partials) return cudaErrorInvalidValue;
   a.src[0] = u;
   a.src[1] = v;
   a.dst[0] = ua;
   a.dst[1] = va;
   a.exps[0] = eu;
   a.exps[1] = ev;
+  a.part[0] = partials;
+  a.part[1] = partials ? partials + (int64_t)a.parts * p.n_q * p.M : nullptr;
   a.fast_rows[0] = rows_fast(p.u);
   a.fast_rows[1] = rows_fast(p.v);
   a.pair_ok[0] = !a.fast_rows[0] && pairs_aligned(p.u);
@@ -594,7 +655,7 @@ cudaError_t launch_prep(const Problem& p, const Tables& t, bool split, int n_sli
   a.zero32 = zero32;
   a.zero32_n = zero32_n;
   void* params[] = {&a};
-  cudaError_t e = cudaLaunchCooperativeKernel((const void*)prep_kernel, dim3(grid), dim3(THREADS),
+  cudaError_t e = cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(THREADS),
                                               params, 0, st);
   ++g_kernel_launches;
   return e;
