@@ -163,6 +163,28 @@ class Clocks:
 
 
 # ---------------------------------------------------------------------------
+# replicas: every rank runs the whole step on its own GPU (the contraction has
+# no exchange step); the job time is the slowest rank's
+# ---------------------------------------------------------------------------
+
+def max_over_ranks(ms, world, device):
+    """The largest per-step time over all ranks (every rank returns it)."""
+    if world <= 1:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    torch.distributed.barrier()
+    return float(t.item())
+
+
+def replicas_value(flops_per_step, ms, world):
+    """Whole-job useful TFLOP/s: every rank completes one step of
+    `flops_per_step` in at most `ms` milliseconds."""
+    return world * flops_per_step / (ms * 1e-3) / 1e12
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
 
@@ -328,13 +350,8 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
     for pl in plans:
         pl.check_device_error()
-    ms = statistics.mean(times)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-        torch.distributed.barrier()
-    value = world * flops / (ms * 1e-3) / 1e12
+    ms = max_over_ranks(statistics.mean(times), world, dev)
+    value = replicas_value(flops, ms, world)
 
     # per-kernel phases (averaged over the timed steps)
     prep = [statistics.mean(ph[i][0] for ph in phases) for i in range(len(plans))]
@@ -369,11 +386,7 @@ def run_ours(args, rank, world):
         o = step(*dins)
         hout.copy_(o, non_blocking=True)
     t_e2e, _ = timed(e2e_step, args.steps, args.warmup)
-    ms_e2e = statistics.mean(t_e2e)
-    if world > 1:
-        t = torch.tensor([ms_e2e], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_e2e = float(t.item())
+    ms_e2e = max_over_ranks(statistics.mean(t_e2e), world, dev)
 
     pk = peaks()
     roofs = rooflines(args, plans, prep, gemm, pk)
@@ -405,7 +418,7 @@ def run_ours(args, rank, world):
         "roofline_other": other[0] if other else None,
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
-        "e2e": {"value": round(world * flops / (ms_e2e * 1e-3) / 1e12, 4), "unit": "TFLOP/s",
+        "e2e": {"value": round(replicas_value(flops, ms_e2e, world), 4), "unit": "TFLOP/s",
                 "ms_per_step": round(ms_e2e, 4),
                 "h2d_bytes_per_step": int(sum(x.nbytes for x in inputs_host)),
                 "d2h_bytes_per_step": int(out.numel() * 8)},
