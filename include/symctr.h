@@ -32,8 +32,11 @@
  *
  * Conventions of every call
  *   Ownership : the caller owns every device pointer, the workspace and the
- *               stream.  A plan owns host metadata only; no call allocates
- *               device memory.
+ *               stream.  A plan owns host memory only: its metadata and, for
+ *               the tensor-core forms, the offset tables of the aligned forms
+ *               (computed at plan creation, page-locked on the first
+ *               contraction and copied into the workspace by every
+ *               contraction).  No call allocates device memory.
  *   Errors    : every call returns a status and never throws across the ABI.
  *               Kernels never trap: a device-side failure (a bounded wait that
  *               expired, a non-finite input) is recorded in the first word of
@@ -202,6 +205,9 @@ SYMCTR_API const char* symctr_status_string(symctr_status status);
 /* Text of the last error raised on the calling host thread (empty if none). */
 SYMCTR_API const char* symctr_last_error_detail(void);
 
+/* Release a plan (NULL is ignored).  If its offset tables were page-locked,
+ * this first waits for all work on the current device (cudaDeviceSynchronize),
+ * since copies from them may still be queued. */
 SYMCTR_API void symctr_plan_destroy(symctr_plan* plan);
 
 #ifdef __cplusplus

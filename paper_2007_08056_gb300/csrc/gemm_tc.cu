@@ -506,17 +506,24 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
+  // W's offset tables are constants of the plan: read before the wait.
+  if (threadIdx.x >= EPI_WARP0 * 32 && threadIdx.x < EPI_WARP0 * 32 + TN) {
+    const int c = threadIdx.x - EPI_WARP0 * 32;
+    const int64_t n = n0 + c, m = m0 + c;
+    coff[c] = n < p.N ? args.wcol[(int64_t)b * p.N + n] : 0;
+    roffs[c] = m < p.M ? args.wrow[(int64_t)b * p.M + m] : 0;
+  }
   // Launched as a programmatic dependent of the operand preparation: the setup
   // above overlaps its tail; everything below reads its outputs.
   asm volatile("griddepcontrol.wait;" ::: "memory");
-  if (threadIdx.x >= EPI_WARP0 * 32 && threadIdx.x < EPI_WARP0 * 32 + TN) {
-    int c = threadIdx.x - EPI_WARP0 * 32;
-    int64_t n = n0 + c;
-    coff[c] = n < p.N ? args.wcol[(int64_t)b * p.N + n] : 0;
-    cexp[c] = (KIND == MODE_SPLIT && n < p.N) ? args.ev[(int64_t)b * p.N + n] - kExpBias : 0;
-    int64_t m = m0 + c;
-    roffs[c] = m < p.M ? args.wrow[(int64_t)b * p.M + m] : 0;
-    rexps[c] = (KIND == MODE_SPLIT && m < p.M) ? args.eu[(int64_t)b * p.M + m] - kExpBias : 0;
+  if (KIND == MODE_SPLIT && threadIdx.x >= EPI_WARP0 * 32 && threadIdx.x < EPI_WARP0 * 32 + TN) {
+    const int c = threadIdx.x - EPI_WARP0 * 32;
+    const int64_t n = n0 + c, m = m0 + c;
+    cexp[c] = n < p.N ? args.ev[(int64_t)b * p.N + n] - kExpBias : 0;
+    rexps[c] = m < p.M ? args.eu[(int64_t)b * p.M + m] - kExpBias : 0;
+  } else if (threadIdx.x >= EPI_WARP0 * 32 && threadIdx.x < EPI_WARP0 * 32 + TN) {
+    cexp[threadIdx.x - EPI_WARP0 * 32] = 0;
+    rexps[threadIdx.x - EPI_WARP0 * 32] = 0;
   }
   tc_fence_before();
   __syncthreads();

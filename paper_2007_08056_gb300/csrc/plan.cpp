@@ -13,6 +13,7 @@
 // (the last follows by eliminating Q, as in the proof of Sec. 2.3).
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -145,6 +146,12 @@ struct symctr_plan {
   bool prof = false;
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   mutable int last_launches = 0;
+  // offset tables of all irreps (tensor-core forms), computed once on the host
+  // in the workspace layout of a single pass; page-locked on first use
+  std::vector<int64_t> htab;
+  mutable std::once_flag pin_once;
+  mutable bool pinned = false;
+  mutable const int64_t* dtab = nullptr;   // device view of the page-locked tables
 };
 
 namespace {
@@ -401,6 +408,23 @@ symctr_status build(const char* einsum, int n_moduli, const int32_t* moduli, con
     return bail(SYMCTR_ERR_ARGUMENT, "split form needs at least 2 slices");
   P->kpad = round_up(pr.K, kKBlock);
   pr.q_base = 0;
+  if (P->tensor_core) {
+    // the six offset tables [U rows | U cols | V rows | V cols | W rows | W cols],
+    // each [n_q][extent]: the same function of the plan on every call
+    const int64_t total = tables_entries(pr);
+    if (total > (int64_t)1 << 28) return bail(SYMCTR_ERR_OVERFLOW, "offset tables too large");
+    try {
+      P->htab.resize((size_t)total);
+    } catch (const std::bad_alloc&) {
+      return bail(SYMCTR_ERR_OVERFLOW, "offset tables: host allocation failed");
+    }
+    int64_t* t = P->htab.data();
+    const AxisMap* maps[6] = {&pr.u.rows, &pr.u.cols, &pr.v.rows, &pr.v.cols, &pr.w.rows, &pr.w.cols};
+    const int64_t ext[6] = {pr.M, pr.K, pr.N, pr.K, pr.M, pr.N};
+    for (int k = 0; k < 6; ++k)
+      for (int b = 0; b < pr.n_q; ++b)
+        for (int64_t r = 0; r < ext[k]; ++r) *t++ = axis_offset(*maps[k], pr.g, batch_irrep(pr, b), r);
+  }
   {
     Layout full = make_layout(pr, P->tensor_core, prec, P->n_slices, P->kpad);
     if (!full.ok) return bail(SYMCTR_ERR_OVERFLOW, "aligned operand too large");
@@ -495,6 +519,18 @@ symctr_status run_contract_body(const symctr_plan* P, const double* u, const dou
   }
   unsigned* barrier = (unsigned*)(base + 64);
   const bool split = P->prec == SYMCTR_SPLIT_BF16;
+  // page-lock the host tables once, so that their copies are plain DMA reads
+  // (without it they are staged through pageable memory, also correct)
+  std::call_once(P->pin_once, [P] {
+    if (!P->htab.empty() &&
+        cudaHostRegister((void*)P->htab.data(), P->htab.size() * sizeof(int64_t),
+                         cudaHostRegisterPortable | cudaHostRegisterMapped) == cudaSuccess) {
+      P->pinned = true;
+      void* d = nullptr;
+      if (cudaHostGetDevicePointer(&d, (void*)P->htab.data(), 0) == cudaSuccess) P->dtab = (const int64_t*)d;
+    }
+    cudaGetLastError();
+  });
   for (int q0 = 0; q0 < pr.n_q; q0 += per_pass) {
     Problem pc = pr;
     if (per_pass < pr.n_q) {
@@ -507,13 +543,40 @@ symctr_status run_contract_body(const symctr_plan* P, const double* u, const dou
     }
     const Layout L = make_layout(pc, true, P->prec, P->n_slices, P->kpad);
     Tables tab;
-    int64_t* t0 = (int64_t*)(base + L.off_tab);
-    tab.urow = t0;
-    tab.ucol = tab.urow + (int64_t)pc.n_q * pc.M;
-    tab.vrow = tab.ucol + (int64_t)pc.n_q * pc.K;
-    tab.vcol = tab.vrow + (int64_t)pc.n_q * pc.N;
-    tab.wrow = tab.vcol + (int64_t)pc.n_q * pc.K;
-    tab.wcol = tab.wrow + (int64_t)pc.n_q * pc.M;
+    const int64_t ext[6] = {pr.M, pr.K, pr.N, pr.K, pr.M, pr.N};
+    if (P->dtab) {
+      // the kernels read this pass's part of the page-locked host tables in place
+      const int64_t* src = P->dtab;
+      const int64_t** dst[6] = {&tab.urow, &tab.ucol, &tab.vrow, &tab.vcol, &tab.wrow, &tab.wcol};
+      for (int k = 0; k < 6; ++k) {
+        *dst[k] = src + (int64_t)q0 * ext[k];
+        src += (int64_t)pr.n_q * ext[k];
+      }
+    } else {
+      // copy this pass's part into the workspace: one copy for a single pass,
+      // one per table otherwise
+      int64_t* t0 = (int64_t*)(base + L.off_tab);
+      tab.urow = t0;
+      tab.ucol = tab.urow + (int64_t)pc.n_q * pc.M;
+      tab.vrow = tab.ucol + (int64_t)pc.n_q * pc.K;
+      tab.vcol = tab.vrow + (int64_t)pc.n_q * pc.N;
+      tab.wrow = tab.vcol + (int64_t)pc.n_q * pc.K;
+      tab.wcol = tab.wrow + (int64_t)pc.n_q * pc.M;
+      if (pc.n_q == pr.n_q) {
+        e = cudaMemcpyAsync(t0, P->htab.data(), P->htab.size() * sizeof(int64_t),
+                            cudaMemcpyHostToDevice, st);
+      } else {
+        const int64_t* src = P->htab.data();
+        int64_t* dst = t0;
+        for (int k = 0; k < 6 && e == cudaSuccess; ++k) {
+          e = cudaMemcpyAsync(dst, src + (int64_t)q0 * ext[k], (size_t)(pc.n_q * ext[k]) * sizeof(int64_t),
+                              cudaMemcpyHostToDevice, st);
+          src += (int64_t)pr.n_q * ext[k];
+          dst += (int64_t)pc.n_q * ext[k];
+        }
+      }
+      if (e != cudaSuccess) return cuda_status(e, "offset tables");
+    }
     unsigned long long* acc = L.ksplit > 1 ? (unsigned long long*)(base + L.off_acc) : nullptr;
     unsigned* tile_ctr = L.ksplit > 1 ? (unsigned*)(base + L.off_ctr) : nullptr;
     const int64_t acc_n = L.ksplit > 1 ? (int64_t)pc.n_q * pc.M * pc.N : 0;
@@ -719,6 +782,11 @@ symctr_status symctr_profile_read(const symctr_plan* P, float* prep_ms, float* g
 void symctr_plan_destroy(symctr_plan* P) {
   if (!P) return;
   symctr_profile_enable(P, 0);
+  if (P->pinned) {
+    // copies of the page-locked tables may still be queued on some stream
+    cudaDeviceSynchronize();
+    cudaHostUnregister((void*)P->htab.data());
+  }
   symctr_plan_destroy(P->bwd_u);
   symctr_plan_destroy(P->bwd_v);
   delete P;

@@ -117,15 +117,17 @@ struct Problem {
 
 SC_HD int batch_irrep(const Problem& p, int b) { return p.q_single >= 0 ? p.q_single : p.q_base + b; }
 
-// Offset tables of the aligned forms for one contraction (device memory in the
-// workspace): row_off / col_off of every (batch, index), int64.
+// Offset tables of the aligned forms for one contraction pass: row_off /
+// col_off of every (batch, index), int64.  They are computed once per plan on
+// the host and read in place through the device view of page-locked host
+// memory, or copied into the workspace where that view is unavailable.
 struct Tables {
-  int64_t* urow;  // [n_q][M]
-  int64_t* ucol;  // [n_q][K]
-  int64_t* vrow;  // [n_q][N]
-  int64_t* vcol;  // [n_q][K]
-  int64_t* wrow;  // [n_q][M]
-  int64_t* wcol;  // [n_q][N]
+  const int64_t* urow;  // [n_q][M]
+  const int64_t* ucol;  // [n_q][K]
+  const int64_t* vrow;  // [n_q][N]
+  const int64_t* vcol;  // [n_q][K]
+  const int64_t* wrow;  // [n_q][M]
+  const int64_t* wcol;  // [n_q][N]
 };
 
 SC_HD int64_t tables_entries(const Problem& p) {

@@ -239,16 +239,16 @@ __device__ __forceinline__ void operand_dims(const Problem& p, int op, int64_t* 
   *Cn = p.K;
 }
 
-// Exponent scan of 32 rows over one column block, offsets computed in place
-// (the tables are not built yet): the offsets of up to kScanWidth columns at
-// once (independent computations, one exposed latency), then the loads.
+// Exponent scan of 32 rows over one column block: the offsets of up to
+// kScanWidth columns at once, then the loads.
 template <int S>
-__device__ void scan_tile(const PrepArgs& a, const OperandMap* maps, const GroupDesc& g, int op,
-                          uint32_t tile, int64_t* roff, int64_t* coff, unsigned long long* rmax) {
+__device__ void scan_tile(const PrepArgs& a, int op, uint32_t tile, int64_t* roff, int64_t* coff,
+                          unsigned long long* rmax) {
   const Problem& p = a.p;
   int64_t R, Cn;
   operand_dims(p, op, &R, &Cn);
-  const OperandMap& m = maps[op];
+  const int64_t* rtab = op == 0 ? a.t.urow : a.t.vrow;
+  const int64_t* ctab = op == 0 ? a.t.ucol : a.t.vcol;
   const double* src = a.src[op];
   const bool fast_rows = a.fast_rows[op];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
@@ -260,11 +260,10 @@ __device__ void scan_tile(const PrepArgs& a, const OperandMap* maps, const Group
   const int64_t r0 = (int64_t)(rem / P) * TILE;
   const uint32_t j = rem % P;
   const int64_t cb = j * width, ce = min(Cn, cb + width);
-  const int Q = batch_irrep(p, (int)b);
   __syncthreads();
   if (threadIdx.x < TILE) {
     const int64_t r = r0 + threadIdx.x;
-    roff[threadIdx.x] = r < R ? axis_offset(m.rows, g, Q, r) : 0;
+    roff[threadIdx.x] = r < R ? rtab[(int64_t)b * R + r] : 0;
     rmax[threadIdx.x] = 0;
   }
   constexpr int PER = SCAN_COLS / (THREADS / 32);
@@ -274,7 +273,7 @@ __device__ void scan_tile(const PrepArgs& a, const OperandMap* maps, const Group
 #pragma unroll
     for (int i = 0; i < kScanWidth / THREADS; ++i) {
       const int64_t c = sb + threadIdx.x + i * THREADS;
-      coff[threadIdx.x + i * THREADS] = c < se ? axis_offset(m.cols, g, Q, c) : 0;
+      coff[threadIdx.x + i * THREADS] = c < se ? ctab[(int64_t)b * Cn + c] : 0;
     }
     __syncthreads();
     for (int64_t c0 = sb; c0 < se; c0 += SCAN_COLS) {
@@ -479,9 +478,10 @@ __device__ void slice_unit(const PrepArgs& a, int op, uint32_t unit, int64_t* ro
   }
 }
 
-// Operand preparation of one contraction in one cooperative launch:
-//   phase 1  offset tables of the six index maps, zeroed split-K accumulators,
-//            and (split form) the per-row exponent maxima of U and V;
+// Operand preparation of one contraction in one cooperative launch (the
+// offset tables are already in the workspace):
+//   phase 1  zeroed split-K accumulators and (split form) the per-row
+//            exponent maxima of U and V;
 //   phase 2  BF16 slices (split) or TF32 copies of U and V.
 template <int S>
 __global__ void __launch_bounds__(THREADS, 4) prep_kernel(PrepArgs a) {
@@ -489,56 +489,20 @@ __global__ void __launch_bounds__(THREADS, 4) prep_kernel(PrepArgs a) {
   __shared__ unsigned long long rmax[TILE];
   __shared__ int32_t rk0[TILE];
   __shared__ double tilebuf[TILE][SLICE_COLS + 1];
-  // the index maps and the group in shared memory: the offset computations
-  // index them with run-time subscripts
-  __shared__ OperandMap maps[3];
-  __shared__ GroupDesc g;
   const Problem& p = a.p;
-  {
-    static_assert(sizeof(OperandMap) % 4 == 0 && sizeof(GroupDesc) % 4 == 0, "word copy");
-    constexpr int nw = (int)(sizeof(OperandMap) / 4);
-    for (int i = threadIdx.x; i < 3 * nw + (int)(sizeof(GroupDesc) / 4); i += THREADS) {
-      uint32_t v;
-      if (i < nw) v = reinterpret_cast<const uint32_t*>(&p.u)[i];
-      else if (i < 2 * nw) v = reinterpret_cast<const uint32_t*>(&p.v)[i - nw];
-      else if (i < 3 * nw) v = reinterpret_cast<const uint32_t*>(&p.w)[i - 2 * nw];
-      else v = reinterpret_cast<const uint32_t*>(&p.g)[i - 3 * nw];
-      if (i < 3 * nw) reinterpret_cast<uint32_t*>(maps)[i] = v;
-      else reinterpret_cast<uint32_t*>(&g)[i - 3 * nw] = v;
-    }
-  }
-  __syncthreads();
   const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
   const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  {
-    // one grid-stride walk over the six tables, which lie end to end in the
-    // order U rows, U cols, V rows, V cols, W rows, W cols
-    const int64_t nq = p.n_q;
-    const int64_t total = tables_entries(p);
-    for (int64_t e = gtid; e < total; e += gthreads) {
-      int64_t r = e, len = 0;
-      int which = 0;
-      for (; which < 6; ++which) {
-        len = which == 0 || which == 4 ? p.M : which == 2 || which == 5 ? p.N : p.K;
-        if (r < nq * len) break;
-        r -= nq * len;
-      }
-      const AxisMap& m = (which & 1) ? maps[which >> 1].cols : maps[which >> 1].rows;
-      const int64_t b = r / len;
-      a.t.urow[e] = axis_offset(m, g, batch_irrep(p, (int)b), r - b * len);
-    }
-    for (int64_t i = gtid; i < a.zero64_n; i += gthreads) a.zero64[i] = 0ull;
-    for (int64_t i = gtid; i < a.zero32_n; i += gthreads) a.zero32[i] = 0u;
-  }
+  for (int64_t i = gtid; i < a.zero64_n; i += gthreads) a.zero64[i] = 0ull;
+  for (int64_t i = gtid; i < a.zero32_n; i += gthreads) a.zero32[i] = 0u;
   if (S > 0) {
     const uint32_t tiles0 = (uint32_t)(((p.M + TILE - 1) / TILE) * a.parts * p.n_q);
     const uint32_t tiles1 = (uint32_t)(((p.N + TILE - 1) / TILE) * a.parts * p.n_q);
     for (uint32_t t = blockIdx.x; t < tiles0 + tiles1; t += gridDim.x) {
       const int op = t < tiles0 ? 0 : 1;
-      scan_tile<S>(a, maps, g, op, op == 0 ? t : t - tiles0, roff, coff, rmax);
+      scan_tile<S>(a, op, op == 0 ? t : t - tiles0, roff, coff, rmax);
     }
+    grid_barrier(a.barrier, 1, a.err);
   }
-  grid_barrier(a.barrier, 1, a.err);
   // the GEMM that consumes these operands may start its setup now
   asm volatile("griddepcontrol.launch_dependents;");
   {
