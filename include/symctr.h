@@ -167,7 +167,9 @@ SYMCTR_API symctr_status symctr_contract(const symctr_plan* plan, const double* 
  * array: calls that overlap on the GPU race (use one stream).  The first call on
  * a device looks up the array's address (cudaGetSymbolAddress, device current)
  * and should come before any stream capture.  Device-side failures are recorded
- * in the array and not reported; no memory is allocated or freed. */
+ * in the array and not reported; no memory is allocated or freed (the first
+ * contraction of a plan, through either entry point, page-locks the plan's own
+ * host offset tables). */
 SYMCTR_API symctr_status symctr_contract_static_scratch(const symctr_plan* plan,
                                                         const double* u_red, const double* v_red,
                                                         double* w_red, void* stream);
