@@ -432,6 +432,92 @@ def run_ours(args, rank, world):
     return line
 
 
+def run_sweep(args, rank, world):
+    """Config 5: the CC-ladder contraction at virtual 512 / occupied 128 with
+    sector dims 512/G and 128/G.  The operands (up to 275 GB at G = 2) are drawn
+    on the device; the error is taken on entries the oracle computes one by one.
+    Forward, and with --backward the adjoint pair as well."""
+    import torch
+    import oracle as O
+    import paper_2007_08056_gb300 as sc
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+    dev = torch.device("cuda")
+    G = args.sweep_g
+    c = WL.sweep_point(G)
+    operand_bytes = 8 * sum(int(np.prod(WL.reduced_shape(c.moduli, t.dims))) for t in (c.u, c.v))
+    operand_bytes += 8 * int(np.prod(WL.reduced_shape(c.moduli, c.u.dims[:2] + c.v.dims[2:])))
+    if operand_bytes > torch.cuda.mem_get_info()[0] - (8 << 30):
+        return {"workload": c.name, "precision": args.precision, "G": G,
+                "unavailable": f"exceeds one GPU's HBM (u, v, w alone take {operand_bytes / 1e9:.0f} GB)"}
+    gen = torch.Generator(device="cuda").manual_seed(5000 + G)
+    U = torch.randn(WL.reduced_shape(c.moduli, c.u.dims), generator=gen, device=dev,
+                    dtype=torch.float64).mul_(c.u.scale)
+    V = torch.randn(WL.reduced_shape(c.moduli, c.v.dims), generator=gen, device=dev,
+                    dtype=torch.float64).mul_(c.v.scale)
+    p = sc.Plan(c.einsum, c.moduli, spec(c.u), spec(c.v), args.precision)
+    W = torch.empty(p.shape_w, dtype=torch.float64, device=dev)
+    free, _ = torch.cuda.mem_get_info()
+    want = int(p.info.workspace_bytes)
+    budget = free - (8 << 30) - L2_FLUSH_BYTES
+    nbytes = want if want <= budget else max(int(p.info.workspace_bytes_min), budget)
+    if nbytes > budget:
+        return {"workload": c.name, "unavailable": "exceeds one GPU's HBM"}
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    ev_s, ev_e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(args.steps):
+            flush.fill_(1)
+            ev_s.record()
+            fn()
+            ev_e.record()
+            ev_e.synchronize()
+            ts.append(ev_s.elapsed_time(ev_e))
+        return statistics.mean(ts)
+
+    p.profile(True)
+    ms = max_over_ranks(timed(lambda: p.contract(U, V, out=W, workspace=ws)), world, dev)
+    prep_ms, gemm_ms, _ = p.phase_times()
+    p.check_device_error(ws)
+    o = O.plan(c.einsum, O.Group(c.moduli), O.Sym(*spec(c.u)), O.Sym(*spec(c.v)))
+    rng = np.random.default_rng(500 + G)
+    idx = [tuple(int(rng.integers(0, d)) for d in p.shape_w) for _ in range(16)]
+    want_e = [O.contract_element_lazy(o, lambda i: U[i].cpu().numpy(), lambda i: V[i].cpu().numpy(), ix)
+              for ix in idx]
+    got = [W[ix].item() for ix in idx]
+    rel = float(np.linalg.norm(np.subtract(got, want_e)) / np.linalg.norm(want_e))
+    line = {"workload": c.name, "precision": args.precision, "G": G,
+            "M_N_K": [int(p.info.M), int(p.info.N), int(p.info.K)], "n_q": int(p.info.n_q),
+            "useful_tflop": p.useful_flops / 1e12, "ms": round(ms, 3),
+            "useful_tflops": round(replicas_value(p.useful_flops, ms, world), 3),
+            "phases_ms": {"prep": round(prep_ms, 3), "gemm": round(gemm_ms, 3)},
+            "passes": "one" if nbytes >= want else f"Q-streaming, workspace {nbytes / 1e9:.1f} GB",
+            "rel_err_sampled_16": float(f"{rel:.3e}")}
+    pk = peaks()
+    roofs = rooflines(args, [p], [prep_ms], [gemm_ms], pk)
+    line["rooflines"] = roofs
+    if args.backward:
+        del ws
+        torch.cuda.empty_cache()
+        gW = torch.randn(p.shape_w, generator=gen, device=dev, dtype=torch.float64)
+        free, _ = torch.cuda.mem_get_info()
+        need = int(p.info.workspace_bytes_backward) + 8 * (U.numel() + V.numel())
+        if need > free - (8 << 30):
+            line["backward"] = {"unavailable": "exceeds one GPU's HBM (the gradients add the size of u and v)"}
+        else:
+            wsb = torch.empty(int(p.info.workspace_bytes_backward), dtype=torch.uint8, device=dev)
+            msb = max_over_ranks(timed(lambda: p.backward(gW, U, V, workspace=wsb)), world, dev)
+            line["backward"] = {"ms": round(msb, 3),
+                                "useful_tflops": round(replicas_value(2 * p.useful_flops, msb, world), 3)}
+    return line
+
+
 def run_reference(args, rank, world):
     """The oracle on the host cores, on the same workload and metric."""
     if rank != 0:
@@ -475,7 +561,9 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["mps", "cc_ladder"], default="mps")
+    ap.add_argument("--workload", choices=["mps", "cc_ladder", "sweep"], default="mps")
+    ap.add_argument("--sweep-g", type=int, default=16, help="G of the sweep workload (config 5)")
+    ap.add_argument("--backward", action="store_true", help="sweep: time the backward pair too")
     ap.add_argument("--precision", choices=["split_bf16", "fp64", "tf32"], default="split_bf16")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -497,7 +585,7 @@ def main():
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         torch.distributed.init_process_group("nccl")
-    line = run_ours(args, rank, world)
+    line = run_sweep(args, rank, world) if args.workload == "sweep" else run_ours(args, rank, world)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
