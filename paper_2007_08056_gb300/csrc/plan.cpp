@@ -156,6 +156,9 @@ struct symctr_plan {
 
 namespace {
 
+// Offset tables up to this size are read in place from page-locked host memory.
+constexpr size_t kMappedTablesMax = 1 << 20;
+
 int g_label(const GroupDesc& g, const int32_t* comps) {
   int q = 0;
   for (int i = 0; i < g.n; ++i) {
@@ -544,8 +547,10 @@ symctr_status run_contract_body(const symctr_plan* P, const double* u, const dou
     const Layout L = make_layout(pc, true, P->prec, P->n_slices, P->kpad);
     Tables tab;
     const int64_t ext[6] = {pr.M, pr.K, pr.N, pr.K, pr.M, pr.N};
-    if (P->dtab) {
-      // the kernels read this pass's part of the page-locked host tables in place
+    if (P->dtab && P->htab.size() * sizeof(int64_t) <= kMappedTablesMax) {
+      // small tables: the kernels read this pass's part of the page-locked
+      // host tables in place (reads over the CPU-GPU link are not cached on
+      // the GPU, so larger tables, re-read by many tiles, go to HBM instead)
       const int64_t* src = P->dtab;
       const int64_t** dst[6] = {&tab.urow, &tab.ucol, &tab.vrow, &tab.vcol, &tab.wrow, &tab.wcol};
       for (int k = 0; k < 6; ++k) {
