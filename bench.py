@@ -188,11 +188,12 @@ def replicas_value(flops_per_step, ms, world):
 # our arm
 # ---------------------------------------------------------------------------
 
-# the sources that decide each kernel's code and launch shape
+# the sources that decide each kernel's code and launch shape (the launchers
+# sit beside the kernels; the shared sizing rules are in the internal header)
 KERNEL_SOURCES = {
-    "prep_kernel": ("transforms.cu", "symctr_internal.h", "plan.cpp"),
-    "gemm_tc_kernel": ("gemm_tc.cu", "symctr_internal.h", "plan.cpp"),
-    "gemm_f64": ("gemm_f64.cu", "symctr_internal.h", "plan.cpp"),
+    "prep_kernel": ("transforms.cu", "symctr_internal.h"),
+    "gemm_tc_kernel": ("gemm_tc.cu", "symctr_internal.h"),
+    "gemm_f64": ("gemm_f64.cu", "symctr_internal.h"),
 }
 
 
