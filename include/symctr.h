@@ -189,6 +189,19 @@ SYMCTR_API symctr_status symctr_contract_backward(const symctr_plan* plan, const
  * Returns SYMCTR_OK, SYMCTR_ERR_DEVICE_TIMEOUT, SYMCTR_ERR_NONFINITE or SYMCTR_ERR_CUDA. */
 SYMCTR_API symctr_status symctr_check_device_error(const symctr_plan* plan, void* workspace, void* stream);
 
+/* Failure-detection self-test (the paper has no counterpart).  Launches, on
+ * `stream`, one small kernel that waits through the library's bounded-wait
+ * routine (the one every pipeline wait of the tensor-core GEMM uses) on a
+ * barrier that nothing completes.  After wait_cycles SM clock cycles (clamped
+ * to [1e3, 2e9]; 2e6 is about 1 ms) the wait gives up, sets the timeout code in
+ * the first word of `workspace` (at least 256 bytes, device memory) and the
+ * kernel returns; symctr_check_device_error(plan, workspace, stream) then
+ * returns SYMCTR_ERR_DEVICE_TIMEOUT.  Nothing traps; the context stays usable.
+ * Returns SYMCTR_OK once launched, SYMCTR_ERR_NULLPTR, SYMCTR_ERR_WORKSPACE or
+ * SYMCTR_ERR_CUDA. */
+SYMCTR_API symctr_status symctr_selftest_bounded_wait(void* workspace, size_t workspace_bytes,
+                                                     int64_t wait_cycles, void* stream);
+
 /* Phase timing for measurement.  enable = 1 creates CUDA events on the plan;
  * each later symctr_contract on it records them on the call's stream around
  * the operand preparation (split / TF32 transforms) and the GEMM launch.

@@ -101,11 +101,13 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
                                         ctypes.POINTER(ctypes.c_float),
                                         ctypes.POINTER(ctypes.c_int)]
     lib.symctr_contract_static_scratch.argtypes = [P, P, P, P, P]
+    lib.symctr_selftest_bounded_wait.argtypes = [P, ctypes.c_size_t, ctypes.c_int64, P]
     lib.symctr_plan_destroy.argtypes = [P]
     lib.symctr_plan_destroy.restype = None
     for f in ("symctr_plan_create", "symctr_plan_query", "symctr_align", "symctr_contract",
               "symctr_contract_backward", "symctr_check_device_error", "symctr_profile_enable",
-              "symctr_profile_read", "symctr_contract_static_scratch"):
+              "symctr_profile_read", "symctr_contract_static_scratch",
+              "symctr_selftest_bounded_wait"):
         getattr(lib, f).restype = ctypes.c_int
     _LIB = lib
     return lib
@@ -315,6 +317,17 @@ def contract(plan: Plan, u: torch.Tensor, v: torch.Tensor) -> torch.Tensor:
     return SymContract.apply(plan, u, v)
 
 
+def selftest_bounded_wait(workspace: torch.Tensor, wait_cycles: int = 2_000_000) -> None:
+    """Launch the failure-detection self-test on the current stream: a kernel
+    whose bounded wait on a barrier nothing completes gives up after
+    `wait_cycles` cycles and records the timeout in `workspace`'s error word
+    (read it with Plan.check_device_error)."""
+    if not (isinstance(workspace, torch.Tensor) and workspace.is_cuda):
+        raise TypeError("workspace must be a CUDA tensor")
+    nbytes = workspace.numel() * workspace.element_size()
+    _check(load().symctr_selftest_bounded_wait(_ptr(workspace), nbytes, int(wait_cycles), _stream()))
+
+
 def einsum(spec: str, u: torch.Tensor, v: torch.Tensor, moduli, sym_u, sym_v,
            precision: str = "fp64") -> torch.Tensor:
     """One-shot convenience: plan + differentiable contraction."""
@@ -322,4 +335,4 @@ def einsum(spec: str, u: torch.Tensor, v: torch.Tensor, moduli, sym_u, sym_v,
 
 
 __all__ = ["Plan", "PlanInfo", "SymSpec", "SymContract", "SymctrError", "contract", "einsum",
-           "load", "library_path", "PRECISIONS"]
+           "load", "library_path", "PRECISIONS", "selftest_bounded_wait"]

@@ -812,6 +812,25 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
 }
 
+// Failure-detection self-test: one CTA waits, through the same bounded wait as
+// the GEMM's pipeline, on an mbarrier that nothing arrives on.  The wait gives
+// up after `limit` cycles, records DEVERR_TIMEOUT in the error word and the
+// kernel returns normally (no trap, the context stays usable).
+__global__ void bounded_wait_selftest_kernel(unsigned* err, long long limit) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ Ctl ctl;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    ctl.abort = 0;
+    ctl.last = 0;
+    ctl.err = err;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) wait_phase(&bar, 0, &ctl, limit);
+  __syncthreads();
+}
+
 // ---------------------------------------------------------------- host side
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
@@ -924,6 +943,12 @@ cudaError_t launch_gemm_tf32(const Problem& p, const Tables& tab, const float* u
                              int64_t kpad, double* w, unsigned* err, cudaStream_t st) {
   return launch_tc<MODE_TF32, 1, 6>(p, tab, u, v, nullptr, nullptr, kpad, w, err, 1, nullptr, nullptr,
                                     st);
+}
+
+cudaError_t launch_bounded_wait_selftest(unsigned* err, long long limit_cycles, cudaStream_t st) {
+  bounded_wait_selftest_kernel<<<1, 32, 0, st>>>(err, limit_cycles);
+  ++g_kernel_launches;
+  return cudaGetLastError();
 }
 
 }  // namespace symctr

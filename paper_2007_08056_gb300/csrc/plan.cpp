@@ -737,6 +737,17 @@ symctr_status symctr_check_device_error(const symctr_plan* P, void* ws, void* st
   return SYMCTR_OK;
 }
 
+symctr_status symctr_selftest_bounded_wait(void* ws, size_t ws_bytes, int64_t wait_cycles,
+                                           void* stream) {
+  if (!ws) return fail(SYMCTR_ERR_NULLPTR, "NULL workspace");
+  if (ws_bytes < 256) return fail(SYMCTR_ERR_WORKSPACE, "workspace smaller than its 256-byte header");
+  if (wait_cycles < 1000) wait_cycles = 1000;
+  if (wait_cycles > 2000000000ll) wait_cycles = 2000000000ll;
+  return cuda_status(launch_bounded_wait_selftest((unsigned*)ws, (long long)wait_cycles,
+                                                  (cudaStream_t)stream),
+                     "bounded-wait self-test");
+}
+
 const char* symctr_status_string(symctr_status s) {
   switch (s) {
     case SYMCTR_OK: return "SYMCTR_OK";
