@@ -433,25 +433,33 @@ def run_ours(args, rank, world):
     return line
 
 
-def run_sweep(args, rank, world):
-    """Config 5: the CC-ladder contraction at virtual 512 / occupied 128 with
-    sector dims 512/G and 128/G.  The operands (up to 275 GB at G = 2) are drawn
-    on the device; the error is taken on entries the oracle computes one by one.
-    Forward, and with --backward the adjoint pair as well."""
+def run_device(args, rank, world):
+    """Workloads whose operands are drawn on the device: config 5 (the
+    CC-ladder contraction at virtual 512 / occupied 128 with sector dims 512/G
+    and 128/G, up to 275 GB at G = 2) and the Table-2 instances of the Table-1
+    contraction families.  The error is taken on entries the oracle computes
+    one by one.  Forward, and with --backward the adjoint pair as well."""
     import torch
     import oracle as O
     import paper_2007_08056_gb300 as sc
 
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
     dev = torch.device("cuda")
-    G = args.sweep_g
-    c = WL.sweep_point(G)
-    operand_bytes = 8 * sum(int(np.prod(WL.reduced_shape(c.moduli, t.dims))) for t in (c.u, c.v))
-    operand_bytes += 8 * int(np.prod(WL.reduced_shape(c.moduli, c.u.dims[:2] + c.v.dims[2:])))
+    if args.workload == "sweep":
+        G = args.sweep_g
+        c = WL.sweep_point(G)
+        seed = 5000 + G
+    else:
+        c = WL.TABLE2[args.case]
+        G = c.moduli[0]
+        seed = c.u.seed
+    probe = sc.Plan(c.einsum, c.moduli, spec(c.u), spec(c.v), "fp64")
+    operand_bytes = 8 * (probe.info.numel_u + probe.info.numel_v + probe.info.numel_w)
+    del probe
     if operand_bytes > torch.cuda.mem_get_info()[0] - (8 << 30):
         return {"workload": c.name, "precision": args.precision, "G": G,
                 "unavailable": f"exceeds one GPU's HBM (u, v, w alone take {operand_bytes / 1e9:.0f} GB)"}
-    gen = torch.Generator(device="cuda").manual_seed(5000 + G)
+    gen = torch.Generator(device="cuda").manual_seed(seed)
     U = torch.randn(WL.reduced_shape(c.moduli, c.u.dims), generator=gen, device=dev,
                     dtype=torch.float64).mul_(c.u.scale)
     V = torch.randn(WL.reduced_shape(c.moduli, c.v.dims), generator=gen, device=dev,
@@ -487,13 +495,13 @@ def run_sweep(args, rank, world):
     prep_ms, gemm_ms, _ = p.phase_times()
     p.check_device_error(ws)
     o = O.plan(c.einsum, O.Group(c.moduli), O.Sym(*spec(c.u)), O.Sym(*spec(c.v)))
-    rng = np.random.default_rng(500 + G)
+    rng = np.random.default_rng(seed + 500)
     idx = [tuple(int(rng.integers(0, d)) for d in p.shape_w) for _ in range(16)]
     want_e = [O.contract_element_lazy(o, lambda i: U[i].cpu().numpy(), lambda i: V[i].cpu().numpy(), ix)
               for ix in idx]
     got = [W[ix].item() for ix in idx]
     rel = float(np.linalg.norm(np.subtract(got, want_e)) / np.linalg.norm(want_e))
-    line = {"workload": c.name, "precision": args.precision, "G": G,
+    line = {"workload": c.name, "einsum": c.einsum, "precision": args.precision, "G": G,
             "M_N_K": [int(p.info.M), int(p.info.N), int(p.info.K)], "n_q": int(p.info.n_q),
             "useful_tflop": p.useful_flops / 1e12, "ms": round(ms, 3),
             "useful_tflops": round(replicas_value(p.useful_flops, ms, world), 3),
@@ -562,7 +570,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["mps", "cc_ladder", "sweep"], default="mps")
+    ap.add_argument("--workload", choices=["mps", "cc_ladder", "sweep", "table"], default="mps")
+    ap.add_argument("--case", default="CC1_a", help="table: a Table-2 case (" + ", ".join(WL.TABLE2) + ")")
     ap.add_argument("--sweep-g", type=int, default=16, help="G of the sweep workload (config 5)")
     ap.add_argument("--backward", action="store_true", help="sweep: time the backward pair too")
     ap.add_argument("--precision", choices=["split_bf16", "fp64", "tf32"], default="split_bf16")
@@ -586,7 +595,8 @@ def main():
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         torch.distributed.init_process_group("nccl")
-    line = run_sweep(args, rank, world) if args.workload == "sweep" else run_ours(args, rank, world)
+    line = (run_device(args, rank, world) if args.workload in ("sweep", "table")
+            else run_ours(args, rank, world))
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -139,6 +139,37 @@ def sweep_point(G: int) -> Contraction:
     return cc_ladder(G, 512, 128)
 
 
+# The contraction families of Table 1 at the tensor dimensions of Table 2
+# (per-mode sector dims; Table 1 gives no charge signs, these are the ones the
+# parity suite uses).  Entries N(0,1) scaled by 1/sqrt(contracted length).
+def _t2(label, einsum, G, su, du, sv, dv, k):
+    import math as _m
+    contracted = [ch for ch in einsum.split("->")[0].split(",")[0] if ch in einsum.split(",")[1].split("->")[0]]
+    klen = 1
+    lab_u = einsum.split(",")[0]
+    for ch in contracted:
+        klen *= G * du[lab_u.index(ch)]
+    sc = 1.0 / _m.sqrt(klen)
+    return Contraction(label, einsum, (G,), TensorSpec(su, (0,), du, sc, 8000 + 2 * k),
+                       TensorSpec(sv, (0,), dv, sc, 8001 + 2 * k))
+
+
+TABLE2 = {c.name: c for c in [
+    _t2("CC1_a", "ijkl,mnkl->ijmn", 8, PP, (32, 32, 32, 32), PP, (16, 16, 32, 32), 0),
+    _t2("CC2_a", "opij,opkm->ijmk", 8, PP, (16, 16, 32, 32), (-1, -1, 1, 1), (16, 16, 32, 16), 1),
+    _t2("CC3_a", "opmn,opij->ijmn", 8, PP, (16, 16, 16, 16), PP, (16, 16, 32, 32), 2),
+    _t2("CC1_b", "ijkl,mnkl->ijmn", 16, PP, (16, 16, 16, 16), PP, (8, 8, 16, 16), 3),
+    _t2("CC2_b", "opij,opkm->ijmk", 16, PP, (8, 8, 16, 16), (-1, -1, 1, 1), (8, 8, 16, 8), 4),
+    _t2("CC3_b", "opmn,opij->ijmn", 16, PP, (8, 8, 8, 8), PP, (8, 8, 16, 16), 5),
+    _t2("MM_a", "ij,jk->ik", 2, (1, -1), (10000, 10000), (1, -1), (10000, 10000), 6),
+    _t2("MM_b", "ij,jk->ik", 100, (1, -1), (2000, 2000), (1, -1), (2000, 2000), 7),
+    _t2("MPS_a", "ijk,klm->ijlm", 2, (1, 1, -1), (3000, 10, 3000), (1, 1, -1), (3000, 1, 3000), 8),
+    _t2("MPS_b", "ijk,klm->ijlm", 5, (1, 1, -1), (700, 10, 700), (1, 1, -1), (700, 1, 700), 9),
+    _t2("PEPS_a", "ijkl,klmn->ijmn", 2, PP, (400, 400, 20, 20), PP, (20, 20, 20, 20), 10),
+    _t2("PEPS_b", "ijkl,klmn->ijmn", 10, PP, (64, 64, 8, 8), PP, (8, 8, 8, 8), 11),
+]}
+
+
 def small_cases() -> List[Contraction]:
     """Small contractions (seconds on the oracle) spanning the (s,t,v) shapes,
     sigma = +-1, nonzero target charges and a product group."""
