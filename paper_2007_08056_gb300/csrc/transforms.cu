@@ -267,7 +267,9 @@ __device__ void scan_tile(const PrepArgs& a, int op, uint32_t tile, int64_t* rof
     rmax[threadIdx.x] = 0;
   }
   constexpr int PER = SCAN_COLS / (THREADS / 32);
-  uint64_t mx = 0;   // fast rows: this thread's row (tx)
+  constexpr int RPW = TILE / (THREADS / 32);   // rows per warp (column paths)
+  uint64_t mx = 0;          // fast rows: this thread's row (tx)
+  uint64_t mxr[RPW] = {};   // column paths: this lane's share of its warp's rows
   for (int64_t sb = cb; sb < ce; sb += kScanWidth) {
     const int64_t se = min(ce, sb + kScanWidth);
 #pragma unroll
@@ -293,10 +295,29 @@ __device__ void scan_tile(const PrepArgs& a, int op, uint32_t tile, int64_t* rof
 #pragma unroll
           for (int i = 0; i < PER / 2; ++i) mx = max(mx, abs_bits(x[i]));
         }
+      } else if (a.pair_ok[op]) {
+        // lanes walk column pairs (16-byte loads), warps walk rows; per-row
+        // maxima stay in registers until the end of the tile
+#pragma unroll
+        for (int h = 0; h < RPW; ++h) {
+          const int rr = ty + h * (THREADS / 32);
+          const bool rok = r0 + rr < R;
+          const double* rowp = src + roff[rr];
+          double2 x[SCAN_COLS / 64];
+#pragma unroll
+          for (int i = 0; i < SCAN_COLS / 64; ++i) {
+            const int cc = 2 * tx + 64 * i;
+            x[i] = (rok && c0 + cc < se) ? *reinterpret_cast<const double2*>(rowp + co[cc])
+                                         : make_double2(0.0, 0.0);
+          }
+#pragma unroll
+          for (int i = 0; i < SCAN_COLS / 64; ++i)
+            mxr[h] = max(mxr[h], max(abs_bits(x[i].x), abs_bits(x[i].y)));
+        }
       } else {
         // lanes walk columns (contiguous), warps walk rows
 #pragma unroll
-        for (int h = 0; h < TILE / (THREADS / 32); ++h) {
+        for (int h = 0; h < RPW; ++h) {
           const int rr = ty + h * (THREADS / 32);
           const bool rok = r0 + rr < R;
           const double* rowp = src + roff[rr];
@@ -306,15 +327,20 @@ __device__ void scan_tile(const PrepArgs& a, int op, uint32_t tile, int64_t* rof
             const int cc = tx + 32 * i;
             x[i] = (rok && c0 + cc < se) ? rowp[co[cc]] : 0.0;
           }
-          uint64_t v = 0;
 #pragma unroll
-          for (int i = 0; i < SCAN_COLS / 32; ++i) v = max(v, abs_bits(x[i]));
-          for (int o = 16; o > 0; o >>= 1) v = max(v, (uint64_t)__shfl_xor_sync(0xffffffffu, (unsigned long long)v, o));
-          if (tx == 0) rmax[rr] = max((uint64_t)rmax[rr], v);   // row rr belongs to this warp alone
+          for (int i = 0; i < SCAN_COLS / 32; ++i) mxr[h] = max(mxr[h], abs_bits(x[i]));
         }
       }
     }
     __syncthreads();
+  }
+  if (!fast_rows) {
+#pragma unroll
+    for (int h = 0; h < RPW; ++h) {
+      uint64_t v = mxr[h];
+      for (int o = 16; o > 0; o >>= 1) v = max(v, (uint64_t)__shfl_xor_sync(0xffffffffu, (unsigned long long)v, o));
+      if (tx == 0) rmax[ty + h * (THREADS / 32)] = v;   // row belongs to this warp alone
+    }
   }
   if (fast_rows) atomicMax(&rmax[tx], (unsigned long long)mx);
   __syncthreads();
@@ -416,6 +442,47 @@ __device__ void slice_unit(const PrepArgs& a, int op, uint32_t unit, int64_t* ro
     }
   }
   __syncthreads();
+  if (!fast_rows && a.pair_ok[op]) {
+    // lanes walk column pairs with 16-byte loads, warps walk rows; the column
+    // offsets of all sub-tiles are loaded first, then two sub-tiles' data
+    // (eight 16-byte loads per lane) go out before any of it is sliced
+    int64_t co[SLICE_GROUP];
+#pragma unroll
+    for (int g = 0; g < SLICE_GROUP; ++g) {
+      const int64_t c = cu + g * SLICE_COLS + 2 * tx;
+      co[g] = c < Cn ? ctab[(int64_t)b * Cn + c] : 0;
+    }
+    constexpr int RPW = TILE / (THREADS / 32);
+#pragma unroll
+    for (int g0 = 0; g0 < SLICE_GROUP; g0 += 2) {
+      double2 x[2][RPW];
+#pragma unroll
+      for (int g = 0; g < 2; ++g) {
+        const int64_t c = cu + (g0 + g) * SLICE_COLS + 2 * tx;
+#pragma unroll
+        for (int rg = 0; rg < RPW; ++rg) {
+          const int rr = ty + rg * (THREADS / 32);
+          x[g][rg] = (c < Cn && r0 + rr < R)
+                         ? *reinterpret_cast<const double2*>(src + roff[rr] + co[g0 + g])
+                         : make_double2(0.0, 0.0);
+        }
+      }
+#pragma unroll
+      for (int g = 0; g < 2; ++g) {
+        const int64_t c = cu + (g0 + g) * SLICE_COLS + 2 * tx;
+        if (c >= kpad) continue;
+#pragma unroll
+        for (int rg = 0; rg < RPW; ++rg) {
+          const int rr = ty + rg * (THREADS / 32);
+          const int64_t r = r0 + rr;
+          if (r >= R) continue;
+          put_pair<S>(a, op, x[g][rg].x, x[g][rg].y, S > 0 ? rk0[rr] : 0, (brow + r) * kpad + c,
+                      slice_stride);
+        }
+      }
+    }
+    return;
+  }
   if (!fast_rows) {
     // lanes walk column pairs, warps walk rows; no shared-memory transpose
     const bool pair = a.pair_ok[op];
