@@ -10,10 +10,12 @@
 //   FP32 by diagonal d = i + j, for d <= S-1:
 //     TMEM acc0: d = 0, acc1: d = 1, acc2: d = 2   (exact, see below)
 //     TMEM acc3: d >= 3                             (rounded; weight <= 2^-24)
-//   Every 64 columns of K (kKChunk) the epilogue warps drain acc0..acc2 while
-//   the tensor core keeps working on the d >= 3 pairs: at most 3 pairs x 64 x
-//   2^14 <= 2^22 per drain, so each drained value is an exact integer that
-//   FP32 represents and that a magic-number add turns into an int32.  The
+//   The epilogue warps drain acc2 after every 64 columns of K (kKChunk), acc1
+//   after every 128 and acc0 after every 256, while the tensor core keeps
+//   working on the d >= 3 pairs: diagonal d has d + 1 pairs per K step, so a
+//   drain carries at most 3 x 64, 2 x 128 or 1 x 256 products of 2^14, i.e.
+//   <= 2^22: an exact integer that FP32 represents and that a magic-number add
+//   turns into an int32.  The
 //   integers are summed in three int32 registers per output element; at the
 //   end they and acc3 are combined in one int64 that is rounded once to
 //   float64 with the row and column exponents applied (integer arithmetic
@@ -55,6 +57,13 @@ constexpr int kExpBias = 4096;     // row exponents are stored biased (0 = all-z
 // tensor core keeps accumulating into a small value.  This bounds the drift of
 // its FP32 accumulation over long K.
 constexpr int kFoldChunks = 16;
+
+// Exact accumulators drained after chunk c (bit d = diagonal d): diagonal 2
+// after every chunk, 1 after every second, 0 after every fourth (c = -1: none
+// were filled yet, all start fresh).
+__host__ __device__ constexpr uint32_t drained_after(int c) {
+  return c < 0 ? 7u : (4u | (((c + 1) % 2 == 0) ? 2u : 0u) | (((c + 1) % 4 == 0) ? 1u : 0u));
+}
 constexpr long long kTimeoutCycles = 4000000000ll;  // ~2 s per wait at 2 GHz
 
 enum Mode { MODE_SPLIT = 0, MODE_TF32 = 1 };
@@ -386,18 +395,19 @@ __device__ __forceinline__ void mma_ij(uint32_t tacc, uint64_t da, uint64_t db, 
   }
 }
 
-// Slice pairs of diagonals 0, 1, 2, one exact TMEM accumulator each.  The first
-// MMA into each accumulator overwrites it when `fresh`.
+// Slice pairs of the exact diagonals 0, 1, 2, each into its own accumulator;
+// bit d of `fresh` makes diagonal d's first MMA overwrite its accumulator
+// (it was drained after the previous chunk).
 template <int KIND, int S>
 __device__ __forceinline__ void issue_top(uint32_t tmem, uint64_t da, uint64_t db, uint32_t id,
-                                          bool fresh) {
+                                          uint32_t fresh) {
   static_for<3>([&](auto D) {
     if constexpr (D.value <= S - 1) {
       static_for<D.value + 1>([&](auto I) {
         static_for<2>([&](auto KK) {
           constexpr bool first = I.value == 0 && KK.value == 0;
-          mma_ij<KIND, I.value, D.value - I.value, KK.value>(tmem + 128u * D.value, da, db, id,
-                                                             (fresh && first) ? 0u : 1u);
+          mma_ij<KIND, I.value, D.value - I.value, KK.value>(
+              tmem + 128u * D.value, da, db, id, (first && ((fresh >> D.value) & 1u)) ? 0u : 1u);
         });
       });
     }
@@ -584,9 +594,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             ok = wait_phase(top_empty, (chunk - 1) & 1, ctl);
             tc_fence_after();
           }
-          if (ok) issue_top<KIND, S>(tmem, da, db, id, true);
+          if (ok) issue_top<KIND, S>(tmem, da, db, id, KIND == MODE_TF32 ? 7u : drained_after(chunk - 1));
         } else {
-          issue_top<KIND, S>(tmem, da, db, id, false);
+          issue_top<KIND, S>(tmem, da, db, id, 0u);
           if (!final_chunk) tc_commit(top_full);
           issue_low<KIND, S>(tmem, da, db, id, false);
           if (has_low && !final_chunk && (chunk + 1) % kFoldChunks == 0) tc_commit(low_full);
@@ -608,8 +618,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int64_t m = m0 + row;
     const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(half * 64);
     // Running sums of the exact diagonals d = 0, 1, 2 in their own units
-    // (1, 2^-8, 2^-16): each drain adds at most 3 * 64 * 2^14 < 2^22, so int32
-    // holds 2^9 drains, i.e. K up to 32768 per K range (longer K is split).
+    // (1, 2^-8, 2^-16).  Diagonal d has d + 1 slice pairs of |a_i b_j| <= 2^14
+    // per K step and is drained every 4, 2, 1 chunks of 64 K (d = 0, 1, 2): at
+    // most 256 * 2^14, 2 * 128 * 2^14, 3 * 64 * 2^14 <= 2^22 per drain, which
+    // the magic-number drain and the FP32 accumulator hold exactly; int32 holds
+    // the sums of 512 chunks, i.e. K up to 32768 per K range (longer K is split).
     int32_t s0[64], s1[64], s2[64];
 #pragma unroll
     for (int j = 0; j < 64; ++j) s0[j] = s1[j] = s2[j] = 0;
@@ -619,19 +632,23 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int32_t B0 = (int32_t)__float_as_uint(M0), B1 = (int32_t)__float_as_uint(M1),
                   B2 = (int32_t)__float_as_uint(M2);
     constexpr bool live1 = S >= 2, live2 = S >= 3, live3 = S >= 4;
-    auto drain_top = [&]() {
+    // after chunk c: the accumulators in drained_after(c) (always diagonal 2's;
+    // every 2nd chunk diagonal 1's, every 4th diagonal 0's), as three
+    // straight-line variants
+    auto drain_top = [&](auto D0c, auto D1c) {
+      constexpr bool d0 = decltype(D0c)::value, d1 = live1 && decltype(D1c)::value, d2 = live2;
 #pragma unroll
       for (int pc = 0; pc < 16; ++pc) {
         uint32_t a0[4], a1[4], a2[4];
-        tmem_ld4(lane_base + 0 + pc * 4, a0);
-        if (live1) tmem_ld4(lane_base + 128 + pc * 4, a1);
-        if (live2) tmem_ld4(lane_base + 256 + pc * 4, a2);
+        if constexpr (d0) tmem_ld4(lane_base + 0 + pc * 4, a0);
+        if constexpr (d1) tmem_ld4(lane_base + 128 + pc * 4, a1);
+        if constexpr (d2) tmem_ld4(lane_base + 256 + pc * 4, a2);
         tmem_wait_ld();
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          s0[pc * 4 + j] += (int32_t)__float_as_uint(__uint_as_float(a0[j]) + M0) - B0;
-          if (live1) s1[pc * 4 + j] += (int32_t)__float_as_uint(__uint_as_float(a1[j]) + M1) - B1;
-          if (live2) s2[pc * 4 + j] += (int32_t)__float_as_uint(__uint_as_float(a2[j]) + M2) - B2;
+          if constexpr (d0) s0[pc * 4 + j] += (int32_t)__float_as_uint(__uint_as_float(a0[j]) + M0) - B0;
+          if constexpr (d1) s1[pc * 4 + j] += (int32_t)__float_as_uint(__uint_as_float(a1[j]) + M1) - B1;
+          if constexpr (d2) s2[pc * 4 + j] += (int32_t)__float_as_uint(__uint_as_float(a2[j]) + M2) - B2;
         }
       }
     };
@@ -643,7 +660,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           break;
         }
         tc_fence_after();
-        drain_top();
+        switch (drained_after(c)) {
+          case 7u: drain_top(std::true_type{}, std::true_type{}); break;
+          case 6u: drain_top(std::false_type{}, std::true_type{}); break;
+          default: drain_top(std::false_type{}, std::false_type{}); break;
+        }
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(top_empty);
