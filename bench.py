@@ -509,8 +509,11 @@ def run_device(args, rank, world):
             "passes": "one" if nbytes >= want else f"Q-streaming, workspace {nbytes / 1e9:.1f} GB",
             "rel_err_sampled_16": float(f"{rel:.3e}")}
     pk = peaks()
-    roofs = rooflines(args, [p], [prep_ms], [gemm_ms], pk)
-    line["rooflines"] = roofs
+    if nbytes >= want:
+        line["rooflines"] = rooflines(args, [p], [prep_ms], [gemm_ms], pk)
+    else:
+        line["rooflines"] = ("not separable: with Q-streaming the passes interleave operand "
+                             "preparation and GEMM, and the phase events bracket the first pass")
     if args.backward:
         del ws
         torch.cuda.empty_cache()
