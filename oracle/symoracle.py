@@ -159,17 +159,23 @@ def _block(qs, dims):
     return tuple(slice(q * d, (q + 1) * d) for q, d in zip(qs, dims))
 
 
+def _as_real_or_complex(a) -> np.ndarray:
+    """float64, or complex128 for complex input (tensors may be complex, Sec. 1)."""
+    a = np.asarray(a)
+    return a.astype(np.complex128 if np.iscomplexobj(a) else np.float64, copy=False)
+
+
 def expand(group: Group, sym: Sym, red: np.ndarray) -> np.ndarray:
     """Dense tensor T[x] = red[q_0..q_{N-2}, b_0..b_{N-1}] if the sectors
     conserve charge, else 0, with q = x div D and b = x mod D."""
-    red = np.asarray(red, dtype=np.float64)
+    red = _as_real_or_complex(red)
     if red.shape != reduced_shape(group, sym):
         raise ValueError(f"reduced shape {red.shape} != {reduced_shape(group, sym)}")
     n = sym.order
     if n == 0:
         ok = group.conserves((), (), sym.charge)
-        return red.copy() if ok else np.zeros((), dtype=np.float64)
-    dense = np.zeros([group.order * d for d in sym.dims], dtype=np.float64)
+        return red.copy() if ok else np.zeros((), dtype=red.dtype)
+    dense = np.zeros([group.order * d for d in sym.dims], dtype=red.dtype)
     for qs in itertools.product(range(group.order), repeat=n):
         if group.conserves(sym.signs, qs, sym.charge):
             dense[_block(qs, sym.dims)] = red[qs[:-1]]
@@ -178,12 +184,12 @@ def expand(group: Group, sym: Sym, red: np.ndarray) -> np.ndarray:
 
 def restrict(group: Group, sym: Sym, dense: np.ndarray) -> Tuple[np.ndarray, float]:
     """Inverse of expand.  Also returns max |entry| over forbidden blocks."""
-    dense = np.asarray(dense, dtype=np.float64)
+    dense = _as_real_or_complex(dense)
     n = sym.order
     if n == 0:
         ok = group.conserves((), (), sym.charge)
-        return (dense.copy() if ok else np.zeros(())), (0.0 if ok else float(abs(dense)))
-    red = np.zeros(reduced_shape(group, sym), dtype=np.float64)
+        return (dense.copy() if ok else np.zeros((), dtype=dense.dtype)), (0.0 if ok else float(abs(dense)))
+    red = np.zeros(reduced_shape(group, sym), dtype=dense.dtype)
     worst = 0.0
     for qs in itertools.product(range(group.order), repeat=n):
         blk = dense[_block(qs, sym.dims)]
@@ -323,9 +329,9 @@ def contract_blockloop(p: Plan, u_red, v_red, counter: Optional[list] = None) ->
     W's implicit sector from W's law (Algorithm 1 for s=t=v=2); multiply the
     two blocks (numpy.tensordot) and accumulate into W's reduced form."""
     G = p.group
-    u_red = np.asarray(u_red, dtype=np.float64)
-    v_red = np.asarray(v_red, dtype=np.float64)
-    w_red = np.zeros(reduced_shape(G, p.sym_w), dtype=np.float64)
+    u_red = _as_real_or_complex(u_red)
+    v_red = _as_real_or_complex(v_red)
+    w_red = np.zeros(reduced_shape(G, p.sym_w), dtype=np.result_type(u_red, v_red))
     lw = p.lw
     wsig = dict(zip(lw, p.sym_w.signs))
     usig = dict(zip(p.lu, p.sym_u.signs))

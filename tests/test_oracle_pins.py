@@ -462,3 +462,66 @@ def test_planted_transposed_operand_is_caught():
     good, _ = O.contract_dense_einsum(p, u, v)
     q = O.plan("alk,klb->ab", g, su, sv)
     assert rel(O.contract_blockloop(q, u, v), good) > 1e-3
+
+
+# --------------------------------------------------------------------------
+# complex tensors (Sec. 1: entries may be complex; conj(T) carries the
+# negated law, i.e. negated coefficients and target charge)
+# --------------------------------------------------------------------------
+
+def _negated(sym):
+    return O.Sym(tuple(-c for c in sym.signs), tuple(-z for z in sym.charge), sym.dims)
+
+
+def _complexify(rng, a):
+    return a + 1j * rng.standard_normal(a.shape)
+
+
+@pytest.mark.parametrize("s,t,v", [(1, 1, 1), (2, 1, 2), (2, 2, 2), (0, 2, 1), (1, 0, 2), (2, 1, 0)])
+def test_complex_block_loop_matches_dense_bruteforce(s, t, v):
+    """The block loop on complex reduced forms equals the dense complex einsum
+    of the expanded tensors (Eq. ctr), with exact zeros off-sector."""
+    rng = np.random.default_rng(900 + 100 * s + 10 * t + v)
+    for G, sigma, moduli in [(3, -1, None), (4, 1, None), (6, -1, (2, 3))]:
+        p, u, vv = random_case(s, t, v, G, rng, sigma, moduli)
+        uc, vc = _complexify(rng, u), _complexify(rng, vv)
+        w3, forb = O.contract_dense_einsum(p, uc, vc)
+        assert forb == 0.0 and np.iscomplexobj(w3)
+        w4 = O.contract_blockloop(p, uc, vc)
+        assert np.iscomplexobj(w4)
+        assert rel(w4, w3) <= 1e-13
+
+
+@pytest.mark.parametrize("case", WL.small_cases()[:5], ids=lambda c: c.name)
+def test_complex_product_is_four_real_contractions(case):
+    """(Ur + i Ui)(Vr + i Vi) = (UrVr - UiVi) + i(UrVi + UiVr), contraction
+    by contraction, against the complex route."""
+    p = mk(case)
+    rng = np.random.default_rng(31)
+    ur, ui, vr, vi = (rng.standard_normal(O.reduced_shape(p.group, sy))
+                      for sy in (p.sym_u, p.sym_u, p.sym_v, p.sym_v))
+    want = O.contract_blockloop(p, ur + 1j * ui, vr + 1j * vi)
+    real = O.contract_blockloop(p, ur, vr) - O.contract_blockloop(p, ui, vi)
+    imag = O.contract_blockloop(p, ur, vi) + O.contract_blockloop(p, ui, vr)
+    assert rel(real + 1j * imag, want) <= 1e-13
+
+
+def test_conjugate_operand_carries_the_negated_law():
+    """conj(V) stored under the negated law has the same reduced array as V
+    (same allowed blocks, same implicit sector) with conjugated entries, and
+    contracting U with it matches the dense einsum of U and conj(dense V)."""
+    rng = np.random.default_rng(77)
+    for (s, t, v) in [(1, 1, 1), (2, 1, 2), (1, 2, 1)]:
+        for G, sigma, moduli in [(3, 1, None), (6, -1, (2, 3))]:
+            p, u, vv = random_case(s, t, v, G, rng, sigma, moduli)
+            uc, vc = _complexify(rng, u), _complexify(rng, vv)
+            sv_neg = _negated(p.sym_v)
+            assert O.reduced_shape(p.group, sv_neg) == O.reduced_shape(p.group, p.sym_v)
+            dense_conj = np.conj(O.expand(p.group, p.sym_v, vc))
+            assert np.array_equal(O.expand(p.group, sv_neg, np.conj(vc)), dense_conj)
+            pc = O.plan(f"{p.lu},{p.lv}->{p.lw}", p.group, p.sym_u, sv_neg)
+            got = O.contract_blockloop(pc, uc, np.conj(vc))
+            W = np.einsum(f"{p.lu},{p.lv}->{p.lw}", O.expand(p.group, p.sym_u, uc), dense_conj)
+            want, forb = O.restrict(p.group, pc.sym_w, W)
+            assert forb == 0.0
+            assert rel(got, want) <= 1e-13
