@@ -158,6 +158,22 @@ SYMCTR_API symctr_status symctr_contract(const symctr_plan* plan, const double* 
                               double* w_red, void* workspace, size_t workspace_bytes,
                               void* stream);
 
+/* Complex tensors (Sec. 1: tensor entries may be complex).  u_red, v_red and
+ * w_red hold interleaved complex128 reduced forms (real, imaginary pairs of
+ * float64; numel_u / numel_v / numel_w complex entries each).  Computes
+ *   W = einsum(op_u(U), op_v(V)),  op = complex conjugate where conj_u / conj_v
+ * is nonzero.  The plan describes the operands as contracted: the conjugate of
+ * a tensor with law (c, Z) carries the law (-c, -Z), so a plan for a
+ * conjugated operand is created with that operand's signs and charge negated
+ * (its reduced array is the same).  Runs as four real contractions of the
+ * plan's precision form on the real and imaginary parts (four times the real
+ * work), with the same workspace and error reporting as symctr_contract.
+ * Returns as symctr_contract. */
+SYMCTR_API symctr_status symctr_contract_complex(const symctr_plan* plan, int conj_u, int conj_v,
+                                                const double* u_red, const double* v_red,
+                                                double* w_red, void* workspace,
+                                                size_t workspace_bytes, void* stream);
+
 /* symctr_contract without a caller-provided workspace, for callers that cannot
  * allocate device memory (they are handed only their input and output buffers,
  * or run where no allocator may be called).  The paper has no counterpart: this

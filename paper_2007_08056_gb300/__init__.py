@@ -102,12 +102,14 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
                                         ctypes.POINTER(ctypes.c_int)]
     lib.symctr_contract_static_scratch.argtypes = [P, P, P, P, P]
     lib.symctr_selftest_bounded_wait.argtypes = [P, ctypes.c_size_t, ctypes.c_int64, P]
+    lib.symctr_contract_complex.argtypes = [P, ctypes.c_int, ctypes.c_int, P, P, P, P,
+                                            ctypes.c_size_t, P]
     lib.symctr_plan_destroy.argtypes = [P]
     lib.symctr_plan_destroy.restype = None
     for f in ("symctr_plan_create", "symctr_plan_query", "symctr_align", "symctr_contract",
               "symctr_contract_backward", "symctr_check_device_error", "symctr_profile_enable",
               "symctr_profile_read", "symctr_contract_static_scratch",
-              "symctr_selftest_bounded_wait"):
+              "symctr_selftest_bounded_wait", "symctr_contract_complex"):
         getattr(lib, f).restype = ctypes.c_int
     _LIB = lib
     return lib
@@ -222,6 +224,25 @@ class Plan:
         ws = workspace if workspace is not None else self.workspace(device=u.device)
         _check(load().symctr_contract(self._h, _ptr(u), _ptr(v), _ptr(out), _ptr(ws),
                                       ws.numel(), _stream()))
+        return out
+
+    def contract_complex(self, u: torch.Tensor, v: torch.Tensor, out: Optional[torch.Tensor] = None,
+                         conj_u: bool = False, conj_v: bool = False,
+                         workspace: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """W = einsum(op(U), op(V)) for complex128 reduced forms (op = conj where
+        asked; the plan must carry the conjugated operand's negated law)."""
+        for t, shape, name in ((u, self.shape_u, "u"), (v, self.shape_v, "v")):
+            if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.complex128):
+                raise TypeError(f"{name} must be a complex128 CUDA tensor")
+            if tuple(t.shape) != tuple(shape) or not t.is_contiguous():
+                raise ValueError(f"{name} must be contiguous with shape {tuple(shape)}")
+        if out is None:
+            out = torch.empty(self.shape_w, dtype=torch.complex128, device=u.device)
+        if out.dtype != torch.complex128 or tuple(out.shape) != tuple(self.shape_w) or not out.is_contiguous():
+            raise ValueError("out must be a contiguous complex128 tensor of the output shape")
+        ws = workspace if workspace is not None else self.workspace(device=u.device)
+        _check(load().symctr_contract_complex(self._h, int(conj_u), int(conj_v), _ptr(u), _ptr(v),
+                                              _ptr(out), _ptr(ws), ws.numel(), _stream()))
         return out
 
     def contract_static_scratch(self, u: torch.Tensor, v: torch.Tensor,

@@ -10,7 +10,7 @@
 // Two kernels: a 64x64 register-tiled kernel for GEMM-shaped problems and a
 // warp-per-row dot-product kernel for skinny ones (a few rows or columns, or
 // a tiny contracted extent), both with optional split-K through atomicAdd
-// into a zeroed output.
+// into a zeroed output (or onto the existing output in accumulate mode).
 #include <cstdint>
 
 #include "symctr_internal.h"
@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(THREADS) gemm_f64_tiled(Problem p, int ksplit,
         int mm = u_rows_fast ? e % BM : e / BK;
         int kk = u_rows_fast ? e / BM : e % BK;
         double x = 0.0;
-        if (m0 + mm < p.M && k0 + kk < kend) x = U[uoff[mm] + kuoff[kk]];
+        if (m0 + mm < p.M && k0 + kk < kend) x = U[p.es * (uoff[mm] + kuoff[kk])];
         As[kk][mm] = x;
       }
 #pragma unroll
@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(THREADS) gemm_f64_tiled(Problem p, int ksplit,
         int nn = v_rows_fast ? e % BN : e / BK;
         int kk = v_rows_fast ? e / BN : e % BK;
         double x = 0.0;
-        if (n0 + nn < p.N && k0 + kk < kend) x = V[voff[nn] + kvoff[kk]];
+        if (n0 + nn < p.N && k0 + kk < kend) x = V[p.es * (voff[nn] + kvoff[kk])];
         Bs[kk][nn] = x;
       }
       __syncthreads();
@@ -111,9 +111,9 @@ __global__ void __launch_bounds__(THREADS) gemm_f64_tiled(Problem p, int ksplit,
       for (int j = 0; j < 4; ++j) {
         int nn = tc + 16 * j;
         if (n0 + nn >= p.N) continue;
-        double* dst = W + woffr[mm] + woffc[nn];
-        if (ksplit > 1) atomicAdd(dst, acc[i][j]);
-        else *dst = acc[i][j];
+        double* dst = W + p.es * (woffr[mm] + woffc[nn]);
+        if (ksplit > 1) atomicAdd(dst, signed_result(p, acc[i][j]));
+        else store_w(p, dst, acc[i][j]);
       }
     }
   }
@@ -156,11 +156,11 @@ __global__ void __launch_bounds__(THREADS) gemm_f64_skinny(Problem p, bool long_
 #pragma unroll
     for (int s = 0; s < SKINNY_MAX; ++s) acc[s] = 0.0;
     for (int64_t k = kbeg + lane; k < kend; k += 32) {
-      double x = Lp[loff + axis_offset(Lcols, p.g, Q, k)];
+      double x = Lp[p.es * (loff + axis_offset(Lcols, p.g, Q, k))];
       int64_t sc = axis_offset(Scols, p.g, Q, k);
 #pragma unroll
       for (int s = 0; s < SKINNY_MAX; ++s)
-        if (s < nS) acc[s] = fma(x, Sp[soff[s] + sc], acc[s]);
+        if (s < nS) acc[s] = fma(x, Sp[p.es * (soff[s] + sc)], acc[s]);
     }
 #pragma unroll
     for (int s = 0; s < SKINNY_MAX; ++s) {
@@ -171,9 +171,9 @@ __global__ void __launch_bounds__(THREADS) gemm_f64_skinny(Problem p, bool long_
     if (lane == 0) {
       for (int s = 0; s < nS; ++s) {
         int64_t m = long_is_u ? l : s, n = long_is_u ? s : l;
-        double* dst = W + axis_offset(p.w.rows, p.g, Q, m) + axis_offset(p.w.cols, p.g, Q, n);
-        if (ksplit > 1) atomicAdd(dst, acc[s]);
-        else *dst = acc[s];
+        double* dst = W + p.es * (axis_offset(p.w.rows, p.g, Q, m) + axis_offset(p.w.cols, p.g, Q, n));
+        if (ksplit > 1) atomicAdd(dst, signed_result(p, acc[s]));
+        else store_w(p, dst, acc[s]);
       }
     }
   }
@@ -194,7 +194,7 @@ __global__ void zero_w_entries(Problem p, double* __restrict__ W) {
     int64_t r = i - b * p.M * p.N;
     int64_t m = r / p.N, n = r % p.N;
     int Q = batch_irrep(p, (int)b);
-    W[axis_offset(p.w.rows, p.g, Q, m) + axis_offset(p.w.cols, p.g, Q, n)] = 0.0;
+    W[p.es * (axis_offset(p.w.rows, p.g, Q, m) + axis_offset(p.w.cols, p.g, Q, n))] = 0.0;
   }
 }
 
@@ -214,7 +214,7 @@ cudaError_t launch_gemm_f64(const Problem& p, const double* u, const double* v, 
     int ksplit = 1;
     int64_t want_warps = (int64_t)sms * (THREADS / 32) * 4;
     while (warps * ksplit < want_warps && p.K / (ksplit * 2) >= 256) ksplit *= 2;
-    if (ksplit > 1) {
+    if (ksplit > 1 && !p.accumulate) {
       zero_w_entries<<<sms * 4, 256, 0, st>>>(p, w);
       ++g_kernel_launches;
     }
@@ -228,8 +228,10 @@ cudaError_t launch_gemm_f64(const Problem& p, const double* u, const double* v, 
   int64_t tiles = ((p.M + BM - 1) / BM) * ((p.N + BN - 1) / BN) * p.n_q;
   int ksplit = 1;
   while (tiles * ksplit < target && p.K / (ksplit * 2) >= 512) ksplit *= 2;
-  if (ksplit > 1) zero_w_entries<<<sms * 4, 256, 0, st>>>(p, w);
-  ++g_kernel_launches;
+  if (ksplit > 1 && !p.accumulate) {
+    zero_w_entries<<<sms * 4, 256, 0, st>>>(p, w);
+    ++g_kernel_launches;
+  }
   int64_t blocks = tiles * ksplit;
   int64_t cap = (int64_t)sms * 4;
   gemm_f64_tiled<<<(int)(blocks < cap ? blocks : cap), THREADS, 0, st>>>(

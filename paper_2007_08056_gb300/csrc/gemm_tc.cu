@@ -355,6 +355,28 @@ __device__ __forceinline__ void f32_to_f64_batch(const uint32_t (&u)[B], double 
   }
 }
 
+// Map-back stores of a batch of results of one column (rows m_first, + rstep,
+// ...): plain stores, or (complex products) adds, with the problem's sign; the
+// output mode is uniform, so the plain path loads nothing from W.
+template <int B, bool GEN>
+__device__ __forceinline__ void store_batch(const Problem& p, double* w, const int64_t (&ro)[B],
+                                            int64_t co, const double (&d)[B], int64_t m_first,
+                                            int rstep) {
+  if constexpr (!GEN) {
+#pragma unroll
+    for (int j = 0; j < B; ++j)
+      if (m_first + rstep * j < p.M) w[ro[j] + co] = d[j];
+  } else if (!p.accumulate) {
+#pragma unroll
+    for (int j = 0; j < B; ++j)
+      if (m_first + rstep * j < p.M) w[(int64_t)p.es * (ro[j] + co)] = signed_result(p, d[j]);
+  } else {
+#pragma unroll
+    for (int j = 0; j < B; ++j)
+      if (m_first + rstep * j < p.M) w[(int64_t)p.es * (ro[j] + co)] += signed_result(p, d[j]);
+  }
+}
+
 // Descriptor offset of slice tile `i`, K step `kk` (16-byte units).
 __host__ __device__ constexpr uint64_t dofs(int i, int kk) {
   return (uint64_t)((i * TILE_BYTES + kk * 32) >> 4);
@@ -460,7 +482,9 @@ __host__ __device__ constexpr size_t tile_region_bytes() {
                                                                : STAGE_BYTES_EPI;
 }
 
-template <int KIND, int S, int STAGES>
+// GEN: the general output mode (complex element stride, sign, accumulate);
+// real contractions use the plain instance, whose epilogue is unchanged.
+template <int KIND, int S, int STAGES, bool GEN>
 __global__ void __launch_bounds__(NTHREADS, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap tma_a, const __grid_constant__ CUtensorMap tma_b,
                    const __grid_constant__ TcArgs args) {
@@ -773,9 +797,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
             double d[BATCH];
             i64_scaled_batch<BATCH>(Rv, ex, d);
-#pragma unroll
-            for (int j = 0; j < BATCH; ++j)
-              if (m0 + rb + RSTEP * j < p.M) args.w[ro[j] + co] = d[j];
+            store_batch<BATCH, GEN>(p, args.w, ro, co, d, m0 + rb, RSTEP);
           }
         } else {
           uint32_t a[BATCH];
@@ -787,9 +809,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           }
           double d[BATCH];
           f32_to_f64_batch<BATCH>(a, d);
-#pragma unroll
-          for (int j = 0; j < BATCH; ++j)
-            if (m0 + rb + RSTEP * j < p.M) args.w[ro[j] + co] = d[j];
+          store_batch<BATCH, GEN>(p, args.w, ro, co, d, m0 + rb, RSTEP);
         }
       }
     }
@@ -818,9 +838,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           }
           double d[BATCH];
           i64_scaled_batch<BATCH>(Rv, ex, d);
-#pragma unroll
-          for (int j = 0; j < BATCH; ++j)
-            if (m0 + rb + RSTEP * j < p.M) args.w[ro[j] + co] = d[j];
+          store_batch<BATCH, GEN>(p, args.w, ro, co, d, m0 + rb, RSTEP);
         }
       }
     }
@@ -888,8 +906,8 @@ bool make_map(CUtensorMap* map, const void* base, bool is_f32, int64_t kpad, int
   return r == CUDA_SUCCESS;
 }
 
-template <int KIND, int S, int STAGES>
-cudaError_t launch_tc(const Problem& p, const Tables& tab, const void* a, const void* bop, const int32_t* eu,
+template <int KIND, int S, int STAGES, bool GEN>
+cudaError_t launch_tc_mode(const Problem& p, const Tables& tab, const void* a, const void* bop, const int32_t* eu,
                       const int32_t* ev, int64_t kpad, double* w, unsigned* err, int ksplit,
                       unsigned long long* wacc, unsigned* tile_ctr, cudaStream_t st) {
   const bool f32 = KIND == MODE_TF32;
@@ -916,7 +934,7 @@ cudaError_t launch_tc(const Problem& p, const Tables& tab, const void* a, const 
   args.wcol = tab.wcol;
   size_t smem = 1024 + tile_region_bytes<S, STAGES>() + 8 * (2 * STAGES + 6) + 8 * TN + 4 * TN +
                 8 * TM + 4 * TM + 16 + 64;
-  auto kern = gemm_tc_kernel<KIND, S, STAGES>;
+  auto kern = gemm_tc_kernel<KIND, S, STAGES, GEN>;
   static bool attr_set[64] = {};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
@@ -942,6 +960,17 @@ cudaError_t launch_tc(const Problem& p, const Tables& tab, const void* a, const 
   cudaError_t le = cudaLaunchKernelEx(&cfg, kern, ma, mb, args);
   ++g_kernel_launches;
   return le;
+}
+
+template <int KIND, int S, int STAGES>
+cudaError_t launch_tc(const Problem& p, const Tables& tab, const void* a, const void* bop, const int32_t* eu,
+                      const int32_t* ev, int64_t kpad, double* w, unsigned* err, int ksplit,
+                      unsigned long long* wacc, unsigned* tile_ctr, cudaStream_t st) {
+  if (p.es == 1 && !p.negate && !p.accumulate)
+    return launch_tc_mode<KIND, S, STAGES, false>(p, tab, a, bop, eu, ev, kpad, w, err, ksplit, wacc,
+                                                  tile_ctr, st);
+  return launch_tc_mode<KIND, S, STAGES, true>(p, tab, a, bop, eu, ev, kpad, w, err, ksplit, wacc,
+                                               tile_ctr, st);
 }
 
 }  // namespace

@@ -473,20 +473,40 @@ symctr_status cuda_status(cudaError_t e, const char* where) {
   return fail(SYMCTR_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
+// How one real contraction reads and writes: element stride (2 when the
+// pointers address the real or imaginary parts of interleaved complex data),
+// output mode W = (-)R or W += (-)R, whether the workspace's error word
+// is cleared first, and how many doubles of W are zeroed up front (the entries
+// of irreps that carry no work; -1: W's reduced form).
+struct RunMode {
+  int es = 1;
+  int negate = 0;
+  int accumulate = 0;
+  bool clear_err = true;
+  int64_t fill_n = -1;
+};
+
 symctr_status run_contract_body(const symctr_plan* P, const double* u, const double* v,
-                                double* w, void* ws, size_t ws_bytes, cudaStream_t st);
+                                double* w, void* ws, size_t ws_bytes, cudaStream_t st,
+                                const RunMode& mode);
 
 symctr_status run_contract(const symctr_plan* P, const double* u, const double* v, double* w,
-                           void* ws, size_t ws_bytes, cudaStream_t st) {
+                           void* ws, size_t ws_bytes, cudaStream_t st,
+                           const RunMode& mode = RunMode()) {
   long long before = g_kernel_launches;
-  symctr_status s = run_contract_body(P, u, v, w, ws, ws_bytes, st);
+  symctr_status s = run_contract_body(P, u, v, w, ws, ws_bytes, st, mode);
   P->last_launches = (int)(g_kernel_launches - before);
   return s;
 }
 
 symctr_status run_contract_body(const symctr_plan* P, const double* u, const double* v,
-                                double* w, void* ws, size_t ws_bytes, cudaStream_t st) {
-  const Problem& pr = P->prob;
+                                double* w, void* ws, size_t ws_bytes, cudaStream_t st,
+                                const RunMode& mode) {
+  Problem prob = P->prob;
+  prob.es = mode.es;
+  prob.negate = mode.negate;
+  prob.accumulate = mode.accumulate;
+  const Problem& pr = prob;
   if (!w || (!u && P->numel_u) || (!v && P->numel_v))
     return fail(SYMCTR_ERR_NULLPTR, "NULL tensor pointer");
   if (!ws || ws_bytes < P->ws_bytes_min)
@@ -494,11 +514,12 @@ symctr_status run_contract_body(const symctr_plan* P, const double* u, const dou
   char* base = (char*)ws;
   unsigned* err = (unsigned*)base;
   // header: error word (byte 0) and the prep kernel's grid-barrier counter (byte 64)
-  cudaError_t e = cudaMemsetAsync(err, 0, 128, st);
+  cudaError_t e = mode.clear_err ? cudaMemsetAsync(err, 0, 128, st) : cudaMemsetAsync(base + 64, 0, 64, st);
   if (e != cudaSuccess) return cuda_status(e, "clear workspace header");
   // Entries of W whose irrep Q carries no work are zero.
-  if ((int64_t)pr.n_q * pr.M * pr.N < P->numel_w) {
-    e = launch_fill_zero(w, P->numel_w, st);
+  const int64_t fill_n = mode.fill_n < 0 ? P->numel_w : mode.fill_n;
+  if ((int64_t)pr.n_q * pr.M * pr.N < P->numel_w && fill_n > 0) {
+    e = launch_fill_zero(w, fill_n, st);
     if (e != cudaSuccess) return cuda_status(e, "zero fill");
   }
   if (pr.n_q == 0) return SYMCTR_OK;
@@ -716,7 +737,38 @@ symctr_status symctr_contract_backward(const symctr_plan* P, const double* gw, c
     if (s != SYMCTR_OK) return s;
   }
   if (gv) {
-    symctr_status s = run_contract(P->bwd_v, u, gw, gv, ws, ws_bytes, st);
+    RunMode m;
+    m.clear_err = gu == nullptr;   // keep a device error of the first contraction
+    symctr_status s = run_contract(P->bwd_v, u, gw, gv, ws, ws_bytes, st, m);
+    if (s != SYMCTR_OK) return s;
+  }
+  return SYMCTR_OK;
+}
+
+symctr_status symctr_contract_complex(const symctr_plan* P, int conj_u, int conj_v, const double* u,
+                                      const double* v, double* w, void* ws, size_t ws_bytes,
+                                      void* stream) {
+  if (!P) return fail(SYMCTR_ERR_NULLPTR, "NULL plan");
+  if (!w || !u || !v) return fail(SYMCTR_ERR_NULLPTR, "NULL tensor pointer");
+  cudaStream_t st = (cudaStream_t)stream;
+  const double su = conj_u ? -1.0 : 1.0, sv = conj_v ? -1.0 : 1.0;
+  // (Ur + i su Ui)(Vr + i sv Vi) = Ur Vr - su sv Ui Vi + i (sv Ur Vi + su Ui Vr):
+  // four real contractions on the real (+0) and imaginary (+1) parts
+  struct Term {
+    int ui, vi, wi;
+    double sign;
+    int accumulate;
+  };
+  const Term terms[4] = {{0, 0, 0, 1.0, 0}, {1, 1, 0, -su * sv, 1}, {0, 1, 1, sv, 0}, {1, 0, 1, su, 1}};
+  for (int k = 0; k < 4; ++k) {
+    RunMode m;
+    m.es = 2;
+    m.negate = terms[k].sign < 0 ? 1 : 0;
+    m.accumulate = terms[k].accumulate;
+    m.clear_err = k == 0;
+    m.fill_n = k == 0 ? 2 * P->numel_w : 0;   // both parts of W once
+    symctr_status s = run_contract(P, u + terms[k].ui, v + terms[k].vi, w + terms[k].wi, ws, ws_bytes,
+                                   st, m);
     if (s != SYMCTR_OK) return s;
   }
   return SYMCTR_OK;

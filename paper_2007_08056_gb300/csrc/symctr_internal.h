@@ -113,7 +113,29 @@ struct Problem {
   int64_t M, N, K;
   OperandMap u, v, w; // U: rows = free-U, cols = contracted; V: rows = free-V, cols = contracted;
                       // W: rows = free-U, cols = free-V
+  // element stride of U, V and W in doubles: 1 for real data, 2 when the
+  // reduced forms hold interleaved complex entries and the pointers address
+  // their real or imaginary parts
+  int es = 1;
+  int negate = 0;     // W = (-)result, or W += (-)result when accumulate
+  int accumulate = 0;
 };
+
+#ifdef __CUDACC__
+// The result with the problem's sign (a sign-bit flip, no float64 arithmetic).
+__device__ __forceinline__ double signed_result(const Problem& p, double x) {
+  return p.negate ? __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ull) : x;
+}
+
+// Store of one result into W under the problem's output mode.
+__device__ __forceinline__ void store_w(const Problem& p, double* dst, double x) {
+  x = signed_result(p, x);
+  if (p.accumulate)
+    *dst += x;
+  else
+    *dst = x;
+}
+#endif
 
 SC_HD int batch_irrep(const Problem& p, int b) { return p.q_single >= 0 ? p.q_single : p.q_base + b; }
 

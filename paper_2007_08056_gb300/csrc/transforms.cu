@@ -283,14 +283,14 @@ __device__ void scan_tile(const PrepArgs& a, int op, uint32_t tile, int64_t* rof
       if (fast_rows) {
         // lanes walk rows (contiguous), warps walk columns
         const bool rok = r0 + tx < R;
-        const double* rowp = src + roff[tx];
+        const double* rowp = src + (int64_t)p.es * roff[tx];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           double x[PER / 2];
 #pragma unroll
           for (int i = 0; i < PER / 2; ++i) {
             const int cc = ty + (h * (PER / 2) + i) * (THREADS / 32);
-            x[i] = (rok && c0 + cc < se) ? rowp[co[cc]] : 0.0;
+            x[i] = (rok && c0 + cc < se) ? rowp[(int64_t)p.es * co[cc]] : 0.0;
           }
 #pragma unroll
           for (int i = 0; i < PER / 2; ++i) mx = max(mx, abs_bits(x[i]));
@@ -302,7 +302,7 @@ __device__ void scan_tile(const PrepArgs& a, int op, uint32_t tile, int64_t* rof
         for (int h = 0; h < RPW; ++h) {
           const int rr = ty + h * (THREADS / 32);
           const bool rok = r0 + rr < R;
-          const double* rowp = src + roff[rr];
+          const double* rowp = src + (int64_t)p.es * roff[rr];
           double2 x[SCAN_COLS / 64];
 #pragma unroll
           for (int i = 0; i < SCAN_COLS / 64; ++i) {
@@ -320,12 +320,12 @@ __device__ void scan_tile(const PrepArgs& a, int op, uint32_t tile, int64_t* rof
         for (int h = 0; h < RPW; ++h) {
           const int rr = ty + h * (THREADS / 32);
           const bool rok = r0 + rr < R;
-          const double* rowp = src + roff[rr];
+          const double* rowp = src + (int64_t)p.es * roff[rr];
           double x[SCAN_COLS / 32];
 #pragma unroll
           for (int i = 0; i < SCAN_COLS / 32; ++i) {
             const int cc = tx + 32 * i;
-            x[i] = (rok && c0 + cc < se) ? rowp[co[cc]] : 0.0;
+            x[i] = (rok && c0 + cc < se) ? rowp[(int64_t)p.es * co[cc]] : 0.0;
           }
 #pragma unroll
           for (int i = 0; i < SCAN_COLS / 32; ++i) mxr[h] = max(mxr[h], abs_bits(x[i]));
@@ -463,7 +463,7 @@ __device__ void slice_unit(const PrepArgs& a, int op, uint32_t unit, int64_t* ro
         for (int rg = 0; rg < RPW; ++rg) {
           const int rr = ty + rg * (THREADS / 32);
           x[g][rg] = (c < Cn && r0 + rr < R)
-                         ? *reinterpret_cast<const double2*>(src + roff[rr] + co[g0 + g])
+                         ? *reinterpret_cast<const double2*>(src + (int64_t)p.es * roff[rr] + co[g0 + g])
                          : make_double2(0.0, 0.0);
         }
       }
@@ -498,7 +498,7 @@ __device__ void slice_unit(const PrepArgs& a, int op, uint32_t unit, int64_t* ro
         const int rr = ty + rg * (THREADS / 32);
         const int64_t r = r0 + rr;
         if (r >= R) continue;
-        const double* rowp = src + roff[rr];
+        const double* rowp = src + (int64_t)p.es * roff[rr];
         double x0 = 0.0, x1 = 0.0;
         if (pair) {
           if (c < Cn) {
@@ -507,8 +507,8 @@ __device__ void slice_unit(const PrepArgs& a, int op, uint32_t unit, int64_t* ro
             x1 = v2.y;
           }
         } else {
-          if (c < Cn) x0 = rowp[co0];
-          if (c + 1 < Cn) x1 = rowp[co1];
+          if (c < Cn) x0 = rowp[(int64_t)p.es * co0];
+          if (c + 1 < Cn) x1 = rowp[(int64_t)p.es * co1];
         }
         put_pair<S>(a, op, x0, x1, S > 0 ? rk0[rr] : 0, (brow + r) * kpad + c, slice_stride);
       }
@@ -516,7 +516,7 @@ __device__ void slice_unit(const PrepArgs& a, int op, uint32_t unit, int64_t* ro
     return;
   }
   const bool rok = r0 + tx < R;
-  const double* rowp = src + roff[tx];
+  const double* rowp = src + (int64_t)p.es * roff[tx];
 #pragma unroll 1
   for (int sub = 0; sub < SLICE_GROUP; ++sub) {
     const int64_t c0 = cu + sub * SLICE_COLS;
@@ -527,7 +527,7 @@ __device__ void slice_unit(const PrepArgs& a, int op, uint32_t unit, int64_t* ro
 #pragma unroll
       for (int i = 0; i < SLICE_COLS / (THREADS / 32); ++i) {
         const int cc = ty + i * (THREADS / 32);
-        x[i] = (rok && c0 + cc < Cn) ? rowp[coff[sub * SLICE_COLS + cc]] : 0.0;
+        x[i] = (rok && c0 + cc < Cn) ? rowp[(int64_t)p.es * coff[sub * SLICE_COLS + cc]] : 0.0;
       }
 #pragma unroll
       for (int i = 0; i < SLICE_COLS / (THREADS / 32); ++i) tilebuf[tx][ty + i * (THREADS / 32)] = x[i];
@@ -677,8 +677,9 @@ cudaError_t launch_prep(const Problem& p, const Tables& t, bool split, int n_sli
   a.part[1] = partials ? partials + (int64_t)a.parts * p.n_q * p.M : nullptr;
   a.fast_rows[0] = rows_fast(p.u);
   a.fast_rows[1] = rows_fast(p.v);
-  a.pair_ok[0] = !a.fast_rows[0] && pairs_aligned(p.u);
-  a.pair_ok[1] = !a.fast_rows[1] && pairs_aligned(p.v);
+  // 16-byte pair loads need adjacent real entries (not interleaved complex ones)
+  a.pair_ok[0] = p.es == 1 && !a.fast_rows[0] && pairs_aligned(p.u);
+  a.pair_ok[1] = p.es == 1 && !a.fast_rows[1] && pairs_aligned(p.v);
   a.err = err;
   a.barrier = barrier;
   a.zero64 = zero64;
