@@ -433,6 +433,78 @@ def run_ours(args, rank, world):
     return line
 
 
+def run_complex(args, rank, world):
+    """The MPS transfer step with complex tensors, E' = sum E A conj(A): X = E.A,
+    then E' = X.conj(A), conj(A) carrying A's negated law.  Useful flops count
+    the four real products of each complex contraction."""
+    import torch
+    import oracle as O
+    import paper_2007_08056_gb300 as sc
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+    dev = torch.device("cuda")
+    g = WL.MPS_G
+    sE, sA = spec(WL.MPS_E), spec(WL.MPS_A)
+    negA = (tuple(-c for c in sA[0]), tuple(-z for z in sA[1]), sA[2])
+    rng = np.random.default_rng(2101)
+    shE = WL.reduced_shape((g,), WL.MPS_E.dims)
+    shA = WL.reduced_shape((g,), WL.MPS_A.dims)
+    Eh = rng.standard_normal(shE) + 1j * rng.standard_normal(shE)
+    Ah = rng.standard_normal(shA) + 1j * rng.standard_normal(shA)
+    p1 = sc.Plan(WL.MPS_STEP1, (g,), sE, sA, args.precision)
+    p2 = sc.Plan(WL.MPS_STEP2, (g,), p1.sym_w, negA, args.precision)
+    E, A = torch.from_numpy(Eh).to(dev), torch.from_numpy(Ah).to(dev)
+    X = torch.empty(p1.shape_w, dtype=torch.complex128, device=dev)
+    out = torch.empty(p2.shape_w, dtype=torch.complex128, device=dev)
+
+    def step(e=E, a=A):
+        p1.contract_complex(e, a, out=X)
+        p2.contract_complex(X, a, out=out, conj_v=True)
+        return out
+
+    flops = 4 * (p1.useful_flops + p2.useful_flops)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    ev_s, ev_e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(args.steps):
+            flush.fill_(1)
+            ev_s.record()
+            fn()
+            ev_e.record()
+            ev_e.synchronize()
+            ts.append(ev_s.elapsed_time(ev_e))
+        return statistics.mean(ts)
+
+    ms = max_over_ranks(timed(step), world, dev)
+    p2.check_device_error()
+    G = O.Group((g,))
+    o1 = O.plan(WL.MPS_STEP1, G, O.Sym(*sE), O.Sym(*sA))
+    o2 = O.plan(WL.MPS_STEP2, G, o1.sym_w, O.Sym(*negA))
+    want = O.contract_blockloop(o2, O.contract_blockloop(o1, Eh, Ah), np.conj(Ah))
+    got = step().cpu().numpy()
+    hin = [torch.from_numpy(x).pin_memory() for x in (Eh, Ah)]
+    dins = [torch.empty(x.shape, dtype=torch.complex128, device=dev) for x in (Eh, Ah)]
+    hout = torch.empty(tuple(out.shape), dtype=torch.complex128).pin_memory()
+
+    def e2e_step():
+        for h, d in zip(hin, dins):
+            d.copy_(h, non_blocking=True)
+        o = step(*dins)
+        hout.copy_(o, non_blocking=True)
+    ms_e2e = max_over_ranks(timed(e2e_step), world, dev)
+    return {"workload": "mps_transfer_Z8_complex (X=E.A, E'=X.conj(A))", "precision": args.precision,
+            "ms_per_step": round(ms, 4), "useful_tflops": round(replicas_value(flops, ms, world), 4),
+            "useful_gflop_per_step": flops / 1e9,
+            "rel_err_vs_oracle": float(f"{np.linalg.norm(got - want) / np.linalg.norm(want):.3e}"),
+            "e2e": {"value": round(replicas_value(flops, ms_e2e, world), 4), "ms_per_step": round(ms_e2e, 4),
+                    "h2d_bytes_per_step": int(Eh.nbytes + Ah.nbytes), "d2h_bytes_per_step": int(out.numel() * 16)}}
+
+
 def run_device(args, rank, world):
     """Workloads whose operands are drawn on the device: config 5 (the
     CC-ladder contraction at virtual 512 / occupied 128 with sector dims 512/G
@@ -577,6 +649,8 @@ def main():
     ap.add_argument("--case", default="CC1_a", help="table: a Table-2 case (" + ", ".join(WL.TABLE2) + ")")
     ap.add_argument("--sweep-g", type=int, default=16, help="G of the sweep workload (config 5)")
     ap.add_argument("--backward", action="store_true", help="sweep: time the backward pair too")
+    ap.add_argument("--complex", action="store_true",
+                    help="mps: complex tensors, E' = sum E A conj(A) (four real products per contraction)")
     ap.add_argument("--precision", choices=["split_bf16", "fp64", "tf32"], default="split_bf16")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -598,8 +672,12 @@ def main():
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         torch.distributed.init_process_group("nccl")
-    line = (run_device(args, rank, world) if args.workload in ("sweep", "table")
-            else run_ours(args, rank, world))
+    if args.workload in ("sweep", "table"):
+        line = run_device(args, rank, world)
+    elif args.complex:
+        line = run_complex(args, rank, world)
+    else:
+        line = run_ours(args, rank, world)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
