@@ -108,6 +108,8 @@ def test_error_statuses():
     assert plan_status("abkl,klij->abij", (3,), pp, pp, ((-1, -1, 1, 1), (0,), (2,) * 4)) == 0
     big = ((1,) * 9, (0,), (1,) * 9)
     assert plan_status("abcdefghi,a->bcdefghi", (2,), big, ((-1,), (0,), (1,))) == 5
+    # an empty sector (D = 0) is rejected
+    assert plan_status("abkl,klij->abij", (3,), pp, ((1, 1, -1, -1), (0,), (2, 2, 2, 0))) == 3
 
 
 def test_null_arguments():
@@ -118,6 +120,8 @@ def test_null_arguments():
     assert st == 6
     assert lib.symctr_plan_query(None, None) == 6
     assert lib.symctr_contract(None, None, None, None, None, 0, None) == 6
+    assert lib.symctr_contract_complex(None, 0, 0, None, None, None, None, 0, None) == 6
+    assert lib.symctr_selftest_bounded_wait(None, 0, 0, None) == 6
 
 
 def test_workspace_too_small_is_rejected_before_any_launch():

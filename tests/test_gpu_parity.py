@@ -253,3 +253,20 @@ def test_autograd_function(sc):
     wref = O.contract_blockloop(o, u, v)
     assert rel(host(ut.grad), O.grad_u(o, 2 * wref, v)) <= 1e-12
     assert rel(host(vt.grad), O.grad_v(o, u, 2 * wref)) <= 1e-12
+
+
+@pytest.mark.parametrize("precision", ["fp64", "split_bf16", "tf32"])
+def test_no_irrep_carries_work(sc, precision):
+    """A full contraction whose laws admit no irrep Q (s = t = 0 and
+    Z_U != sigma Z_V): every block product is forbidden, W is exactly zero."""
+    su, sv = ((1, -1), (1,), (3, 3)), ((1, -1), (2,), (3, 3))
+    p = sc.Plan("ij,ij->", (4,), su, sv, precision)
+    assert p.info.n_q == 0
+    o = oplan("ij,ij->", (4,), su, sv)
+    rng = np.random.default_rng(5)
+    u = rng.standard_normal(O.reduced_shape(o.group, o.sym_u))
+    v = rng.standard_normal(O.reduced_shape(o.group, o.sym_v))
+    w = p.contract(dev(u), dev(v))
+    p.check_device_error()
+    assert O.contract_blockloop(o, u, v) == 0.0
+    assert host(w) == 0.0
