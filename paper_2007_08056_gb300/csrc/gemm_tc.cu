@@ -889,9 +889,39 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// 3-D map over [planes][rows][kpad] with a (64-byte, 128-row, 1) box.
+bool encode_map(CUtensorMap* map, const void* base, bool is_f32, int64_t kpad, int64_t rows,
+                int64_t planes);
+
+// 3-D map over [planes][rows][kpad] with a (64-byte, 128-row, 1) box.  The
+// encoding is a pure function of its arguments, so the last few are kept per
+// host thread (a contraction called again on the same workspace reuses them).
 bool make_map(CUtensorMap* map, const void* base, bool is_f32, int64_t kpad, int64_t rows,
               int64_t planes) {
+  struct Entry {
+    const void* base;
+    bool f32;
+    int64_t kpad, rows, planes;
+    CUtensorMap map;
+  };
+  constexpr int kEntries = 8;
+  thread_local Entry cache[kEntries];
+  thread_local int used = 0, next = 0;
+  for (int i = 0; i < used; ++i) {
+    const Entry& e = cache[i];
+    if (e.base == base && e.f32 == is_f32 && e.kpad == kpad && e.rows == rows && e.planes == planes) {
+      *map = e.map;
+      return true;
+    }
+  }
+  if (!encode_map(map, base, is_f32, kpad, rows, planes)) return false;
+  cache[next] = Entry{base, is_f32, kpad, rows, planes, *map};
+  next = (next + 1) % kEntries;
+  if (used < kEntries) ++used;
+  return true;
+}
+
+bool encode_map(CUtensorMap* map, const void* base, bool is_f32, int64_t kpad, int64_t rows,
+                int64_t planes) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
   int eb = is_f32 ? 4 : 2;
