@@ -185,6 +185,8 @@ class Plan:
             n = len(spec.dims)
             return tuple([G] * (n - 1) + list(spec.dims)) if n else ()
         self.shape_u, self.shape_v, self.shape_w = shape(su), shape(sv), shape(self.sym_w)
+        self._size_u, self._size_v, self._size_w = (torch.Size(self.shape_u), torch.Size(self.shape_v),
+                                                     torch.Size(self.shape_w))
         self._ws = None
 
     def __del__(self):
@@ -214,16 +216,23 @@ class Plan:
             raise ValueError(f"{name} must be contiguous")
 
     # -- operations ------------------------------------------------------------
+    def _ok64(self, t, size) -> bool:
+        return (type(t) is torch.Tensor and t.dtype is torch.float64 and t.is_cuda
+                and t.shape == size and t.is_contiguous())
+
     def contract(self, u: torch.Tensor, v: torch.Tensor, out: Optional[torch.Tensor] = None,
                  workspace: Optional[torch.Tensor] = None) -> torch.Tensor:
-        self._dev64(u, self.shape_u, "u")
-        self._dev64(v, self.shape_v, "v")
+        # one combined check on the common path; the detailed ones name the culprit
+        if not (self._ok64(u, self._size_u) and self._ok64(v, self._size_v)):
+            self._dev64(u, self.shape_u, "u")
+            self._dev64(v, self.shape_v, "v")
         if out is None:
             out = torch.empty(self.shape_w, dtype=torch.float64, device=u.device)
-        self._dev64(out, self.shape_w, "out")
+        elif not self._ok64(out, self._size_w):
+            self._dev64(out, self.shape_w, "out")
         ws = workspace if workspace is not None else self.workspace(device=u.device)
-        _check(load().symctr_contract(self._h, _ptr(u), _ptr(v), _ptr(out), _ptr(ws),
-                                      ws.numel(), _stream()))
+        _check(_LIB.symctr_contract(self._h, u.data_ptr(), v.data_ptr(), out.data_ptr(), ws.data_ptr(),
+                                    ws.numel(), torch.cuda.current_stream().cuda_stream))
         return out
 
     def contract_complex(self, u: torch.Tensor, v: torch.Tensor, out: Optional[torch.Tensor] = None,
