@@ -965,7 +965,7 @@ cudaError_t launch_tc_mode(const Problem& p, const Tables& tab, const void* a, c
   size_t smem = 1024 + tile_region_bytes<S, STAGES>() + 8 * (2 * STAGES + 6) + 8 * TN + 4 * TN +
                 8 * TM + 4 * TM + 16 + 64;
   auto kern = gemm_tc_kernel<KIND, S, STAGES, GEN>;
-  static bool attr_set[64] = {};
+  thread_local bool attr_set[64] = {};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
   if (!attr_set[dev]) {

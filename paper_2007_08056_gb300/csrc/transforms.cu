@@ -643,15 +643,24 @@ cudaError_t launch_prep(const Problem& p, const Tables& t, bool split, int n_sli
     case 5: kern = prep_kernel<5>; break;
     default: kern = prep_kernel<6>; break;
   }
-  static int max_blocks[kMaxSlices + 1] = {};
-  if (max_blocks[S] == 0) {
-    int dev = 0, sms = 0, per = 0;
+  // co-resident CTAs of the cooperative launch, per instance and device (kept
+  // per host thread: no shared mutable state between threads)
+  thread_local int max_blocks[kMaxSlices + 1][16] = {};
+  int dev = 0;
+  {
     cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 16) return cudaErrorInvalidDevice;
+  }
+  if (max_blocks[S][dev] == 0) {
+    int sms = 0, per = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, THREADS, 0);
     if (e != cudaSuccess) return e;
-    max_blocks[S] = sms * (per < 4 ? per : 4);
+    if (per < 1) return cudaErrorInvalidConfiguration;
+    max_blocks[S][dev] = sms * (per < 4 ? per : 4);
   }
+  const int cap = max_blocks[S][dev];
   int64_t work = 0;
   {
     int64_t rt_u = (p.M + TILE - 1) / TILE, rt_v = (p.N + TILE - 1) / TILE;
@@ -660,7 +669,7 @@ cudaError_t launch_prep(const Problem& p, const Tables& t, bool split, int n_sli
     if (work > 0xFFFFFFFFll / 2 || (rt_u + rt_v) * (int64_t)prep_scan_parts(p) * p.n_q > 0xFFFFFFFFll / 2)
       return cudaErrorInvalidValue;
   }
-  int grid = (int)(work < max_blocks[S] ? (work > 0 ? work : 1) : max_blocks[S]);
+  int grid = (int)(work < cap ? (work > 0 ? work : 1) : cap);
   PrepArgs a;
   a.p = p;
   a.t = t;
