@@ -270,3 +270,27 @@ def test_no_irrep_carries_work(sc, precision):
     p.check_device_error()
     assert O.contract_blockloop(o, u, v) == 0.0
     assert host(w) == 0.0
+
+
+@pytest.mark.parametrize("k_sectors,D", [(2, 64), (2, 4096), (4, 8192)])
+def test_split_bit_exact_on_integer_inputs(sc, k_sectors, D):
+    """Integer entries with |x| <= 2^12 are exactly two balanced BF16 digits
+    at their row scale, so every slice-pair product lands in the exact
+    diagonals 0..2: the split form must return the exact integer matrix
+    product rounded once to float64, bit for bit.  Rows at the maximum
+    magnitude (all digits at the bound) drive every drain to its limit."""
+    G = k_sectors
+    su = ((1, -1), (0,), (128, D))
+    sv = ((1, -1), (0,), (D, 96))
+    rng = np.random.default_rng(600 + D)
+    u = rng.integers(-4096, 4097, size=(G, 128, D)).astype(np.float64)
+    v = rng.integers(-4096, 4097, size=(G, D, 96)).astype(np.float64)
+    u[:, :4, :] = 4096.0          # all-maximum rows and columns
+    v[:, :, :3] = 4096.0
+    u[:, 4:6, :] = -4096.0
+    p = sc.Plan("ij,jk->ik", (G,), su, sv, "split_bf16")
+    got = host(p.contract(dev(u), dev(v)))
+    p.check_device_error()
+    # exact integer products (|sum| <= D * 2^24 < 2^63), rounded once to float64
+    want = np.stack([np.matmul(u[q].astype(np.int64), v[q].astype(np.int64)) for q in range(G)])
+    assert np.array_equal(got, want.astype(np.float64))
