@@ -21,16 +21,18 @@
 //   float64 with the row and column exponents applied (integer arithmetic
 //   only: GB300 has little float64 throughput).
 // TF32 form: one FP32 operand per side (rounded to TF32), kind::tf32,
-//   one accumulator, FP32 -> float64 in the epilogue.
+//   one 128 x 256 accumulator, FP32 -> float64 in the epilogue.
 //
 // CTA: 384 threads.  warp 0 = TMA producer, warp 1 = MMA issuer and TMEM
 // owner, warps 2-3 idle, warps 4..11 = epilogue (two warps per 32-lane TMEM
-// quadrant, one per half of the 128 columns).  Warpgroup 0 gives registers
+// quadrant, one per half of the tile's columns).  Warpgroup 0 gives registers
 // to the two epilogue warpgroups (setmaxnreg 56 / 224), which hold the int32
 // running sums of their 64 columns.  Optional split-K: each K range adds its
 // exact int64 partial sums into a workspace with integer atomics (order-free,
-// so the result is deterministic) and a finalize kernel rounds them.  Tile 128 x 128, 64-byte K rows (32 BF16 or 16
-// FP32), SWIZZLE_64B, all 512 TMEM columns (4 x 128 FP32 accumulators).
+// so the result is deterministic) and a finalize kernel rounds them.  Tiles
+// 128 x 128 (split) or 128 x 256 (TF32), 64-byte K rows (32 BF16 or 16 FP32),
+// SWIZZLE_64B, all 512 TMEM columns allocated (4 x 128 FP32 accumulators in
+// the split form).
 // Every wait is bounded: on expiry the kernel records DEVERR_TIMEOUT in the
 // workspace error word, drains its own copies and MMAs, frees TMEM, returns.
 #include <cuda.h>
@@ -45,9 +47,9 @@ namespace symctr {
 
 namespace {
 
-constexpr int TM = 128, TN = 128;
+constexpr int TM = 128;
 constexpr int ROW_BYTES = 64;                  // K bytes per tile row per stage
-constexpr int TILE_BYTES = TM * ROW_BYTES;     // 8 KB per operand tile per stage
+constexpr int TILE_BYTES = TM * ROW_BYTES;     // 8 KB per 128-row slice tile per stage
 constexpr int NTHREADS = 384;
 constexpr int EPI_WARP0 = 4;
 constexpr int kExpBias = 4096;     // row exponents are stored biased (0 = all-zero row)
@@ -67,6 +69,18 @@ __host__ __device__ constexpr uint32_t drained_after(int c) {
 constexpr long long kTimeoutCycles = 4000000000ll;  // ~2 s per wait at 2 GHz
 
 enum Mode { MODE_SPLIT = 0, MODE_TF32 = 1 };
+
+// Tile shapes per form: the split form 128 x 128 (four accumulators fill
+// TMEM), the TF32 form 128 x 256 (one accumulator; the wider B tile doubles
+// the MMA work per byte staged, which bounds TF32 at 128 x 128).
+template <int KIND>
+struct TileCfg {
+  static constexpr int N = KIND == MODE_TF32 ? 256 : 128;    // output columns per CTA
+  static constexpr int A_BYTES = TM * ROW_BYTES;             // per slice, per stage
+  static constexpr int B_BYTES = N * ROW_BYTES;
+  static constexpr int LD = N + 1;                           // staging row stride (elements)
+  static constexpr size_t EPI_BYTES = (size_t)TM * LD * (KIND == MODE_SPLIT ? 8 : 4);
+};
 
 // ---------------------------------------------------------------- PTX helpers
 __device__ __forceinline__ uint32_t su32(const void* p) {
@@ -216,11 +230,12 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
   return d;
 }
 
-// Instruction descriptor: FP32 accumulate, K-major A and B, M = 128, N = 128.
+// Instruction descriptor: FP32 accumulate, K-major A and B, M = 128,
+// N = the form's tile width.
 template <int KIND>
 __host__ __device__ constexpr uint32_t idesc() {
   return (1u << 4) | ((KIND == MODE_SPLIT ? 1u : 2u) << 7) | ((KIND == MODE_SPLIT ? 1u : 2u) << 10) |
-         ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+         ((uint32_t)(TileCfg<KIND>::N >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
 }
 
 // RN(R * 2^e) as float64 using integer operations only (ties to even).
@@ -471,15 +486,14 @@ struct TcArgs {
   const int64_t* wcol;       // [n_q][N] offsets of W's columns
 };
 
-// Epilogue staging: the results of the 128 x 128 tile in shared memory (the
-// operand stages are free by then), rows padded to 129 entries.
-constexpr int STAGE_LD = TN + 1;
-constexpr size_t STAGE_BYTES_EPI = (size_t)TM * STAGE_LD * 8;
-
-template <int S, int STAGES>
+// Epilogue staging: the results of the tile in shared memory (the operand
+// stages are free by then), rows padded by one entry.
+template <int KIND, int S, int STAGES>
 __host__ __device__ constexpr size_t tile_region_bytes() {
-  return (size_t)STAGES * 2 * S * TILE_BYTES > STAGE_BYTES_EPI ? (size_t)STAGES * 2 * S * TILE_BYTES
-                                                               : STAGE_BYTES_EPI;
+  using C = TileCfg<KIND>;
+  return (size_t)STAGES * S * (C::A_BYTES + C::B_BYTES) > C::EPI_BYTES
+             ? (size_t)STAGES * S * (C::A_BYTES + C::B_BYTES)
+             : C::EPI_BYTES;
 }
 
 // GEN: the general output mode (complex element stride, sign, accumulate);
@@ -491,8 +505,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const Problem& p = args.p;
-  uint8_t* tiles = smem;  // [STAGES][2][S][TILE_BYTES], later the epilogue staging
-  uint8_t* ctl_base = smem + tile_region_bytes<S, STAGES>();
+  using Cfg = TileCfg<KIND>;
+  constexpr int TNk = Cfg::N;
+  constexpr int STAGE_LD = Cfg::LD;
+  uint8_t* tiles = smem;  // [STAGES][S A tiles, S B tiles], later the epilogue staging
+  uint8_t* ctl_base = smem + tile_region_bytes<KIND, S, STAGES>();
   uint64_t* full = (uint64_t*)ctl_base;
   uint64_t* empty = full + STAGES;
   uint64_t* top_full = empty + STAGES;
@@ -501,15 +518,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   uint64_t* drain = acc_full + 1;
   uint64_t* low_full = drain + 1;
   uint64_t* low_empty = low_full + 1;
-  int64_t* coff = (int64_t*)(low_empty + 1);   // [TN] W column offsets
-  int32_t* cexp = (int32_t*)(coff + TN);        // [TN] column exponents
-  int64_t* roffs = (int64_t*)(cexp + TN);        // [TM] W row offsets
+  int64_t* coff = (int64_t*)(low_empty + 1);   // [TNk] W column offsets
+  int32_t* cexp = (int32_t*)(coff + TNk);       // [TNk] column exponents
+  int64_t* roffs = (int64_t*)(cexp + TNk);       // [TM] W row offsets
   int32_t* rexps = (int32_t*)(roffs + TM);       // [TM] row exponents
   uint32_t* tmem_slot = (uint32_t*)(rexps + TM);
   Ctl* ctl = (Ctl*)(tmem_slot + 4);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t n0 = (int64_t)blockIdx.x * TN, m0 = (int64_t)blockIdx.y * TM;
+  const int64_t n0 = (int64_t)blockIdx.x * TNk, m0 = (int64_t)blockIdx.y * TM;
   const int b = blockIdx.z / args.ksplit;
   const int ks = blockIdx.z % args.ksplit;
   const int Q = batch_irrep(p, b);
@@ -517,7 +534,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const int kb1 = min(args.n_kb, kb0 + args.kb_per_split);
   const int n_kb = kb1 - kb0;
   const int n_chunks = KIND == MODE_SPLIT ? (n_kb + 1) / 2 : 1;
-  const int stage_bytes = 2 * S * TILE_BYTES;
+  const int stage_bytes = S * (Cfg::A_BYTES + Cfg::B_BYTES);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -541,23 +558,25 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   // W's offset tables are constants of the plan: read before the wait.
-  if (threadIdx.x >= EPI_WARP0 * 32 && threadIdx.x < EPI_WARP0 * 32 + TN) {
+  if (threadIdx.x >= EPI_WARP0 * 32 && threadIdx.x < EPI_WARP0 * 32 + TNk) {
     const int c = threadIdx.x - EPI_WARP0 * 32;
     const int64_t n = n0 + c, m = m0 + c;
     coff[c] = n < p.N ? args.wcol[(int64_t)b * p.N + n] : 0;
-    roffs[c] = m < p.M ? args.wrow[(int64_t)b * p.M + m] : 0;
+    if (c < TM) roffs[c] = m < p.M ? args.wrow[(int64_t)b * p.M + m] : 0;
   }
   // Launched as a programmatic dependent of the operand preparation: the setup
   // above overlaps its tail; everything below reads its outputs.
   asm volatile("griddepcontrol.wait;" ::: "memory");
-  if (KIND == MODE_SPLIT && threadIdx.x >= EPI_WARP0 * 32 && threadIdx.x < EPI_WARP0 * 32 + TN) {
+  if (threadIdx.x >= EPI_WARP0 * 32 && threadIdx.x < EPI_WARP0 * 32 + TNk) {
     const int c = threadIdx.x - EPI_WARP0 * 32;
     const int64_t n = n0 + c, m = m0 + c;
-    cexp[c] = n < p.N ? args.ev[(int64_t)b * p.N + n] - kExpBias : 0;
-    rexps[c] = m < p.M ? args.eu[(int64_t)b * p.M + m] - kExpBias : 0;
-  } else if (threadIdx.x >= EPI_WARP0 * 32 && threadIdx.x < EPI_WARP0 * 32 + TN) {
-    cexp[threadIdx.x - EPI_WARP0 * 32] = 0;
-    rexps[threadIdx.x - EPI_WARP0 * 32] = 0;
+    if (KIND == MODE_SPLIT) {
+      cexp[c] = n < p.N ? args.ev[(int64_t)b * p.N + n] - kExpBias : 0;
+      if (c < TM) rexps[c] = m < p.M ? args.eu[(int64_t)b * p.M + m] - kExpBias : 0;
+    } else {
+      cexp[c] = 0;
+      if (c < TM) rexps[c] = 0;
+    }
   }
   tc_fence_before();
   __syncthreads();
@@ -575,11 +594,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (!wait_phase(&empty[st], ph ^ 1, ctl)) break;
         mbar_expect_tx(&full[st], stage_bytes);
         uint8_t* sa = tiles + (size_t)st * stage_bytes;
-        uint8_t* sb = sa + S * TILE_BYTES;
+        uint8_t* sb = sa + S * Cfg::A_BYTES;
         int kc = (kb0 + kb) * (ROW_BYTES / args.ebytes);
         for (int i = 0; i < S; ++i) {
-          tma_load_3d(&tma_a, &full[st], sa + i * TILE_BYTES, kc, (int)m0, i * p.n_q + b);
-          tma_load_3d(&tma_b, &full[st], sb + i * TILE_BYTES, kc, (int)n0, i * p.n_q + b);
+          tma_load_3d(&tma_a, &full[st], sa + i * Cfg::A_BYTES, kc, (int)m0, i * p.n_q + b);
+          tma_load_3d(&tma_b, &full[st], sb + i * Cfg::B_BYTES, kc, (int)n0, i * p.n_q + b);
         }
         ++issued;
       }
@@ -601,7 +620,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (!wait_phase(&full[st], ph, ctl)) break;
         tc_fence_after();
         const uint64_t da = sdesc(ab + st * stage_bytes);
-        const uint64_t db = sdesc(ab + st * stage_bytes + S * TILE_BYTES);
+        const uint64_t db = sdesc(ab + st * stage_bytes + S * Cfg::A_BYTES);
         const bool cfirst = KIND == MODE_TF32 ? (kb == 0) : (kb % 2 == 0);
         const int chunk = KIND == MODE_TF32 ? 0 : kb / 2;
         const bool final_chunk = chunk == n_chunks - 1;
@@ -640,7 +659,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int half = ew >> 2;             // column half
     const int row = quad * 32 + lane;
     const int64_t m = m0 + row;
-    const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(half * 64);
+    const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(half * (TNk / 2));
     // Running sums of the exact diagonals d = 0, 1, 2 in their own units
     // (1, 2^-8, 2^-16).  Diagonal d has d + 1 slice pairs of |a_i b_j| <= 2^14
     // per K step and is drained every 4, 2, 1 chunks of 64 K (d = 0, 1, 2): at
@@ -747,9 +766,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           }
         }
       } else {
-        uint32_t* st32 = (uint32_t*)tiles + row * STAGE_LD + half * 64;
+        uint32_t* st32 = (uint32_t*)tiles + row * STAGE_LD + half * (TNk / 2);
 #pragma unroll
-        for (int pc = 0; pc < 4; ++pc) {
+        for (int pc = 0; pc < TNk / 32; ++pc) {
           uint32_t a0[16];
           tmem_ld16(lane_base + pc * 16, a0);
           tmem_wait_ld();
@@ -762,21 +781,21 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     // all 256 epilogue threads meet here, whatever path they took
     asm volatile("bar.sync 1, 256;" ::: "memory");
     const int t = threadIdx.x - EPI_WARP0 * 32;
-    // Thread t writes column c = t % TN of rows t / TN, t / TN + 2, ...: the
+    // Thread t writes column c = t % TNk of rows t / TNk, t / TNk + RSTEP, ...: the
     // column's offset and exponent stay in registers, and each batch issues
     // all of its shared-memory (or L2) loads before any global store, so the
     // loads of a batch overlap instead of waiting behind the stores.
-    constexpr int RSTEP = 256 / TN;
+    constexpr int RSTEP = 256 / TNk;
     constexpr int BATCH = 8;
-    static_assert(TM % (RSTEP * BATCH) == 0 && 256 % TN == 0, "epilogue row walk");
-    const int c = t % TN;
+    static_assert(TM % (RSTEP * BATCH) == 0 && 256 % TNk == 0, "epilogue row walk");
+    const int c = t % TNk;
     const bool col_ok = n0 + c < p.N;
     const int64_t co = coff[c];
     const int ce = cexp[c] - 36;
     const int64_t acc_col = ((int64_t)b * p.M + m0) * p.N + n0 + c;   // wacc index of row 0
     if (ok && col_ok) {
 #pragma unroll 1
-      for (int rb = t / TN; rb < TM; rb += RSTEP * BATCH) {
+      for (int rb = t / TNk; rb < TM; rb += RSTEP * BATCH) {
         if (KIND == MODE_SPLIT) {
           long long Rv[BATCH];
 #pragma unroll
@@ -825,7 +844,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       if (ctl->last && col_ok) {
         __threadfence();
 #pragma unroll 1
-        for (int rb = t / TN; rb < TM; rb += RSTEP * BATCH) {
+        for (int rb = t / TNk; rb < TM; rb += RSTEP * BATCH) {
           long long Rv[BATCH];
           int64_t ro[BATCH];
           int ex[BATCH];
@@ -890,17 +909,18 @@ EncodeTiledFn encode_fn() {
 }
 
 bool encode_map(CUtensorMap* map, const void* base, bool is_f32, int64_t kpad, int64_t rows,
-                int64_t planes);
+                int64_t planes, int box_rows);
 
-// 3-D map over [planes][rows][kpad] with a (64-byte, 128-row, 1) box.  The
+// 3-D map over [planes][rows][kpad] with a (64-byte, box_rows, 1) box.  The
 // encoding is a pure function of its arguments, so the last few are kept per
 // host thread (a contraction called again on the same workspace reuses them).
 bool make_map(CUtensorMap* map, const void* base, bool is_f32, int64_t kpad, int64_t rows,
-              int64_t planes) {
+              int64_t planes, int box_rows) {
   struct Entry {
     const void* base;
     bool f32;
     int64_t kpad, rows, planes;
+    int box_rows;
     CUtensorMap map;
   };
   constexpr int kEntries = 8;
@@ -908,26 +928,27 @@ bool make_map(CUtensorMap* map, const void* base, bool is_f32, int64_t kpad, int
   thread_local int used = 0, next = 0;
   for (int i = 0; i < used; ++i) {
     const Entry& e = cache[i];
-    if (e.base == base && e.f32 == is_f32 && e.kpad == kpad && e.rows == rows && e.planes == planes) {
+    if (e.base == base && e.f32 == is_f32 && e.kpad == kpad && e.rows == rows && e.planes == planes &&
+        e.box_rows == box_rows) {
       *map = e.map;
       return true;
     }
   }
-  if (!encode_map(map, base, is_f32, kpad, rows, planes)) return false;
-  cache[next] = Entry{base, is_f32, kpad, rows, planes, *map};
+  if (!encode_map(map, base, is_f32, kpad, rows, planes, box_rows)) return false;
+  cache[next] = Entry{base, is_f32, kpad, rows, planes, box_rows, *map};
   next = (next + 1) % kEntries;
   if (used < kEntries) ++used;
   return true;
 }
 
 bool encode_map(CUtensorMap* map, const void* base, bool is_f32, int64_t kpad, int64_t rows,
-                int64_t planes) {
+                int64_t planes, int box_rows) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
   int eb = is_f32 ? 4 : 2;
   cuuint64_t dims[3] = {(cuuint64_t)kpad, (cuuint64_t)rows, (cuuint64_t)planes};
   cuuint64_t strides[2] = {(cuuint64_t)(kpad * eb), (cuuint64_t)(kpad * eb * rows)};
-  cuuint32_t box[3] = {(cuuint32_t)(ROW_BYTES / eb), (cuuint32_t)TM, 1};
+  cuuint32_t box[3] = {(cuuint32_t)(ROW_BYTES / eb), (cuuint32_t)box_rows, 1};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = fn(map, is_f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3,
                   const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -942,8 +963,8 @@ cudaError_t launch_tc_mode(const Problem& p, const Tables& tab, const void* a, c
                       unsigned long long* wacc, unsigned* tile_ctr, cudaStream_t st) {
   const bool f32 = KIND == MODE_TF32;
   CUtensorMap ma, mb;
-  if (!make_map(&ma, a, f32, kpad, p.M, (int64_t)S * p.n_q) ||
-      !make_map(&mb, bop, f32, kpad, p.N, (int64_t)S * p.n_q))
+  if (!make_map(&ma, a, f32, kpad, p.M, (int64_t)S * p.n_q, TM) ||
+      !make_map(&mb, bop, f32, kpad, p.N, (int64_t)S * p.n_q, TileCfg<KIND>::N))
     return cudaErrorInvalidValue;
   TcArgs args;
   args.p = p;
@@ -962,7 +983,8 @@ cudaError_t launch_tc_mode(const Problem& p, const Tables& tab, const void* a, c
   args.tile_ctr = tile_ctr;
   args.wrow = tab.wrow;
   args.wcol = tab.wcol;
-  size_t smem = 1024 + tile_region_bytes<S, STAGES>() + 8 * (2 * STAGES + 6) + 8 * TN + 4 * TN +
+  constexpr int TNk = TileCfg<KIND>::N;
+  size_t smem = 1024 + tile_region_bytes<KIND, S, STAGES>() + 8 * (2 * STAGES + 6) + 8 * TNk + 4 * TNk +
                 8 * TM + 4 * TM + 16 + 64;
   auto kern = gemm_tc_kernel<KIND, S, STAGES, GEN>;
   thread_local bool attr_set[64] = {};
@@ -973,7 +995,7 @@ cudaError_t launch_tc_mode(const Problem& p, const Tables& tab, const void* a, c
     if (e != cudaSuccess) return e;
     attr_set[dev] = true;
   }
-  int64_t gx = (p.N + TN - 1) / TN, gy = (p.M + TM - 1) / TM;
+  int64_t gx = (p.N + TNk - 1) / TNk, gy = (p.M + TM - 1) / TM;
   if (gx > 0x7FFFFFFF || gy > 65535 || (int64_t)p.n_q * args.ksplit > 65535)
     return cudaErrorInvalidConfiguration;
   dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)(p.n_q * args.ksplit));
