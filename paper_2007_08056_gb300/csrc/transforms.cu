@@ -253,7 +253,10 @@ __device__ void scan_tile(const PrepArgs& a, int op, uint32_t tile, int64_t* rof
   const bool fast_rows = a.fast_rows[op];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const uint32_t P = (uint32_t)a.parts;
-  const int64_t width = (Cn + P - 1) / P;
+  // column blocks start on multiples of 32 columns: the pair path loads two
+  // adjacent columns with one 16-byte load, which needs an even first column
+  // (a trailing block may be short or empty; an empty one writes key 0)
+  const int64_t width = ((Cn + P - 1) / P + 31) / 32 * 32;
   const uint32_t rt = (uint32_t)((R + TILE - 1) / TILE);
   const uint32_t b = tile / (rt * P);
   const uint32_t rem = tile - b * rt * P;
