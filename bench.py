@@ -514,7 +514,8 @@ def run_complex(args, rank, world):
 def run_device(args, rank, world):
     """Workloads whose operands are drawn on the device: config 5 (the
     CC-ladder contraction at virtual 512 / occupied 128 with sector dims 512/G
-    and 128/G, up to 275 GB at G = 2) and the Table-2 instances of the Table-1
+    and 128/G, up to 275 GB at G = 2; --sweep-dims 256,64 gives the secondary
+    sweep at the CC ladder's dimensions) and the Table-2 instances of the Table-1
     contraction families.  The error is taken on entries the oracle computes
     one by one.  Forward, and with --backward the adjoint pair as well."""
     import torch
@@ -525,8 +526,9 @@ def run_device(args, rank, world):
     dev = torch.device("cuda")
     if args.workload == "sweep":
         G = args.sweep_g
-        c = WL.sweep_point(G)
-        seed = 5000 + G
+        virt, occ = (int(x) for x in args.sweep_dims.split(","))
+        c = WL.cc_ladder(G, virt, occ)
+        seed = 5000 + G if (virt, occ) == (512, 128) else 5100 + G
     else:
         c = WL.TABLE2[args.case]
         G = c.moduli[0]
@@ -659,6 +661,9 @@ def main():
     ap.add_argument("--workload", choices=["mps", "cc_ladder", "sweep", "table"], default="mps")
     ap.add_argument("--case", default="CC1_a", help="table: a Table-2 case (" + ", ".join(WL.TABLE2) + ")")
     ap.add_argument("--sweep-g", type=int, default=16, help="G of the sweep workload (config 5)")
+    ap.add_argument("--sweep-dims", default="512,128",
+                    help="VIRT,OCC of the sweep workload: 512,128 (config 5) or 256,64 (the "
+                         "secondary sweep at the CC ladder's dimensions)")
     ap.add_argument("--backward", action="store_true", help="sweep: time the backward pair too")
     ap.add_argument("--complex", action="store_true",
                     help="mps: complex tensors, E' = sum E A conj(A) (four real products per contraction)")

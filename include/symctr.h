@@ -34,9 +34,11 @@
  *   Ownership : the caller owns every device pointer, the workspace and the
  *               stream.  A plan owns host memory only: its metadata and, for
  *               the tensor-core forms, the offset tables of the aligned forms
- *               (computed at plan creation, page-locked on the first
- *               contraction and copied into the workspace by every
- *               contraction).  No call allocates device memory.
+ *               (computed at plan creation and page-locked on the first
+ *               contraction; read in place when small, else copied into the
+ *               workspace by every contraction, unless the caller has
+ *               attached a device copy with symctr_plan_attach_tables).  No
+ *               call allocates device memory.
  *   Errors    : every call returns a status and never throws across the ABI.
  *               Kernels never trap: a device-side failure (a bounded wait that
  *               expired, a non-finite input) is recorded in the first word of
@@ -116,6 +118,8 @@ typedef struct {
   uint64_t workspace_bytes_backward; /* device workspace symctr_contract_backward needs */
   uint64_t workspace_bytes_min; /* smallest accepted workspace: the contraction then runs
                                    one pass per group of irreps that fits (Q-streaming) */
+  uint64_t table_bytes;         /* device buffer symctr_plan_attach_tables takes (0: the
+                                   plan has no offset tables, e.g. the float64 form) */
 } symctr_plan_info;
 
 /* Build a plan for W = einsum(spec, U, V).
@@ -139,6 +143,27 @@ SYMCTR_API symctr_status symctr_plan_create(const char* einsum, int n_moduli, co
 
 /* Fill *out with the plan's derived quantities.  Host only. */
 SYMCTR_API symctr_status symctr_plan_query(const symctr_plan* plan, symctr_plan_info* out);
+
+/* Give the plan a device-resident copy of its offset tables (the row and column
+ * offsets of Alg. 2's aligned operands in the standard reduced forms, computed
+ * on the host at plan creation, including those of the backward's two
+ * contractions).  Without it each contraction reads the tables from
+ * page-locked host memory (up to 1 MiB, over the CPU-GPU link) or copies them
+ * into the workspace; with it the kernels read them from HBM.
+ *  tables : caller-owned device memory (256-byte aligned) of at least
+ *           table_bytes bytes, on the device that is current during the call;
+ *           NULL detaches (the plan reverts to the host tables).
+ *  stream : the copy is queued on it; the caller orders contractions on other
+ *           streams after it (e.g. synchronises the stream once).
+ * The caller keeps the buffer allocated and unmodified until it detaches or
+ * destroys the plan.  Contractions running on another device than the
+ * buffer's keep using the host tables.  Not to be called while a contraction
+ * with this plan is being issued on another host thread.
+ * Returns SYMCTR_OK (also when table_bytes is 0: nothing to copy),
+ * SYMCTR_ERR_NULLPTR (plan), SYMCTR_ERR_WORKSPACE (bytes < table_bytes),
+ * SYMCTR_ERR_ARGUMENT (misaligned) or SYMCTR_ERR_CUDA. */
+SYMCTR_API symctr_status symctr_plan_attach_tables(symctr_plan* plan, void* tables, size_t bytes,
+                                                  void* stream);
 
 /* Bit-exact alignment transforms (Alg. 2 input transformations and output step).
  *  operand   : 0 = U, 1 = V, 2 = W.

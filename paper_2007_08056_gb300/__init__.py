@@ -18,6 +18,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import threading
 from dataclasses import dataclass
 from typing import Optional, Sequence, Tuple
 
@@ -60,7 +61,7 @@ class PlanInfo(ctypes.Structure):
         ("aligned_numel_w", ctypes.c_int64),
         ("useful_flops", ctypes.c_double), ("transform_bytes", ctypes.c_double),
         ("workspace_bytes", ctypes.c_uint64), ("workspace_bytes_backward", ctypes.c_uint64),
-        ("workspace_bytes_min", ctypes.c_uint64),
+        ("workspace_bytes_min", ctypes.c_uint64), ("table_bytes", ctypes.c_uint64),
     ]
 
 
@@ -104,12 +105,14 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.symctr_selftest_bounded_wait.argtypes = [P, ctypes.c_size_t, ctypes.c_int64, P]
     lib.symctr_contract_complex.argtypes = [P, ctypes.c_int, ctypes.c_int, P, P, P, P,
                                             ctypes.c_size_t, P]
+    lib.symctr_plan_attach_tables.argtypes = [P, P, ctypes.c_size_t, P]
     lib.symctr_plan_destroy.argtypes = [P]
     lib.symctr_plan_destroy.restype = None
     for f in ("symctr_plan_create", "symctr_plan_query", "symctr_align", "symctr_contract",
               "symctr_contract_backward", "symctr_check_device_error", "symctr_profile_enable",
               "symctr_profile_read", "symctr_contract_static_scratch",
-              "symctr_selftest_bounded_wait", "symctr_contract_complex"):
+              "symctr_selftest_bounded_wait", "symctr_contract_complex",
+              "symctr_plan_attach_tables"):
         getattr(lib, f).restype = ctypes.c_int
     _LIB = lib
     return lib
@@ -188,14 +191,38 @@ class Plan:
         self._size_u, self._size_v, self._size_w = (torch.Size(self.shape_u), torch.Size(self.shape_v),
                                                      torch.Size(self.shape_w))
         self._ws = None
+        self._tables = None
+        self._tables_ready = info.table_bytes == 0
+        self._lock = threading.Lock()
 
     def __del__(self):
         try:
             if getattr(self, "_h", None) is not None and _LIB is not None:
+                if getattr(self, "_tables", None) is not None:
+                    # kernels issued on any stream may still read the tables
+                    torch.cuda.synchronize(self._tables.device)
                 _LIB.symctr_plan_destroy(self._h)
                 self._h = None
         except Exception:
             pass
+
+    # -- device tables -------------------------------------------------------
+    def attach_tables(self, device=None):
+        """Give the plan a device copy of its offset tables (symctr_plan_attach_tables),
+        so that its kernels read them from HBM instead of host memory.  The
+        first contraction does this; the buffer lives as long as the plan."""
+        with self._lock:
+            if not self._tables_ready:
+                buf = torch.empty(int(self.info.table_bytes), dtype=torch.uint8,
+                                  device=device or "cuda")
+                with torch.cuda.device(buf.device):
+                    s = torch.cuda.current_stream(buf.device)
+                    _check(load().symctr_plan_attach_tables(self._h, buf.data_ptr(), buf.numel(),
+                                                            s.cuda_stream))
+                    # contractions on other streams read the copy too
+                    s.synchronize()
+                self._tables = buf
+                self._tables_ready = True
 
     # -- workspace -----------------------------------------------------------
     def workspace(self, backward: bool = False, device=None) -> torch.Tensor:
@@ -230,6 +257,8 @@ class Plan:
             out = torch.empty(self.shape_w, dtype=torch.float64, device=u.device)
         elif not self._ok64(out, self._size_w):
             self._dev64(out, self.shape_w, "out")
+        if not self._tables_ready:
+            self.attach_tables(u.device)
         ws = workspace if workspace is not None else self.workspace(device=u.device)
         _check(_LIB.symctr_contract(self._h, u.data_ptr(), v.data_ptr(), out.data_ptr(), ws.data_ptr(),
                                     ws.numel(), torch.cuda.current_stream().cuda_stream))
@@ -249,6 +278,8 @@ class Plan:
             out = torch.empty(self.shape_w, dtype=torch.complex128, device=u.device)
         if out.dtype != torch.complex128 or tuple(out.shape) != tuple(self.shape_w) or not out.is_contiguous():
             raise ValueError("out must be a contiguous complex128 tensor of the output shape")
+        if not self._tables_ready:
+            self.attach_tables(u.device)
         ws = workspace if workspace is not None else self.workspace(device=u.device)
         _check(load().symctr_contract_complex(self._h, int(conj_u), int(conj_v), _ptr(u), _ptr(v),
                                               _ptr(out), _ptr(ws), ws.numel(), _stream()))
@@ -266,6 +297,8 @@ class Plan:
         if out is None:
             out = torch.empty(self.shape_w, dtype=torch.float64, device=u.device)
         self._dev64(out, self.shape_w, "out")
+        # no table buffer is attached here (that would allocate device memory);
+        # tables attached by an earlier contract() are used
         _check(load().symctr_contract_static_scratch(self._h, _ptr(u), _ptr(v), _ptr(out),
                                                      _stream()))
         return out
@@ -276,6 +309,8 @@ class Plan:
         self._dev64(grad_w, self.shape_w, "grad_w")
         gu = torch.empty(self.shape_u, dtype=torch.float64, device=u.device) if need_u else None
         gv = torch.empty(self.shape_v, dtype=torch.float64, device=u.device) if need_v else None
+        if not self._tables_ready:
+            self.attach_tables(u.device)
         ws = workspace if workspace is not None else self.workspace(True, u.device)
         _check(load().symctr_contract_backward(self._h, _ptr(grad_w), _ptr(u), _ptr(v), _ptr(gu),
                                                _ptr(gv), _ptr(ws), ws.numel(), _stream()))

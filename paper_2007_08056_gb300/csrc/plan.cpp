@@ -152,6 +152,9 @@ struct symctr_plan {
   mutable std::once_flag pin_once;
   mutable bool pinned = false;
   mutable const int64_t* dtab = nullptr;   // device view of the page-locked tables
+  // caller-owned device copy of htab (symctr_plan_attach_tables) and its device
+  const int64_t* dev_tab = nullptr;
+  int dev_tab_device = -1;
 };
 
 namespace {
@@ -543,9 +546,15 @@ symctr_status run_contract_body(const symctr_plan* P, const double* u, const dou
   }
   unsigned* barrier = (unsigned*)(base + 64);
   const bool split = P->prec == SYMCTR_SPLIT_BF16;
+  // the attached device tables, if they live on the current device
+  bool attached = false;
+  if (P->dev_tab) {
+    int dev = -1;
+    attached = cudaGetDevice(&dev) == cudaSuccess && dev == P->dev_tab_device;
+  }
   // page-lock the host tables once, so that their copies are plain DMA reads
   // (without it they are staged through pageable memory, also correct)
-  std::call_once(P->pin_once, [P] {
+  if (!attached) std::call_once(P->pin_once, [P] {
     if (!P->htab.empty() &&
         cudaHostRegister((void*)P->htab.data(), P->htab.size() * sizeof(int64_t),
                          cudaHostRegisterPortable | cudaHostRegisterMapped) == cudaSuccess) {
@@ -568,11 +577,15 @@ symctr_status run_contract_body(const symctr_plan* P, const double* u, const dou
     const Layout L = make_layout(pc, true, P->prec, P->n_slices, P->kpad);
     Tables tab;
     const int64_t ext[6] = {pr.M, pr.K, pr.N, pr.K, pr.M, pr.N};
-    if (P->dtab && P->htab.size() * sizeof(int64_t) <= kMappedTablesMax) {
-      // small tables: the kernels read this pass's part of the page-locked
-      // host tables in place (reads over the CPU-GPU link are not cached on
-      // the GPU, so larger tables, re-read by many tiles, go to HBM instead)
-      const int64_t* src = P->dtab;
+    const int64_t* in_place = attached ? P->dev_tab
+                              : (P->dtab && P->htab.size() * sizeof(int64_t) <= kMappedTablesMax)
+                                  ? P->dtab
+                                  : nullptr;
+    if (in_place) {
+      // the attached device copy, or small page-locked host tables read in
+      // place (reads over the CPU-GPU link are not cached on the GPU, so
+      // larger tables, re-read by many tiles, are copied to HBM instead)
+      const int64_t* src = in_place;
       const int64_t** dst[6] = {&tab.urow, &tab.ucol, &tab.vrow, &tab.vcol, &tab.wrow, &tab.wcol};
       for (int k = 0; k < 6; ++k) {
         *dst[k] = src + (int64_t)q0 * ext[k];
@@ -643,6 +656,34 @@ symctr_status record_error(symctr_status st, const char* detail) { return fail(s
 
 }  // namespace symctr
 
+static uint64_t own_table_bytes(const symctr_plan* P) {
+  return (uint64_t)round_up((int64_t)(P->htab.size() * sizeof(int64_t)), 256);
+}
+
+// The plan's tables, then the backward plans' (recursively), each 256-byte aligned.
+static uint64_t all_table_bytes(const symctr_plan* P) {
+  if (!P) return 0;
+  return own_table_bytes(P) + all_table_bytes(P->bwd_u) + all_table_bytes(P->bwd_v);
+}
+
+static symctr_status attach_tables(symctr_plan* P, uint8_t* buf, int dev, cudaStream_t st) {
+  if (!P) return SYMCTR_OK;
+  if (!buf) {
+    P->dev_tab = nullptr;
+    P->dev_tab_device = -1;
+  } else if (!P->htab.empty()) {
+    cudaError_t e = cudaMemcpyAsync(buf, P->htab.data(), P->htab.size() * sizeof(int64_t),
+                                    cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_status(e, "attach offset tables");
+    P->dev_tab = (const int64_t*)buf;
+    P->dev_tab_device = dev;
+  }
+  uint8_t* next = buf ? buf + own_table_bytes(P) : nullptr;
+  symctr_status r = attach_tables(P->bwd_u, next, dev, st);
+  if (r != SYMCTR_OK) return r;
+  return attach_tables(P->bwd_v, next ? next + all_table_bytes(P->bwd_u) : nullptr, dev, st);
+}
+
 extern "C" {
 
 symctr_status symctr_plan_create(const char* einsum, int n_moduli, const int32_t* moduli,
@@ -696,7 +737,24 @@ symctr_status symctr_plan_query(const symctr_plan* P, symctr_plan_info* o) {
   if (P->bwd_u && P->bwd_u->ws_bytes > wb) wb = P->bwd_u->ws_bytes;
   if (P->bwd_v && P->bwd_v->ws_bytes > wb) wb = P->bwd_v->ws_bytes;
   o->workspace_bytes_backward = wb;
+  o->table_bytes = all_table_bytes(P);
   return SYMCTR_OK;
+}
+
+symctr_status symctr_plan_attach_tables(symctr_plan* P, void* tables, size_t bytes, void* stream) {
+  if (!P) return fail(SYMCTR_ERR_NULLPTR, "NULL plan");
+  if (!tables) return attach_tables(P, nullptr, -1, nullptr);
+  if ((uint64_t)bytes < all_table_bytes(P)) return fail(SYMCTR_ERR_WORKSPACE, "table buffer too small");
+  if ((uintptr_t)tables % 256 != 0) return fail(SYMCTR_ERR_ARGUMENT, "table buffer not 256-byte aligned");
+  if (all_table_bytes(P) == 0) return SYMCTR_OK;
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_status(e, "current device");
+  // detach first: a failed copy leaves no half-attached plan behind
+  attach_tables(P, nullptr, -1, nullptr);
+  symctr_status r = attach_tables(P, (uint8_t*)tables, dev, (cudaStream_t)stream);
+  if (r != SYMCTR_OK) attach_tables(P, nullptr, -1, nullptr);
+  return r;
 }
 
 symctr_status symctr_align(const symctr_plan* P, int operand, int direction, const double* src,

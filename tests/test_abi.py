@@ -132,3 +132,23 @@ def test_workspace_too_small_is_rejected_before_any_launch():
     fake = ctypes.c_void_p(4096)
     st = lib.symctr_contract(p._h, fake, fake, fake, fake, 16, None)
     assert st == 7
+
+
+def test_attach_tables_argument_checks():
+    """symctr_plan_attach_tables checks its arguments on the host before any
+    CUDA call; detaching (NULL buffer) touches no device either."""
+    lib = sc.load()
+    assert lib.symctr_plan_attach_tables(None, None, 0, None) == 6
+    spec = lambda t: (t.signs, t.charge, t.dims)
+    p = sc.Plan(WL.MPS_STEP1, (8,), spec(WL.MPS_E), spec(WL.MPS_A), "split_bf16")
+    # forward tables (U, V and W rows and columns per irrep) plus the backward plans'
+    own = 8 * 8 * (2 * p.info.M + 2 * p.info.N + 2 * p.info.K)
+    assert p.info.table_bytes >= own and p.info.table_bytes % 256 == 0
+    n = int(p.info.table_bytes)
+    assert lib.symctr_plan_attach_tables(p._h, ctypes.c_void_p(4096), n - 1, None) == 7
+    assert lib.symctr_plan_attach_tables(p._h, ctypes.c_void_p(4096 + 16), n, None) == 12
+    assert lib.symctr_plan_attach_tables(p._h, None, 0, None) == 0
+    # the float64 form keeps no tables
+    p64 = sc.Plan(WL.MPS_STEP1, (8,), spec(WL.MPS_E), spec(WL.MPS_A), "fp64")
+    assert p64.info.table_bytes == 0
+    assert lib.symctr_plan_attach_tables(p64._h, ctypes.c_void_p(4096), 0, None) == 0

@@ -185,9 +185,9 @@ def device_operands(c, seed):
     return u, v
 
 
-def sweep_check(sc, G, precision, workspace_fraction=None, samples=24):
+def sweep_check(sc, G, precision, workspace_fraction=None, samples=24, dims=None):
     torch.cuda.empty_cache()
-    c = WL.sweep_point(G)
+    c = WL.sweep_point(G) if dims is None else WL.cc_ladder(G, *dims)
     u, v = device_operands(c, 5000 + G)
     p = sc.Plan(c.einsum, c.moduli, spec(c.u), spec(c.v), precision)
     ws = None
@@ -226,3 +226,10 @@ def test_config5_sweep_G4_q_streaming(sc):
     if free < 230e9:
         pytest.skip(f"needs ~230 GB free device memory, {free / 1e9:.0f} GB free")
     assert sweep_check(sc, 4, "split_bf16", workspace_fraction=0.26, samples=12) <= TOL["split_bf16"]
+
+
+@pytest.mark.parametrize("G", [2, 4])
+def test_secondary_sweep_at_cc_ladder_dims(sc, G):
+    """The sweep at the CC ladder's dimensions (virtual 256, occupied 64), where
+    G = 2 fits one GPU (v is 17 GB)."""
+    assert sweep_check(sc, G, "split_bf16", samples=16, dims=(256, 64)) <= TOL["split_bf16"]
