@@ -111,7 +111,6 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
 
 struct Ctl {
   volatile int abort;
-  int last;          // this CTA finalizes its tile (split-K)
   unsigned* err;
 };
 
@@ -481,7 +480,6 @@ struct TcArgs {
   int ksplit;        // K ranges (grid.z = n_q * ksplit)
   int kb_per_split;  // stages per K range (a multiple of 2)
   unsigned long long* wacc;  // [n_q][M][N] int64 partial sums when ksplit > 1 (zeroed)
-  unsigned* tile_ctr;        // [n_q][gy][gx] K ranges finished per tile (zeroed)
   const int64_t* wrow;       // [n_q][M] offsets of W's rows in its reduced form
   const int64_t* wcol;       // [n_q][N] offsets of W's columns
 };
@@ -832,36 +830,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
       }
     }
-    if (KIND == MODE_SPLIT && args.ksplit > 1) {
-      // the CTA that completes a tile's last K range rounds the summed partials
-      __threadfence();
-      asm volatile("bar.sync 1, 256;" ::: "memory");
-      if (t == 0) {
-        const unsigned tile_id = ((unsigned)b * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-        ctl->last = ok && atomicAdd(args.tile_ctr + tile_id, 1u) == (unsigned)args.ksplit - 1;
-      }
-      asm volatile("bar.sync 1, 256;" ::: "memory");
-      if (ctl->last && col_ok) {
-        __threadfence();
-#pragma unroll 1
-        for (int rb = t / TNk; rb < TM; rb += RSTEP * BATCH) {
-          long long Rv[BATCH];
-          int64_t ro[BATCH];
-          int ex[BATCH];
-#pragma unroll
-          for (int j = 0; j < BATCH; ++j) {
-            const int r = rb + RSTEP * j;
-            Rv[j] = m0 + r < p.M ? (long long)__ldcg(args.wacc + acc_col + (int64_t)r * p.N) : 0ll;
-            ro[j] = roffs[r];
-            ex[j] = rexps[r] + ce;
-          }
-          double d[BATCH];
-          i64_scaled_batch<BATCH>(Rv, ex, d);
-          store_batch<BATCH, GEN>(p, args.w, ro, co, d, m0 + rb, RSTEP);
-        }
-      }
-    }
   }
+  // a split-K rounding kernel behind this one may start its launch now
+  asm volatile("griddepcontrol.launch_dependents;");
   __syncthreads();
   if (warp == 1) {
     __syncwarp();
@@ -880,13 +851,56 @@ __global__ void bounded_wait_selftest_kernel(unsigned* err, long long limit) {
   if (threadIdx.x == 0) {
     mbar_init(&bar, 1);
     ctl.abort = 0;
-    ctl.last = 0;
     ctl.err = err;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
   if (threadIdx.x == 0) wait_phase(&bar, 0, &ctl, limit);
   __syncthreads();
+}
+
+// Split-K rounding: once every K range of the GEMM has added its exact int64
+// partial sums into wacc ([n_q][M][N]), each thread takes one column n and
+// kRoundRows consecutive rows of one irrep, rounds R * 2^(row exponent +
+// column exponent - 36) once to float64 (the same integer-only rounding as the
+// GEMM's own epilogue) and stores it through the offset tables.  Launched
+// behind the GEMM with programmatic serialization; griddepcontrol.wait makes
+// the GEMM's partial sums visible.  Skipped when a GEMM wait timed out (the
+// sums are incomplete; the error word already reports it).
+constexpr int kRoundRows = 4;
+constexpr int kRoundThreads = 256;
+
+template <bool GEN>
+__global__ void __launch_bounds__(kRoundThreads) splitk_round_kernel(
+    Problem p, const unsigned long long* __restrict__ wacc, const int32_t* __restrict__ eu,
+    const int32_t* __restrict__ ev, const int64_t* __restrict__ wrow,
+    const int64_t* __restrict__ wcol, double* w, const unsigned* err) {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  if (*(const volatile unsigned*)err & DEVERR_TIMEOUT) return;
+  const int64_t M = p.M, N = p.N;
+  const int64_t row_groups = (M + kRoundRows - 1) / kRoundRows;
+  const int64_t total = (int64_t)p.n_q * row_groups * N;
+  for (int64_t i = (int64_t)blockIdx.x * kRoundThreads + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * kRoundThreads) {
+    const int64_t n = i % N, g = i / N;
+    const int64_t b = g / row_groups, m0 = (g % row_groups) * kRoundRows;
+    const int64_t co = wcol[b * N + n];
+    const int ce = ev[b * N + n] - kExpBias - 36;
+    long long Rv[kRoundRows];
+    int64_t ro[kRoundRows];
+    int ex[kRoundRows];
+#pragma unroll
+    for (int j = 0; j < kRoundRows; ++j) {
+      const int64_t m = m0 + j;
+      const bool in = m < M;
+      Rv[j] = in ? (long long)__ldcg(wacc + (b * M + m) * N + n) : 0ll;
+      ro[j] = in ? wrow[b * M + m] : 0;
+      ex[j] = (in ? eu[b * M + m] - kExpBias : 0) + ce;
+    }
+    double d[kRoundRows];
+    i64_scaled_batch<kRoundRows>(Rv, ex, d);
+    store_batch<kRoundRows, GEN>(p, w, ro, co, d, m0, 1);
+  }
 }
 
 // ---------------------------------------------------------------- host side
@@ -960,7 +974,7 @@ bool encode_map(CUtensorMap* map, const void* base, bool is_f32, int64_t kpad, i
 template <int KIND, int S, int STAGES, bool GEN>
 cudaError_t launch_tc_mode(const Problem& p, const Tables& tab, const void* a, const void* bop, const int32_t* eu,
                       const int32_t* ev, int64_t kpad, double* w, unsigned* err, int ksplit,
-                      unsigned long long* wacc, unsigned* tile_ctr, cudaStream_t st) {
+                      unsigned long long* wacc, cudaStream_t st) {
   const bool f32 = KIND == MODE_TF32;
   CUtensorMap ma, mb;
   if (!make_map(&ma, a, f32, kpad, p.M, (int64_t)S * p.n_q, TM) ||
@@ -980,7 +994,6 @@ cudaError_t launch_tc_mode(const Problem& p, const Tables& tab, const void* a, c
   if (args.kb_per_split < 2) args.kb_per_split = 2;
   args.ksplit = (args.n_kb + args.kb_per_split - 1) / args.kb_per_split;
   args.wacc = wacc;
-  args.tile_ctr = tile_ctr;
   args.wrow = tab.wrow;
   args.wcol = tab.wcol;
   constexpr int TNk = TileCfg<KIND>::N;
@@ -1011,18 +1024,31 @@ cudaError_t launch_tc_mode(const Problem& p, const Tables& tab, const void* a, c
   cfg.numAttrs = 1;
   cudaError_t le = cudaLaunchKernelEx(&cfg, kern, ma, mb, args);
   ++g_kernel_launches;
+  if (le != cudaSuccess || KIND != MODE_SPLIT || args.ksplit == 1) return le;
+  // the rounding of the split-K sums, one thread per kRoundRows outputs
+  const int64_t work = (int64_t)p.n_q * ((p.M + kRoundRows - 1) / kRoundRows) * p.N;
+  int sms = 148;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t blocks = (work + kRoundThreads - 1) / kRoundThreads;
+  cudaLaunchConfig_t rc = cfg;
+  rc.gridDim = dim3((unsigned)(blocks < (int64_t)sms * 8 ? blocks : (int64_t)sms * 8));
+  rc.blockDim = dim3(kRoundThreads);
+  rc.dynamicSmemBytes = 0;
+  le = cudaLaunchKernelEx(&rc, splitk_round_kernel<GEN>, p, (const unsigned long long*)wacc, eu, ev,
+                          tab.wrow, tab.wcol, w, (const unsigned*)err);
+  ++g_kernel_launches;
   return le;
 }
 
 template <int KIND, int S, int STAGES>
 cudaError_t launch_tc(const Problem& p, const Tables& tab, const void* a, const void* bop, const int32_t* eu,
                       const int32_t* ev, int64_t kpad, double* w, unsigned* err, int ksplit,
-                      unsigned long long* wacc, unsigned* tile_ctr, cudaStream_t st) {
+                      unsigned long long* wacc, cudaStream_t st) {
   if (p.es == 1 && !p.negate && !p.accumulate)
     return launch_tc_mode<KIND, S, STAGES, false>(p, tab, a, bop, eu, ev, kpad, w, err, ksplit, wacc,
-                                                  tile_ctr, st);
+                                                  st);
   return launch_tc_mode<KIND, S, STAGES, true>(p, tab, a, bop, eu, ev, kpad, w, err, ksplit, wacc,
-                                               tile_ctr, st);
+                                               st);
 }
 
 }  // namespace
@@ -1030,21 +1056,20 @@ cudaError_t launch_tc(const Problem& p, const Tables& tab, const void* a, const 
 cudaError_t launch_gemm_split(const Problem& p, const Tables& tab, int n_slices, const uint16_t* us,
                               const uint16_t* vs, const int32_t* eu, const int32_t* ev,
                               int64_t kpad, double* w, unsigned* err, int ksplit,
-                              unsigned long long* wacc, unsigned* tile_ctr, cudaStream_t st) {
+                              unsigned long long* wacc, cudaStream_t st) {
   switch (n_slices) {
-    case 2: return launch_tc<MODE_SPLIT, 2, 2>(p, tab, us, vs, eu, ev, kpad, w, err, ksplit, wacc, tile_ctr, st);
-    case 3: return launch_tc<MODE_SPLIT, 3, 2>(p, tab, us, vs, eu, ev, kpad, w, err, ksplit, wacc, tile_ctr, st);
-    case 4: return launch_tc<MODE_SPLIT, 4, 2>(p, tab, us, vs, eu, ev, kpad, w, err, ksplit, wacc, tile_ctr, st);
-    case 5: return launch_tc<MODE_SPLIT, 5, 2>(p, tab, us, vs, eu, ev, kpad, w, err, ksplit, wacc, tile_ctr, st);
-    case 6: return launch_tc<MODE_SPLIT, 6, 2>(p, tab, us, vs, eu, ev, kpad, w, err, ksplit, wacc, tile_ctr, st);
+    case 2: return launch_tc<MODE_SPLIT, 2, 2>(p, tab, us, vs, eu, ev, kpad, w, err, ksplit, wacc, st);
+    case 3: return launch_tc<MODE_SPLIT, 3, 2>(p, tab, us, vs, eu, ev, kpad, w, err, ksplit, wacc, st);
+    case 4: return launch_tc<MODE_SPLIT, 4, 2>(p, tab, us, vs, eu, ev, kpad, w, err, ksplit, wacc, st);
+    case 5: return launch_tc<MODE_SPLIT, 5, 2>(p, tab, us, vs, eu, ev, kpad, w, err, ksplit, wacc, st);
+    case 6: return launch_tc<MODE_SPLIT, 6, 2>(p, tab, us, vs, eu, ev, kpad, w, err, ksplit, wacc, st);
   }
   return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_gemm_tf32(const Problem& p, const Tables& tab, const float* u, const float* v,
                              int64_t kpad, double* w, unsigned* err, cudaStream_t st) {
-  return launch_tc<MODE_TF32, 1, 6>(p, tab, u, v, nullptr, nullptr, kpad, w, err, 1, nullptr, nullptr,
-                                    st);
+  return launch_tc<MODE_TF32, 1, 8>(p, tab, u, v, nullptr, nullptr, kpad, w, err, 1, nullptr, st);
 }
 
 cudaError_t launch_bounded_wait_selftest(unsigned* err, long long limit_cycles, cudaStream_t st) {

@@ -46,11 +46,10 @@ int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
 // Byte offsets of one pass's workspace regions (a pass covers n_q irreps).
 struct Layout {
-  uint64_t off_tab = 0, off_a = 0, off_b = 0, off_ea = 0, off_eb = 0, off_acc = 0, off_ctr = 0;
+  uint64_t off_tab = 0, off_a = 0, off_b = 0, off_ea = 0, off_eb = 0, off_acc = 0;
   uint64_t off_part = 0;
   uint64_t bytes = 256;
   int ksplit = 1;
-  int64_t n_tiles = 0;
   bool ok = true;
 };
 
@@ -78,11 +77,7 @@ Layout make_layout(const Problem& pr, bool tensor_core, symctr_precision prec, i
       L.off_eb = region(nq * pr.N * 4);
       if (prep_partials_entries(pr) > 0) L.off_part = region(prep_partials_entries(pr) * 4);
       L.ksplit = split_k_ranges(pr, kpad);
-      L.n_tiles = ((pr.M + 127) / 128) * ((pr.N + 127) / 128) * nq;
-      if (L.ksplit > 1) {
-        L.off_acc = region(nq * pr.M * pr.N * 8);
-        L.off_ctr = region(L.n_tiles * 4);
-      }
+      if (L.ksplit > 1) L.off_acc = region(nq * pr.M * pr.N * 8);
     } else {
       L.off_a = region(ra * 4);
       L.off_b = region(rb * 4);
@@ -617,20 +612,18 @@ symctr_status run_contract_body(const symctr_plan* P, const double* u, const dou
       if (e != cudaSuccess) return cuda_status(e, "offset tables");
     }
     unsigned long long* acc = L.ksplit > 1 ? (unsigned long long*)(base + L.off_acc) : nullptr;
-    unsigned* tile_ctr = L.ksplit > 1 ? (unsigned*)(base + L.off_ctr) : nullptr;
     const int64_t acc_n = L.ksplit > 1 ? (int64_t)pc.n_q * pc.M * pc.N : 0;
-    const int64_t ctr_n = L.ksplit > 1 ? L.n_tiles : 0;
     int32_t* ea = split ? (int32_t*)(base + L.off_ea) : nullptr;
     int32_t* eb = split ? (int32_t*)(base + L.off_eb) : nullptr;
     int32_t* part = split && L.off_part ? (int32_t*)(base + L.off_part) : nullptr;
     e = launch_prep(pc, tab, split, P->n_slices, u, v, base + L.off_a, base + L.off_b, ea, eb, part,
-                    P->kpad, err, barrier, acc, acc_n, tile_ctr, ctr_n, st);
+                    P->kpad, err, barrier, acc, acc_n, st);
     if (e != cudaSuccess) return cuda_status(e, "operand preparation");
     if (P->prof && q0 == 0) cudaEventRecord(P->ev[1], st);
     if (split)
       e = launch_gemm_split(pc, tab, P->n_slices, (const uint16_t*)(base + L.off_a),
                             (const uint16_t*)(base + L.off_b), ea, eb, P->kpad, w, err, L.ksplit,
-                            acc, tile_ctr, st);
+                            acc, st);
     else
       e = launch_gemm_tf32(pc, tab, (const float*)(base + L.off_a),
                            (const float*)(base + L.off_b), P->kpad, w, err, st);

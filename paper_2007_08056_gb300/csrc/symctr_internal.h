@@ -199,13 +199,12 @@ cudaError_t launch_fill_zero(double* w, int64_t n, cudaStream_t st);
 cudaError_t launch_prep(const Problem& p, const Tables& t, bool split, int n_slices,
                         const double* u, const double* v, void* ua, void* va, int32_t* eu,
                         int32_t* ev, int32_t* partials, int64_t kpad, unsigned* err, unsigned* barrier,
-                        unsigned long long* zero64, int64_t zero64_n, unsigned* zero32,
-                        int64_t zero32_n, cudaStream_t st);
+                        unsigned long long* zero64, int64_t zero64_n, cudaStream_t st);
 cudaError_t launch_bounded_wait_selftest(unsigned* err, long long limit_cycles, cudaStream_t st);
 cudaError_t launch_gemm_split(const Problem& p, const Tables& t, int n_slices, const uint16_t* us,
                               const uint16_t* vs, const int32_t* eu, const int32_t* ev,
                               int64_t kpad, double* w, unsigned* err, int ksplit,
-                              unsigned long long* wacc, unsigned* tile_ctr, cudaStream_t st);
+                              unsigned long long* wacc, cudaStream_t st);
 cudaError_t launch_gemm_tf32(const Problem& p, const Tables& t, const float* u, const float* v,
                              int64_t kpad, double* w, unsigned* err, cudaStream_t st);
 

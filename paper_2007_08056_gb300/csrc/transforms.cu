@@ -230,8 +230,6 @@ struct PrepArgs {
   unsigned* barrier;
   unsigned long long* zero64;  // split-K partial sums, zeroed here
   int64_t zero64_n;
-  unsigned* zero32;            // split-K tile counters, zeroed here
-  int64_t zero32_n;
 };
 
 __device__ __forceinline__ void operand_dims(const Problem& p, int op, int64_t* R, int64_t* Cn) {
@@ -563,7 +561,6 @@ __global__ void __launch_bounds__(THREADS, 4) prep_kernel(PrepArgs a) {
   const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
   const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   for (int64_t i = gtid; i < a.zero64_n; i += gthreads) a.zero64[i] = 0ull;
-  for (int64_t i = gtid; i < a.zero32_n; i += gthreads) a.zero32[i] = 0u;
   if (S > 0) {
     const uint32_t tiles0 = (uint32_t)(((p.M + TILE - 1) / TILE) * a.parts * p.n_q);
     const uint32_t tiles1 = (uint32_t)(((p.N + TILE - 1) / TILE) * a.parts * p.n_q);
@@ -632,8 +629,7 @@ cudaError_t launch_align_f64(const Problem& p, int operand, int direction, const
 cudaError_t launch_prep(const Problem& p, const Tables& t, bool split, int n_slices,
                         const double* u, const double* v, void* ua, void* va, int32_t* eu,
                         int32_t* ev, int32_t* partials, int64_t kpad, unsigned* err, unsigned* barrier,
-                        unsigned long long* zero64, int64_t zero64_n, unsigned* zero32,
-                        int64_t zero32_n, cudaStream_t st) {
+                        unsigned long long* zero64, int64_t zero64_n, cudaStream_t st) {
   const int S = split ? n_slices : 0;
   if (S < 0 || S > kMaxSlices) return cudaErrorInvalidValue;
   void (*kern)(PrepArgs) = nullptr;
@@ -696,8 +692,6 @@ cudaError_t launch_prep(const Problem& p, const Tables& t, bool split, int n_sli
   a.barrier = barrier;
   a.zero64 = zero64;
   a.zero64_n = zero64_n;
-  a.zero32 = zero32;
-  a.zero32_n = zero32_n;
   void* params[] = {&a};
   cudaError_t e = cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(THREADS),
                                               params, 0, st);
