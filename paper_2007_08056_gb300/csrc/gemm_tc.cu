@@ -759,7 +759,21 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             int32_t t0 = s0[jj] + (int32_t)__float_as_uint(__uint_as_float(a0[j]) + M0) - B0;
             int32_t t1 = live1 ? s1[jj] + (int32_t)__float_as_uint(__uint_as_float(a1[j]) + M1) - B1 : 0;
             int32_t t2 = live2 ? s2[jj] + (int32_t)__float_as_uint(__uint_as_float(a2[j]) + M2) - B2 : 0;
-            long long low = live3 ? __float2ll_rn(__uint_as_float(a3[j]) * 16777216.0f) : 0ll;
+            // round(acc3 * 2^24) with FP32 operations only (no 64-bit
+            // conversion: those run on GB300's narrow float64 pipe).  |acc3|
+            // < 64 (at most kFoldChunks chunks since the last fold), so
+            // h = round(acc3 * 2^16) is a magic-number conversion, the
+            // remainder acc3 - h 2^-16 is exact and |.| <= 2^-17, and
+            // round(acc3 * 2^24) = 2^8 h + round(remainder * 2^24).
+            long long low = 0;
+            if (live3) {
+              const float x = __uint_as_float(a3[j]);
+              const float r = __fmaf_rn(x, 65536.0f, M0);
+              const float rem = x - (r - M0) * (1.0f / 65536.0f);
+              const int32_t h = (int32_t)__float_as_uint(r) - B0;
+              const int32_t l = (int32_t)__float_as_uint(__fmaf_rn(rem, 16777216.0f, M0)) - B0;
+              low = ((long long)h << 8) + l;
+            }
             st64[jj] = ((long long)t0 << 24) + ((long long)t1 << 16) + ((long long)t2 << 8) + low;
           }
         }
