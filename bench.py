@@ -615,6 +615,94 @@ def run_device(args, rank, world):
     return line
 
 
+def run_small(args, rank, world):
+    """Config 1 (the order-4 Z_3 contraction of Sec. 2, 6912-entry reduced
+    forms: launch-latency bound) and config 4 (PEPS-style gradients under
+    Z_2 x Z_3: forward y = T.Env, loss = sum y^2, hand-written backward through
+    the autograd Function; HBM-bound, its GEMVs run in float64 on the CUDA
+    cores in every form).  Whole-step device time, L2 flushed between steps,
+    errors against the oracle."""
+    import torch
+    import oracle as O
+    import paper_2007_08056_gb300 as sc
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+    dev = torch.device("cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    ev_s, ev_e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(args.steps):
+            flush.fill_(1)
+            ev_s.record()
+            fn()
+            ev_e.record()
+            ev_e.synchronize()
+            ts.append(ev_s.elapsed_time(ev_e))
+        return statistics.mean(ts)
+
+    if args.workload == "z3":
+        c = WL.Z3_ORDER4
+        uh, vh = WL.draw_pair(c)
+        u, v = torch.from_numpy(uh).to(dev), torch.from_numpy(vh).to(dev)
+        p = sc.Plan(c.einsum, c.moduli, spec(c.u), spec(c.v), args.precision)
+        w = torch.empty(p.shape_w, dtype=torch.float64, device=dev)
+        ms = max_over_ranks(timed(lambda: p.contract(u, v, out=w)), world, dev)
+        want = O.contract_blockloop(O.plan(c.einsum, O.Group(c.moduli), O.Sym(*spec(c.u)),
+                                           O.Sym(*spec(c.v))), uh, vh)
+        got = w.cpu().numpy()
+        return {"workload": "z3_order4 (config 1: G = 3, D = 4, reduced forms [3,3,3,4,4,4,4])",
+                "precision": args.precision, "ms_per_step": round(ms, 4),
+                "useful_flops_per_step": p.useful_flops,
+                "useful_tflops": round(replicas_value(p.useful_flops, ms, world), 6),
+                "bound": "launch latency (0.66 MFLOP per step)",
+                "rel_err_vs_oracle": float(f"{np.linalg.norm(got - want) / np.linalg.norm(want):.3e}")}
+    moduli = WL.PEPS_MODULI
+    Th, Envh = WL.draw(WL.PEPS_T, moduli), WL.draw(WL.PEPS_ENV, moduli)
+    T = torch.from_numpy(Th).to(dev).requires_grad_(True)
+    Env = torch.from_numpy(Envh).to(dev).requires_grad_(True)
+    py = sc.Plan(WL.PEPS_Y, moduli, spec(WL.PEPS_T), spec(WL.PEPS_ENV), args.precision)
+    pl = sc.Plan(WL.PEPS_LOSS, moduli, py.sym_w, py.sym_w, args.precision)
+
+    def step():
+        T.grad = None
+        Env.grad = None
+        y = sc.contract(py, T, Env)
+        sc.contract(pl, y, y).backward()
+
+    ms = max_over_ranks(timed(step), world, dev)
+    step()
+    torch.cuda.synchronize()
+    oy = O.plan(WL.PEPS_Y, O.Group(moduli), O.Sym(*spec(WL.PEPS_T)), O.Sym(*spec(WL.PEPS_ENV)))
+    y_ref = O.contract_blockloop(oy, Th, Envh)
+    gT_ref = O.grad_u(oy, 2 * y_ref, Envh)
+    gE_ref = O.grad_v(oy, Th, 2 * y_ref)
+    gT, gE = T.grad.cpu().numpy(), Env.grad.cpu().numpy()
+    rel = max(np.linalg.norm(gT - gT_ref) / np.linalg.norm(gT_ref),
+              np.linalg.norm(gE - gE_ref) / np.linalg.norm(gE_ref))
+    # algorithmic bytes: forward reads T's live sector and Env; the backward
+    # writes all of gT (zeros outside the live sector), reads Env and T's live
+    # sector again and writes gEnv
+    live_t = py.info.aligned_numel_u * 8
+    env_b = Envh.nbytes
+    nbytes = (live_t + env_b) + (Th.nbytes + env_b) + (live_t + env_b)
+    flops = 3 * py.useful_flops   # forward GEMV and the two adjoint products
+    achieved = nbytes / (ms * 1e-3) / 1e9
+    pk = peaks()
+    return {"workload": "peps_grad (config 4: Z_2 x Z_3, T [6,6,6,6,16,16,16,16,2], Env [6,6,6,16,16,16,16])",
+            "precision": args.precision, "ms_per_step": round(ms, 4),
+            "useful_tflops": round(replicas_value(flops, ms, world), 4),
+            "roofline": {"kernel": "whole step (gemm_f64 GEMVs, fill, align)", "bound": "hbm",
+                         "achieved": round(achieved, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
+                         "frac": round(achieved / pk["hbm_gbs"], 4),
+                         "algorithmic_bytes_per_step": nbytes},
+            "rel_err_grad_vs_oracle": float(f"{rel:.3e}")}
+
+
 def run_reference(args, rank, world):
     """The oracle on the host cores, on the same workload and metric."""
     if rank != 0:
@@ -658,7 +746,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["mps", "cc_ladder", "sweep", "table"], default="mps")
+    ap.add_argument("--workload", choices=["mps", "cc_ladder", "sweep", "table", "z3", "peps"],
+                    default="mps")
     ap.add_argument("--case", default="CC1_a", help="table: a Table-2 case (" + ", ".join(WL.TABLE2) + ")")
     ap.add_argument("--sweep-g", type=int, default=16, help="G of the sweep workload (config 5)")
     ap.add_argument("--sweep-dims", default="512,128",
@@ -690,6 +779,8 @@ def main():
         torch.distributed.init_process_group("nccl")
     if args.workload in ("sweep", "table"):
         line = run_device(args, rank, world)
+    elif args.workload in ("z3", "peps"):
+        line = run_small(args, rank, world)
     elif args.complex:
         line = run_complex(args, rank, world)
     else:

@@ -7,10 +7,12 @@
 // float64 throughput, so the aligned operands are never materialised: the
 // loads are free next to the FMAs.
 //
-// Two kernels: a 64x64 register-tiled kernel for GEMM-shaped problems and a
-// warp-per-row dot-product kernel for skinny ones (a few rows or columns, or
-// a tiny contracted extent), both with optional split-K through atomicAdd
-// into a zeroed output (or onto the existing output in accumulate mode).
+// Three kernels: a 64x64 register-tiled kernel for GEMM-shaped problems, a
+// warp-per-row dot-product kernel for skinny ones (a few rows or columns),
+// both with optional split-K through atomicAdd into a zeroed output (or onto
+// the existing output in accumulate mode), and a thread-per-row kernel for
+// skinny problems with a short contracted extent (the adjoints of a GEMV:
+// an outer product, K = 1, or K = 2), where lanes walking K would idle.
 #include <cstdint>
 
 #include "symctr_internal.h"
@@ -179,6 +181,62 @@ __global__ void __launch_bounds__(THREADS) gemm_f64_skinny(Problem p, bool long_
   }
 }
 
+// Skinny problems with K <= kShortK: one thread per row of the long side.  The
+// short side's values and the long side's column offsets depend only on the
+// irrep, so each block stages them in shared memory once per irrep; a thread
+// then computes two offsets (its row in L and in W) and K loads.
+constexpr int kShortK = 32;
+
+__global__ void __launch_bounds__(THREADS) gemm_f64_shortk(Problem p, bool long_is_u,
+                                                           const double* __restrict__ U,
+                                                           const double* __restrict__ V,
+                                                           double* __restrict__ W) {
+  __shared__ double sval[SKINNY_MAX][kShortK];
+  __shared__ int64_t lco[kShortK];
+  __shared__ int64_t wso[SKINNY_MAX];
+  const AxisMap& Lrows = long_is_u ? p.u.rows : p.v.rows;
+  const AxisMap& Lcols = long_is_u ? p.u.cols : p.v.cols;
+  const AxisMap& Srows = long_is_u ? p.v.rows : p.u.rows;
+  const AxisMap& Scols = long_is_u ? p.v.cols : p.u.cols;
+  const AxisMap& Wl = long_is_u ? p.w.rows : p.w.cols;
+  const AxisMap& Ws = long_is_u ? p.w.cols : p.w.rows;
+  const double* Lp = long_is_u ? U : V;
+  const double* Sp = long_is_u ? V : U;
+  const int64_t nL = long_is_u ? p.M : p.N;
+  const int nS = (int)(long_is_u ? p.N : p.M);
+  const int K = (int)p.K;
+  const int64_t per_q = (nL + THREADS - 1) / THREADS;
+  for (int64_t blk = blockIdx.x; blk < per_q * p.n_q; blk += gridDim.x) {
+    const int b = (int)(blk / per_q);
+    const int64_t l = (blk - (int64_t)b * per_q) * THREADS + threadIdx.x;
+    const int Q = batch_irrep(p, b);
+    __syncthreads();   // the previous irrep's readers are done
+    for (int i = threadIdx.x; i < nS * K; i += THREADS) {
+      const int sr = i / K, k = i - sr * K;
+      sval[sr][k] = Sp[p.es * (axis_offset(Srows, p.g, Q, sr) + axis_offset(Scols, p.g, Q, k))];
+    }
+    for (int k = threadIdx.x; k < K; k += THREADS) lco[k] = axis_offset(Lcols, p.g, Q, k);
+    for (int sr = threadIdx.x; sr < nS; sr += THREADS) wso[sr] = axis_offset(Ws, p.g, Q, sr);
+    __syncthreads();
+    if (l < nL) {
+      const int64_t loff = axis_offset(Lrows, p.g, Q, l);
+      const int64_t woff = axis_offset(Wl, p.g, Q, l);
+      double acc[SKINNY_MAX];
+#pragma unroll
+      for (int sr = 0; sr < SKINNY_MAX; ++sr) acc[sr] = 0.0;
+      for (int k = 0; k < K; ++k) {
+        const double x = Lp[p.es * (loff + lco[k])];
+#pragma unroll
+        for (int sr = 0; sr < SKINNY_MAX; ++sr)
+          if (sr < nS) acc[sr] = fma(x, sval[sr][k], acc[sr]);
+      }
+#pragma unroll
+      for (int sr = 0; sr < SKINNY_MAX; ++sr)
+        if (sr < nS) store_w(p, W + p.es * (woff + wso[sr]), acc[sr]);
+    }
+  }
+}
+
 int sm_count() {
   int dev = 0, sms = 148;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -209,6 +267,14 @@ cudaError_t launch_gemm_f64(const Problem& p, const double* u, const double* v, 
   if (skinny && (p.M <= SKINNY_MAX || p.N <= SKINNY_MAX)) {
     bool long_is_u = p.N <= SKINNY_MAX ? true : false;
     if (p.M <= SKINNY_MAX && p.N <= SKINNY_MAX) long_is_u = p.M >= p.N;
+    if (p.K <= kShortK) {
+      const int64_t nL = long_is_u ? p.M : p.N;
+      const int64_t blocks = (nL + THREADS - 1) / THREADS * p.n_q;
+      const int64_t cap = (int64_t)sms * 16;
+      gemm_f64_shortk<<<(int)(blocks < cap ? blocks : cap), THREADS, 0, st>>>(p, long_is_u, u, v, w);
+      ++g_kernel_launches;
+      return cudaGetLastError();
+    }
     int64_t nL = long_is_u ? p.M : p.N;
     int64_t warps = nL * p.n_q;
     int ksplit = 1;
