@@ -124,12 +124,44 @@ __global__ void __launch_bounds__(THREADS) gemm_f64_tiled(Problem p, int ksplit,
 // Skinny problems: the "long" side L (rows of U or of V, whichever is larger)
 // is spread over warps, the "short" side (<= 8 rows) is held in registers;
 // lanes stride over kappa.  Optional split-K over kappa ranges.
+//
+// Column offsets: kappa = o * I + i, where I (the "inner" extent) is the
+// product of the fastest block dims of the column map up to kInnerMax.  The
+// offset is then axis_offset(o * I) + inner(i), inner(i) being the block part
+// of i alone (independent of Q); each block tabulates inner() in shared
+// memory and each lane recomputes axis_offset(o * I) only when o changes
+// (every I / 32 steps), instead of one mixed-radix decomposition per element.
 constexpr int SKINNY_MAX = 8;
+constexpr int kInnerMax = 2048;
+
+// Product of the fastest block dims that the two column maps share, up to
+// kInnerMax (both maps index the same kappa, so their dims agree).
+__device__ __forceinline__ int64_t inner_extent(const AxisMap& a, const AxisMap& b) {
+  int64_t e = 1;
+  for (int i = a.n - 1, j = b.n - 1; i >= 0 && j >= 0; --i, --j) {
+    if (a.D[i] != b.D[j] || e * a.D[i] > kInnerMax) break;
+    e *= a.D[i];
+  }
+  return e;
+}
+
+// inner(i) for i < I: the block digits of i over the fastest block axes.
+__device__ void fill_inner(const AxisMap& a, int64_t I, int64_t* tab) {
+  for (int64_t i = threadIdx.x; i < I; i += blockDim.x) {
+    int64_t r = i, off = 0;
+    for (int d = a.n - 1; d >= 0 && r > 0; --d) {
+      off += (r % a.D[d]) * a.bstride[d];
+      r /= a.D[d];
+    }
+    tab[i] = off;
+  }
+}
 
 __global__ void __launch_bounds__(THREADS) gemm_f64_skinny(Problem p, bool long_is_u, int ksplit,
                                                            const double* __restrict__ U,
                                                            const double* __restrict__ V,
                                                            double* __restrict__ W) {
+  __shared__ int64_t tab_l[kInnerMax], tab_s[kInnerMax];
   const AxisMap& Lrows = long_is_u ? p.u.rows : p.v.rows;
   const AxisMap& Lcols = long_is_u ? p.u.cols : p.v.cols;
   const AxisMap& Srows = long_is_u ? p.v.rows : p.u.rows;
@@ -141,8 +173,14 @@ __global__ void __launch_bounds__(THREADS) gemm_f64_skinny(Problem p, bool long_
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const int64_t kchunk = (p.K + ksplit - 1) / ksplit;
+  const int64_t I = inner_extent(Lcols, Scols);
+  // K ranges start on multiples of I (K itself is one), so that a range
+  // covers whole inner blocks when I >= 32
+  const int64_t kchunk = ((p.K + ksplit - 1) / ksplit + I - 1) / I * I;
   const int64_t items = nL * p.n_q * ksplit;
+  fill_inner(Lcols, I, tab_l);
+  fill_inner(Scols, I, tab_s);
+  __syncthreads();
   for (int64_t it = warp; it < items; it += nwarps) {
     int64_t ks = it % ksplit;
     int64_t t2 = it / ksplit;
@@ -157,21 +195,71 @@ __global__ void __launch_bounds__(THREADS) gemm_f64_skinny(Problem p, bool long_
     double acc[SKINNY_MAX];
 #pragma unroll
     for (int s = 0; s < SKINNY_MAX; ++s) acc[s] = 0.0;
-    for (int64_t k = kbeg + lane; k < kend; k += 32) {
-      double x = Lp[p.es * (loff + axis_offset(Lcols, p.g, Q, k))];
-      int64_t sc = axis_offset(Scols, p.g, Q, k);
+    if (I >= 32) {
+      // whole inner blocks (kend is a multiple of I): lane j computes the two
+      // offsets of inner block ob + j, for 32 blocks at once, and the warp
+      // walks them with kUnroll independent loads per lane in flight
+      constexpr int kUnroll = 4;
+      for (int64_t ob = kbeg / I; ob * I < kend; ob += 32) {
+        const int64_t oj = ob + lane;
+        const bool own = oj * I < kend;
+        const int64_t lo_j = own ? loff + axis_offset(Lcols, p.g, Q, oj * I) : 0;
+        const int64_t so_j = own ? axis_offset(Scols, p.g, Q, oj * I) : 0;
+        const int64_t left = (kend - ob * I) / I;
+        const int nb = left < 32 ? (int)left : 32;
+        for (int j = 0; j < nb; ++j) {
+          const int64_t lo = __shfl_sync(0xffffffffu, lo_j, j);
+          const int64_t so = __shfl_sync(0xffffffffu, so_j, j);
+          for (int64_t i0 = lane; i0 < I; i0 += 32 * kUnroll) {
+            double x[kUnroll];
+            int64_t sc[kUnroll];
 #pragma unroll
-      for (int s = 0; s < SKINNY_MAX; ++s)
-        if (s < nS) acc[s] = fma(x, Sp[p.es * (soff[s] + sc)], acc[s]);
+            for (int u = 0; u < kUnroll; ++u) {
+              const int64_t i = i0 + 32 * u;
+              const bool in = i < I;
+              x[u] = in ? Lp[p.es * (lo + tab_l[i])] : 0.0;
+              sc[u] = in ? so + tab_s[i] : -1;
+            }
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+#pragma unroll
+              for (int s = 0; s < SKINNY_MAX; ++s)
+                if (s < nS && sc[u] >= 0) acc[s] = fma(x[u], Sp[p.es * (soff[s] + sc[u])], acc[s]);
+            }
+          }
+        }
+      }
+    } else {
+      int64_t k = kbeg + lane;
+      int64_t o = k / I, i = k - o * I;
+      int64_t lo = axis_offset(Lcols, p.g, Q, o * I), so = axis_offset(Scols, p.g, Q, o * I);
+      for (; k < kend; k += 32) {
+        const double x = Lp[p.es * (loff + lo + tab_l[i])];
+        const int64_t sc = so + tab_s[i];
+#pragma unroll
+        for (int s = 0; s < SKINNY_MAX; ++s)
+          if (s < nS) acc[s] = fma(x, Sp[p.es * (soff[s] + sc)], acc[s]);
+        i += 32;
+        if (i >= I) {
+          o += i / I;
+          i %= I;
+          if (k + 32 < kend) {
+            lo = axis_offset(Lcols, p.g, Q, o * I);
+            so = axis_offset(Scols, p.g, Q, o * I);
+          }
+        }
+      }
     }
 #pragma unroll
     for (int s = 0; s < SKINNY_MAX; ++s) {
       double a = acc[s];
-      for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+      for (int o2 = 16; o2 > 0; o2 >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o2);
       acc[s] = a;
     }
     if (lane == 0) {
-      for (int s = 0; s < nS; ++s) {
+#pragma unroll
+      for (int s = 0; s < SKINNY_MAX; ++s) {
+        if (s >= nS) continue;
         int64_t m = long_is_u ? l : s, n = long_is_u ? s : l;
         double* dst = W + p.es * (axis_offset(p.w.rows, p.g, Q, m) + axis_offset(p.w.cols, p.g, Q, n));
         if (ksplit > 1) atomicAdd(dst, signed_result(p, acc[s]));
@@ -181,11 +269,18 @@ __global__ void __launch_bounds__(THREADS) gemm_f64_skinny(Problem p, bool long_
   }
 }
 
-// Skinny problems with K <= kShortK: one thread per row of the long side.  The
-// short side's values and the long side's column offsets depend only on the
-// irrep, so each block stages them in shared memory once per irrep; a thread
-// then computes two offsets (its row in L and in W) and K loads.
+// Skinny problems with K <= kShortK: one thread per row of the long side, a
+// block taking kShortRows consecutive rows at a time (kShortRows / THREADS
+// per thread).  The short side's values and the long side's column offsets
+// depend only on the irrep, so a block stages them in shared memory when the
+// irrep changes.  Row offsets in L and W use the inner-block split of the
+// skinny kernel above (l = o * I + i): a table of inner(i) per map, and
+// axis_offset(o * I) for the inner blocks of a chunk computed by as many
+// threads at once (the index arithmetic of one offset is a long dependent
+// chain under a product group, so it is never left to a single thread).
 constexpr int kShortK = 32;
+constexpr int kShortRows = 4096;
+constexpr int kShortSlots = kShortRows / 32 + 2;
 
 __global__ void __launch_bounds__(THREADS) gemm_f64_shortk(Problem p, bool long_is_u,
                                                            const double* __restrict__ U,
@@ -194,6 +289,8 @@ __global__ void __launch_bounds__(THREADS) gemm_f64_shortk(Problem p, bool long_
   __shared__ double sval[SKINNY_MAX][kShortK];
   __shared__ int64_t lco[kShortK];
   __shared__ int64_t wso[SKINNY_MAX];
+  __shared__ int64_t tab_lr[kInnerMax], tab_w[kInnerMax];
+  __shared__ int64_t ob_l[kShortSlots], ob_w[kShortSlots];
   const AxisMap& Lrows = long_is_u ? p.u.rows : p.v.rows;
   const AxisMap& Lcols = long_is_u ? p.u.cols : p.v.cols;
   const AxisMap& Srows = long_is_u ? p.v.rows : p.u.rows;
@@ -205,22 +302,49 @@ __global__ void __launch_bounds__(THREADS) gemm_f64_shortk(Problem p, bool long_
   const int64_t nL = long_is_u ? p.M : p.N;
   const int nS = (int)(long_is_u ? p.N : p.M);
   const int K = (int)p.K;
-  const int64_t per_q = (nL + THREADS - 1) / THREADS;
+  const int64_t per_q = (nL + kShortRows - 1) / kShortRows;
+  // the rows of L and W's axis along the long side index the same modes
+  const int64_t I = inner_extent(Lrows, Wl);
+  const bool tabulated = I >= 32;   // then a chunk touches <= kShortSlots inner blocks
+  if (tabulated) {
+    fill_inner(Lrows, I, tab_lr);
+    fill_inner(Wl, I, tab_w);
+  }
+  int staged = -1;
   for (int64_t blk = blockIdx.x; blk < per_q * p.n_q; blk += gridDim.x) {
     const int b = (int)(blk / per_q);
-    const int64_t l = (blk - (int64_t)b * per_q) * THREADS + threadIdx.x;
+    const int64_t l0 = (blk - (int64_t)b * per_q) * kShortRows;
+    const int64_t lend = l0 + kShortRows < nL ? l0 + kShortRows : nL;
+    const int64_t o0 = l0 / I;
     const int Q = batch_irrep(p, b);
-    __syncthreads();   // the previous irrep's readers are done
-    for (int i = threadIdx.x; i < nS * K; i += THREADS) {
-      const int sr = i / K, k = i - sr * K;
-      sval[sr][k] = Sp[p.es * (axis_offset(Srows, p.g, Q, sr) + axis_offset(Scols, p.g, Q, k))];
+    __syncthreads();   // the previous chunk's readers are done
+    if (b != staged) {
+      for (int i = threadIdx.x; i < nS * K; i += THREADS) {
+        const int sr = i / K, k = i - sr * K;
+        sval[sr][k] = Sp[p.es * (axis_offset(Srows, p.g, Q, sr) + axis_offset(Scols, p.g, Q, k))];
+      }
+      for (int k = threadIdx.x; k < K; k += THREADS) lco[k] = axis_offset(Lcols, p.g, Q, k);
+      for (int sr = threadIdx.x; sr < nS; sr += THREADS) wso[sr] = axis_offset(Ws, p.g, Q, sr);
+      staged = b;
     }
-    for (int k = threadIdx.x; k < K; k += THREADS) lco[k] = axis_offset(Lcols, p.g, Q, k);
-    for (int sr = threadIdx.x; sr < nS; sr += THREADS) wso[sr] = axis_offset(Ws, p.g, Q, sr);
+    if (tabulated) {
+      const int64_t n_o = (lend - 1) / I - o0 + 1;
+      for (int64_t j = threadIdx.x; j < n_o; j += THREADS) {
+        ob_l[j] = axis_offset(Lrows, p.g, Q, (o0 + j) * I);
+        ob_w[j] = axis_offset(Wl, p.g, Q, (o0 + j) * I);
+      }
+    }
     __syncthreads();
-    if (l < nL) {
-      const int64_t loff = axis_offset(Lrows, p.g, Q, l);
-      const int64_t woff = axis_offset(Wl, p.g, Q, l);
+    for (int64_t l = l0 + threadIdx.x; l < lend; l += THREADS) {
+      int64_t loff, woff;
+      if (tabulated) {
+        const int64_t o = l / I, i = l - o * I;
+        loff = ob_l[o - o0] + tab_lr[i];
+        woff = ob_w[o - o0] + tab_w[i];
+      } else {
+        loff = axis_offset(Lrows, p.g, Q, l);
+        woff = axis_offset(Wl, p.g, Q, l);
+      }
       double acc[SKINNY_MAX];
 #pragma unroll
       for (int sr = 0; sr < SKINNY_MAX; ++sr) acc[sr] = 0.0;
@@ -269,7 +393,7 @@ cudaError_t launch_gemm_f64(const Problem& p, const double* u, const double* v, 
     if (p.M <= SKINNY_MAX && p.N <= SKINNY_MAX) long_is_u = p.M >= p.N;
     if (p.K <= kShortK) {
       const int64_t nL = long_is_u ? p.M : p.N;
-      const int64_t blocks = (nL + THREADS - 1) / THREADS * p.n_q;
+      const int64_t blocks = (nL + kShortRows - 1) / kShortRows * p.n_q;
       const int64_t cap = (int64_t)sms * 16;
       gemm_f64_shortk<<<(int)(blocks < cap ? blocks : cap), THREADS, 0, st>>>(p, long_is_u, u, v, w);
       ++g_kernel_launches;
