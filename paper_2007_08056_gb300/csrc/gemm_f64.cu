@@ -390,7 +390,10 @@ cudaError_t launch_gemm_f64(const Problem& p, const double* u, const double* v, 
   bool skinny = p.M < 16 || p.N < 16;
   if (skinny && (p.M <= SKINNY_MAX || p.N <= SKINNY_MAX)) {
     bool long_is_u = p.N <= SKINNY_MAX ? true : false;
-    if (p.M <= SKINNY_MAX && p.N <= SKINNY_MAX) long_is_u = p.M >= p.N;
+    // both sides short: an item reads one long-side row and every short-side
+    // row along its K range, nL * (1 + nS) rows in all, fewest with the
+    // shorter side as the long one
+    if (p.M <= SKINNY_MAX && p.N <= SKINNY_MAX) long_is_u = p.M <= p.N;
     if (p.K <= kShortK) {
       const int64_t nL = long_is_u ? p.M : p.N;
       const int64_t blocks = (nL + kShortRows - 1) / kShortRows * p.n_q;
