@@ -157,6 +157,10 @@ __device__ void fill_inner(const AxisMap& a, int64_t I, int64_t* tab) {
   }
 }
 
+// NS = the short side's row count (one instance per count, so that no
+// float64 instruction of an absent row is issued: GB300's float64 pipe is
+// narrow and issues predicated-off instructions all the same).
+template <int NS>
 __global__ void __launch_bounds__(THREADS) gemm_f64_skinny(Problem p, bool long_is_u, int ksplit,
                                                            const double* __restrict__ U,
                                                            const double* __restrict__ V,
@@ -169,7 +173,6 @@ __global__ void __launch_bounds__(THREADS) gemm_f64_skinny(Problem p, bool long_
   const double* Lp = long_is_u ? U : V;
   const double* Sp = long_is_u ? V : U;
   const int64_t nL = long_is_u ? p.M : p.N;
-  const int nS = (int)(long_is_u ? p.N : p.M);
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -189,12 +192,12 @@ __global__ void __launch_bounds__(THREADS) gemm_f64_skinny(Problem p, bool long_
     int Q = batch_irrep(p, (int)b);
     int64_t kbeg = ks * kchunk, kend = kbeg + kchunk < p.K ? kbeg + kchunk : p.K;
     int64_t loff = axis_offset(Lrows, p.g, Q, l);
-    int64_t soff[SKINNY_MAX];
+    int64_t soff[NS];
 #pragma unroll
-    for (int s = 0; s < SKINNY_MAX; ++s) soff[s] = s < nS ? axis_offset(Srows, p.g, Q, s) : 0;
-    double acc[SKINNY_MAX];
+    for (int s = 0; s < NS; ++s) soff[s] = axis_offset(Srows, p.g, Q, s);
+    double acc[NS];
 #pragma unroll
-    for (int s = 0; s < SKINNY_MAX; ++s) acc[s] = 0.0;
+    for (int s = 0; s < NS; ++s) acc[s] = 0.0;
     if (I >= 32) {
       // whole inner blocks (kend is a multiple of I): lane j computes the two
       // offsets of inner block ob + j, for 32 blocks at once, and the warp
@@ -223,8 +226,8 @@ __global__ void __launch_bounds__(THREADS) gemm_f64_skinny(Problem p, bool long_
 #pragma unroll
             for (int u = 0; u < kUnroll; ++u) {
 #pragma unroll
-              for (int s = 0; s < SKINNY_MAX; ++s)
-                if (s < nS && sc[u] >= 0) acc[s] = fma(x[u], Sp[p.es * (soff[s] + sc[u])], acc[s]);
+              for (int s = 0; s < NS; ++s)
+                if (sc[u] >= 0) acc[s] = fma(x[u], Sp[p.es * (soff[s] + sc[u])], acc[s]);
             }
           }
         }
@@ -237,8 +240,8 @@ __global__ void __launch_bounds__(THREADS) gemm_f64_skinny(Problem p, bool long_
         const double x = Lp[p.es * (loff + lo + tab_l[i])];
         const int64_t sc = so + tab_s[i];
 #pragma unroll
-        for (int s = 0; s < SKINNY_MAX; ++s)
-          if (s < nS) acc[s] = fma(x, Sp[p.es * (soff[s] + sc)], acc[s]);
+        for (int s = 0; s < NS; ++s)
+          acc[s] = fma(x, Sp[p.es * (soff[s] + sc)], acc[s]);
         i += 32;
         if (i >= I) {
           o += i / I;
@@ -251,15 +254,14 @@ __global__ void __launch_bounds__(THREADS) gemm_f64_skinny(Problem p, bool long_
       }
     }
 #pragma unroll
-    for (int s = 0; s < SKINNY_MAX; ++s) {
+    for (int s = 0; s < NS; ++s) {
       double a = acc[s];
       for (int o2 = 16; o2 > 0; o2 >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o2);
       acc[s] = a;
     }
     if (lane == 0) {
 #pragma unroll
-      for (int s = 0; s < SKINNY_MAX; ++s) {
-        if (s >= nS) continue;
+      for (int s = 0; s < NS; ++s) {
         int64_t m = long_is_u ? l : s, n = long_is_u ? s : l;
         double* dst = W + p.es * (axis_offset(p.w.rows, p.g, Q, m) + axis_offset(p.w.cols, p.g, Q, n));
         if (ksplit > 1) atomicAdd(dst, signed_result(p, acc[s]));
@@ -282,6 +284,7 @@ constexpr int kShortK = 32;
 constexpr int kShortRows = 4096;
 constexpr int kShortSlots = kShortRows / 32 + 2;
 
+template <int NS>
 __global__ void __launch_bounds__(THREADS) gemm_f64_shortk(Problem p, bool long_is_u,
                                                            const double* __restrict__ U,
                                                            const double* __restrict__ V,
@@ -300,7 +303,7 @@ __global__ void __launch_bounds__(THREADS) gemm_f64_shortk(Problem p, bool long_
   const double* Lp = long_is_u ? U : V;
   const double* Sp = long_is_u ? V : U;
   const int64_t nL = long_is_u ? p.M : p.N;
-  const int nS = (int)(long_is_u ? p.N : p.M);
+  constexpr int nS = NS;   // the launcher picks the instance with NS == the short side
   const int K = (int)p.K;
   const int64_t per_q = (nL + kShortRows - 1) / kShortRows;
   // the rows of L and W's axis along the long side index the same modes
@@ -335,28 +338,37 @@ __global__ void __launch_bounds__(THREADS) gemm_f64_shortk(Problem p, bool long_
       }
     }
     __syncthreads();
+    // (o, i) of the thread's first row by one division; later rows step by
+    // THREADS without dividing (64-bit integer division runs on GB300's
+    // narrow float64 pipe)
+    int64_t o = tabulated ? (l0 + threadIdx.x) / I : 0;
+    int64_t i = tabulated ? l0 + threadIdx.x - o * I : 0;
     for (int64_t l = l0 + threadIdx.x; l < lend; l += THREADS) {
       int64_t loff, woff;
       if (tabulated) {
-        const int64_t o = l / I, i = l - o * I;
         loff = ob_l[o - o0] + tab_lr[i];
         woff = ob_w[o - o0] + tab_w[i];
+        i += THREADS;
+        while (i >= I) {
+          i -= I;
+          ++o;
+        }
       } else {
         loff = axis_offset(Lrows, p.g, Q, l);
         woff = axis_offset(Wl, p.g, Q, l);
       }
-      double acc[SKINNY_MAX];
+      double acc[NS];
 #pragma unroll
-      for (int sr = 0; sr < SKINNY_MAX; ++sr) acc[sr] = 0.0;
+      for (int sr = 0; sr < NS; ++sr) acc[sr] = 0.0;
       for (int k = 0; k < K; ++k) {
         const double x = Lp[p.es * (loff + lco[k])];
 #pragma unroll
-        for (int sr = 0; sr < SKINNY_MAX; ++sr)
-          if (sr < nS) acc[sr] = fma(x, sval[sr][k], acc[sr]);
+        for (int sr = 0; sr < NS; ++sr)
+          acc[sr] = fma(x, sval[sr][k], acc[sr]);
       }
 #pragma unroll
-      for (int sr = 0; sr < SKINNY_MAX; ++sr)
-        if (sr < nS) store_w(p, W + p.es * (woff + wso[sr]), acc[sr]);
+      for (int sr = 0; sr < NS; ++sr)
+        store_w(p, W + p.es * (woff + wso[sr]), acc[sr]);
     }
   }
 }
@@ -398,7 +410,17 @@ cudaError_t launch_gemm_f64(const Problem& p, const double* u, const double* v, 
       const int64_t nL = long_is_u ? p.M : p.N;
       const int64_t blocks = (nL + kShortRows - 1) / kShortRows * p.n_q;
       const int64_t cap = (int64_t)sms * 16;
-      gemm_f64_shortk<<<(int)(blocks < cap ? blocks : cap), THREADS, 0, st>>>(p, long_is_u, u, v, w);
+      const int grid = (int)(blocks < cap ? blocks : cap), nS = (int)(long_is_u ? p.N : p.M);
+      switch (nS) {
+        case 1: gemm_f64_shortk<1><<<grid, THREADS, 0, st>>>(p, long_is_u, u, v, w); break;
+        case 2: gemm_f64_shortk<2><<<grid, THREADS, 0, st>>>(p, long_is_u, u, v, w); break;
+        case 3: gemm_f64_shortk<3><<<grid, THREADS, 0, st>>>(p, long_is_u, u, v, w); break;
+        case 4: gemm_f64_shortk<4><<<grid, THREADS, 0, st>>>(p, long_is_u, u, v, w); break;
+        case 5: gemm_f64_shortk<5><<<grid, THREADS, 0, st>>>(p, long_is_u, u, v, w); break;
+        case 6: gemm_f64_shortk<6><<<grid, THREADS, 0, st>>>(p, long_is_u, u, v, w); break;
+        case 7: gemm_f64_shortk<7><<<grid, THREADS, 0, st>>>(p, long_is_u, u, v, w); break;
+        default: gemm_f64_shortk<8><<<grid, THREADS, 0, st>>>(p, long_is_u, u, v, w); break;
+      }
       ++g_kernel_launches;
       return cudaGetLastError();
     }
@@ -413,8 +435,17 @@ cudaError_t launch_gemm_f64(const Problem& p, const double* u, const double* v, 
     }
     int64_t blocks = (warps * ksplit * 32 + THREADS - 1) / THREADS;
     int64_t cap = (int64_t)sms * 16;
-    gemm_f64_skinny<<<(int)(blocks < cap ? blocks : cap), THREADS, 0, st>>>(p, long_is_u, ksplit, u,
-                                                                             v, w);
+    const int grid = (int)(blocks < cap ? blocks : cap), nS = (int)(long_is_u ? p.N : p.M);
+    switch (nS) {
+      case 1: gemm_f64_skinny<1><<<grid, THREADS, 0, st>>>(p, long_is_u, ksplit, u, v, w); break;
+      case 2: gemm_f64_skinny<2><<<grid, THREADS, 0, st>>>(p, long_is_u, ksplit, u, v, w); break;
+      case 3: gemm_f64_skinny<3><<<grid, THREADS, 0, st>>>(p, long_is_u, ksplit, u, v, w); break;
+      case 4: gemm_f64_skinny<4><<<grid, THREADS, 0, st>>>(p, long_is_u, ksplit, u, v, w); break;
+      case 5: gemm_f64_skinny<5><<<grid, THREADS, 0, st>>>(p, long_is_u, ksplit, u, v, w); break;
+      case 6: gemm_f64_skinny<6><<<grid, THREADS, 0, st>>>(p, long_is_u, ksplit, u, v, w); break;
+      case 7: gemm_f64_skinny<7><<<grid, THREADS, 0, st>>>(p, long_is_u, ksplit, u, v, w); break;
+      default: gemm_f64_skinny<8><<<grid, THREADS, 0, st>>>(p, long_is_u, ksplit, u, v, w); break;
+    }
     ++g_kernel_launches;
     return cudaGetLastError();
   }

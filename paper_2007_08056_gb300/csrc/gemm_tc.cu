@@ -187,15 +187,6 @@ __device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t* r) {
                : "r"(taddr));
 }
 
-// 8 consecutive 32-bit TMEM columns of this warp's 32 lanes.
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* r) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7])
-      : "r"(taddr));
-}
-
 // 16 consecutive 32-bit TMEM columns of this warp's 32 lanes.
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
   asm volatile(
@@ -656,7 +647,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int quad = warp & 3;            // TMEM lane quadrant this warp may access
     const int half = ew >> 2;             // column half
     const int row = quad * 32 + lane;
-    const int64_t m = m0 + row;
     const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(half * (TNk / 2));
     // Running sums of the exact diagonals d = 0, 1, 2 in their own units
     // (1, 2^-8, 2^-16).  Diagonal d has d + 1 slice pairs of |a_i b_j| <= 2^14
@@ -681,6 +671,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
       for (int pc = 0; pc < 16; ++pc) {
         uint32_t a0[4], a1[4], a2[4];
+        (void)a0, (void)a1, (void)a2;   // unused in the variants that skip a diagonal
         if constexpr (d0) tmem_ld4(lane_base + 0 + pc * 4, a0);
         if constexpr (d1) tmem_ld4(lane_base + 128 + pc * 4, a1);
         if constexpr (d2) tmem_ld4(lane_base + 256 + pc * 4, a2);
@@ -894,10 +885,23 @@ __global__ void __launch_bounds__(kRoundThreads) splitk_round_kernel(
   const int64_t M = p.M, N = p.N;
   const int64_t row_groups = (M + kRoundRows - 1) / kRoundRows;
   const int64_t total = (int64_t)p.n_q * row_groups * N;
+  // 32-bit index arithmetic where it fits (64-bit integer division runs on
+  // GB300's narrow float64 pipe)
+  const bool narrow = total <= 0x7FFFFFFF;
   for (int64_t i = (int64_t)blockIdx.x * kRoundThreads + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * kRoundThreads) {
-    const int64_t n = i % N, g = i / N;
-    const int64_t b = g / row_groups, m0 = (g % row_groups) * kRoundRows;
+    int64_t n, b, m0;
+    if (narrow) {
+      const uint32_t i32 = (uint32_t)i, n32 = (uint32_t)N, g = i32 / n32, rg = (uint32_t)row_groups;
+      n = i32 - g * n32;
+      b = g / rg;
+      m0 = (int64_t)(g - (uint32_t)b * rg) * kRoundRows;
+    } else {
+      const int64_t g = i / N;
+      n = i - g * N;
+      b = g / row_groups;
+      m0 = (g - b * row_groups) * kRoundRows;
+    }
     const int64_t co = wcol[b * N + n];
     const int ce = ev[b * N + n] - kExpBias - 36;
     long long Rv[kRoundRows];

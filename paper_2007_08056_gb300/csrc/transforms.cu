@@ -108,8 +108,6 @@ __global__ void __launch_bounds__(THREADS) align_kernel(Problem p, OperandMap m,
 // scale 2^(-8(i+j)) and |a_i b_j| <= 2^14.
 // ---------------------------------------------------------------------------
 
-constexpr int32_t kZeroRowExp = -2000;
-
 // Row exponents, stored biased: E + kExpBias for a row whose largest entry
 // lies in [2^E, 2^(E+1)) (E clamped below at 8S - 1076, see row_key), 0 for an
 // all-zero row.
