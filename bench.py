@@ -29,6 +29,7 @@ import hashlib
 import json
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -115,7 +116,7 @@ class Clocks:
 
     def __init__(self, device_index=0):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"symctr_clocks_{os.getpid()}.csv")
         self.dev = device_index
 
     def __enter__(self):

@@ -37,7 +37,7 @@ O5 aligned, dense deltas : Algorithm 2 with the transformations done, as
 O6 gradients             : adjoint contractions, again by the block loop.
 O7 finite differences    : central differences of a scalar loss (FP64).
 
-Readings of points the paper leaves open (also listed in the design doc):
+Readings of points the paper leaves open:
 * Q == sum_{k in C} c^U_k q_k (Alg. 2 coefficient vector c^(B) = [c^U_2; -1]
   with remainder 0); the three aligned deltas are
     delta1[F_U..., Q] : sum c^U_{F_U} q + Q         == Z_U
