@@ -156,7 +156,7 @@ SYMCTR_API symctr_status symctr_plan_query(const symctr_plan* plan, symctr_plan_
  *  stream : the copy is queued on it; the caller orders contractions on other
  *           streams after it (e.g. synchronises the stream once).
  * The caller keeps the buffer allocated and unmodified until it detaches or
- * destroys the plan.  Contractions running on another device than the
+ * destroys the plan and the contractions issued until then have completed.  Contractions running on another device than the
  * buffer's keep using the host tables.  Not to be called while a contraction
  * with this plan is being issued on another host thread.
  * Returns SYMCTR_OK (also when table_bytes is 0: nothing to copy),
