@@ -29,7 +29,7 @@
 // to the two epilogue warpgroups (setmaxnreg 56 / 224), which hold the int32
 // running sums of their 64 columns.  Optional split-K: each K range adds its
 // exact int64 partial sums into a workspace with integer atomics (order-free,
-// so the result is deterministic) and splitk_round_kernel rounds them.  Tiles
+// so the result is deterministic) and a finalize kernel rounds them.  Tiles
 // 128 x 128 (split) or 128 x 256 (TF32), 64-byte K rows (32 BF16 or 16 FP32),
 // SWIZZLE_64B, all 512 TMEM columns allocated (4 x 128 FP32 accumulators in
 // the split form).
