@@ -122,7 +122,7 @@ def test_config1_order4_z3(sc, precision):
     assert e <= TOL[precision], e
 
 
-@pytest.mark.parametrize("precision", ["fp64", "split_bf16"])
+@pytest.mark.parametrize("precision", ["fp64", "split_bf16", "tf32"])
 def test_config2_mps_transfer(sc, precision):
     E = WL.draw(WL.MPS_E, (8,))
     A = WL.draw(WL.MPS_A, (8,))
@@ -134,6 +134,25 @@ def test_config2_mps_transfer(sc, precision):
     o2 = oplan(WL.MPS_STEP2, (8,), (p1.sym_w.signs, p1.sym_w.charge, p1.sym_w.dims), spec(WL.MPS_A))
     want = O.contract_blockloop(o2, want_x, A)
     assert rel(host(E2), want) <= 2 * TOL[precision]
+
+
+def test_tf32_long_k_few_tiles_is_deterministic(sc):
+    """E' = X.A in the TF32 form (M = N = 128, K = 2048, 8 irreps: 8 tiles,
+    each accumulating all of K in TMEM): repeated calls give the same bits, and
+    the result matches the oracle at the TF32 tolerance."""
+    A = WL.draw(WL.MPS_A, (8,))
+    p1 = sc.Plan(WL.MPS_STEP1, (8,), spec(WL.MPS_E), spec(WL.MPS_A), "fp64")
+    X = torch.randn(p1.shape_w, dtype=torch.float64, generator=torch.Generator().manual_seed(77))
+    p2 = sc.Plan(WL.MPS_STEP2, (8,), p1.sym_w, spec(WL.MPS_A), "tf32")
+    assert (p2.info.M, p2.info.N, p2.info.K, p2.info.n_q) == (128, 128, 2048, 8)
+    Xd, Ad = X.cuda(), dev(A)
+    first = p2.contract(Xd, Ad)
+    again = [p2.contract(Xd, Ad) for _ in range(3)]
+    torch.cuda.synchronize()
+    p2.check_device_error()
+    assert all(torch.equal(first, a) for a in again)
+    o2 = oplan(WL.MPS_STEP2, (8,), (p1.sym_w.signs, p1.sym_w.charge, p1.sym_w.dims), spec(WL.MPS_A))
+    assert rel(host(first), O.contract_blockloop(o2, X.numpy(), A)) <= TOL["tf32"]
 
 
 @pytest.mark.parametrize("precision", ["fp64", "split_bf16", "tf32"])
