@@ -23,11 +23,20 @@ namespace {
 
 constexpr int BM = 64, BN = 64, BK = 16, THREADS = 256;
 
+// axis_offset as one out-of-line device function: every kernel below computes
+// offsets in a dozen places (per instance of the short-side row count), and
+// inlining the mixed-radix arithmetic at each of them multiplied the code size
+// and the compile time without changing the speed (none of these calls sits in
+// an innermost loop).
+__device__ __noinline__ int64_t aoff(const AxisMap& a, const GroupDesc& g, int Q, int64_t r) {
+  return axis_offset(a, g, Q, r);
+}
+
 __host__ __device__ inline bool map_rows_fast(const AxisMap& rows) {
   return rows.n > 0 && rows.bstride[rows.n - 1] == 1;
 }
 
-__global__ void __launch_bounds__(THREADS) gemm_f64_tiled(Problem p, int ksplit, bool u_rows_fast,
+__global__ void __launch_bounds__(THREADS) gemm_f64_tiled(const __grid_constant__ Problem p, int ksplit, bool u_rows_fast,
                                                           bool v_rows_fast,
                                                           const double* __restrict__ U,
                                                           const double* __restrict__ V,
@@ -51,12 +60,12 @@ __global__ void __launch_bounds__(THREADS) gemm_f64_tiled(Problem p, int ksplit,
     __syncthreads();
     if (tid < BM) {
       int64_t m = m0 + tid;
-      uoff[tid] = m < p.M ? axis_offset(p.u.rows, p.g, Q, m) : 0;
-      woffr[tid] = m < p.M ? axis_offset(p.w.rows, p.g, Q, m) : 0;
+      uoff[tid] = m < p.M ? aoff(p.u.rows, p.g, Q, m) : 0;
+      woffr[tid] = m < p.M ? aoff(p.w.rows, p.g, Q, m) : 0;
     } else if (tid < BM + BN) {
       int64_t n = n0 + tid - BM;
-      voff[tid - BM] = n < p.N ? axis_offset(p.v.rows, p.g, Q, n) : 0;
-      woffc[tid - BM] = n < p.N ? axis_offset(p.w.cols, p.g, Q, n) : 0;
+      voff[tid - BM] = n < p.N ? aoff(p.v.rows, p.g, Q, n) : 0;
+      woffc[tid - BM] = n < p.N ? aoff(p.w.cols, p.g, Q, n) : 0;
     }
     double acc[4][4];
 #pragma unroll
@@ -67,10 +76,10 @@ __global__ void __launch_bounds__(THREADS) gemm_f64_tiled(Problem p, int ksplit,
       __syncthreads();
       if (tid < BK) {
         int64_t k = k0 + tid;
-        kuoff[tid] = k < kend ? axis_offset(p.u.cols, p.g, Q, k) : 0;
+        kuoff[tid] = k < kend ? aoff(p.u.cols, p.g, Q, k) : 0;
       } else if (tid >= 32 && tid < 32 + BK) {
         int64_t k = k0 + tid - 32;
-        kvoff[tid - 32] = k < kend ? axis_offset(p.v.cols, p.g, Q, k) : 0;
+        kvoff[tid - 32] = k < kend ? aoff(p.v.cols, p.g, Q, k) : 0;
       }
       __syncthreads();
 #pragma unroll
@@ -127,9 +136,9 @@ __global__ void __launch_bounds__(THREADS) gemm_f64_tiled(Problem p, int ksplit,
 //
 // Column offsets: kappa = o * I + i, where I (the "inner" extent) is the
 // product of the fastest block dims of the column map up to kInnerMax.  The
-// offset is then axis_offset(o * I) + inner(i), inner(i) being the block part
+// offset is then aoff(o * I) + inner(i), inner(i) being the block part
 // of i alone (independent of Q); each block tabulates inner() in shared
-// memory and each lane recomputes axis_offset(o * I) only when o changes
+// memory and each lane recomputes aoff(o * I) only when o changes
 // (every I / 32 steps), instead of one mixed-radix decomposition per element.
 constexpr int SKINNY_MAX = 8;
 constexpr int kInnerMax = 2048;
@@ -161,7 +170,7 @@ __device__ void fill_inner(const AxisMap& a, int64_t I, int64_t* tab) {
 // float64 instruction of an absent row is issued: GB300's float64 pipe is
 // narrow and issues predicated-off instructions all the same).
 template <int NS>
-__global__ void __launch_bounds__(THREADS) gemm_f64_skinny(Problem p, bool long_is_u, int ksplit,
+__global__ void __launch_bounds__(THREADS) gemm_f64_skinny(const __grid_constant__ Problem p, bool long_is_u, int ksplit,
                                                            const double* __restrict__ U,
                                                            const double* __restrict__ V,
                                                            double* __restrict__ W) {
@@ -191,10 +200,10 @@ __global__ void __launch_bounds__(THREADS) gemm_f64_skinny(Problem p, bool long_
     int64_t l = t2 - b * nL;
     int Q = batch_irrep(p, (int)b);
     int64_t kbeg = ks * kchunk, kend = kbeg + kchunk < p.K ? kbeg + kchunk : p.K;
-    int64_t loff = axis_offset(Lrows, p.g, Q, l);
+    int64_t loff = aoff(Lrows, p.g, Q, l);
     int64_t soff[NS];
 #pragma unroll
-    for (int s = 0; s < NS; ++s) soff[s] = axis_offset(Srows, p.g, Q, s);
+    for (int s = 0; s < NS; ++s) soff[s] = aoff(Srows, p.g, Q, s);
     double acc[NS];
 #pragma unroll
     for (int s = 0; s < NS; ++s) acc[s] = 0.0;
@@ -206,8 +215,8 @@ __global__ void __launch_bounds__(THREADS) gemm_f64_skinny(Problem p, bool long_
       for (int64_t ob = kbeg / I; ob * I < kend; ob += 32) {
         const int64_t oj = ob + lane;
         const bool own = oj * I < kend;
-        const int64_t lo_j = own ? loff + axis_offset(Lcols, p.g, Q, oj * I) : 0;
-        const int64_t so_j = own ? axis_offset(Scols, p.g, Q, oj * I) : 0;
+        const int64_t lo_j = own ? loff + aoff(Lcols, p.g, Q, oj * I) : 0;
+        const int64_t so_j = own ? aoff(Scols, p.g, Q, oj * I) : 0;
         const int64_t left = (kend - ob * I) / I;
         const int nb = left < 32 ? (int)left : 32;
         for (int j = 0; j < nb; ++j) {
@@ -235,7 +244,7 @@ __global__ void __launch_bounds__(THREADS) gemm_f64_skinny(Problem p, bool long_
     } else {
       int64_t k = kbeg + lane;
       int64_t o = k / I, i = k - o * I;
-      int64_t lo = axis_offset(Lcols, p.g, Q, o * I), so = axis_offset(Scols, p.g, Q, o * I);
+      int64_t lo = aoff(Lcols, p.g, Q, o * I), so = aoff(Scols, p.g, Q, o * I);
       for (; k < kend; k += 32) {
         const double x = Lp[p.es * (loff + lo + tab_l[i])];
         const int64_t sc = so + tab_s[i];
@@ -247,8 +256,8 @@ __global__ void __launch_bounds__(THREADS) gemm_f64_skinny(Problem p, bool long_
           o += i / I;
           i %= I;
           if (k + 32 < kend) {
-            lo = axis_offset(Lcols, p.g, Q, o * I);
-            so = axis_offset(Scols, p.g, Q, o * I);
+            lo = aoff(Lcols, p.g, Q, o * I);
+            so = aoff(Scols, p.g, Q, o * I);
           }
         }
       }
@@ -263,7 +272,7 @@ __global__ void __launch_bounds__(THREADS) gemm_f64_skinny(Problem p, bool long_
 #pragma unroll
       for (int s = 0; s < NS; ++s) {
         int64_t m = long_is_u ? l : s, n = long_is_u ? s : l;
-        double* dst = W + p.es * (axis_offset(p.w.rows, p.g, Q, m) + axis_offset(p.w.cols, p.g, Q, n));
+        double* dst = W + p.es * (aoff(p.w.rows, p.g, Q, m) + aoff(p.w.cols, p.g, Q, n));
         if (ksplit > 1) atomicAdd(dst, signed_result(p, acc[s]));
         else store_w(p, dst, acc[s]);
       }
@@ -277,7 +286,7 @@ __global__ void __launch_bounds__(THREADS) gemm_f64_skinny(Problem p, bool long_
 // depend only on the irrep, so a block stages them in shared memory when the
 // irrep changes.  Row offsets in L and W use the inner-block split of the
 // skinny kernel above (l = o * I + i): a table of inner(i) per map, and
-// axis_offset(o * I) for the inner blocks of a chunk computed by as many
+// aoff(o * I) for the inner blocks of a chunk computed by as many
 // threads at once (the index arithmetic of one offset is a long dependent
 // chain under a product group, so it is never left to a single thread).
 constexpr int kShortK = 32;
@@ -285,7 +294,7 @@ constexpr int kShortRows = 4096;
 constexpr int kShortSlots = kShortRows / 32 + 2;
 
 template <int NS>
-__global__ void __launch_bounds__(THREADS) gemm_f64_shortk(Problem p, bool long_is_u,
+__global__ void __launch_bounds__(THREADS) gemm_f64_shortk(const __grid_constant__ Problem p, bool long_is_u,
                                                            const double* __restrict__ U,
                                                            const double* __restrict__ V,
                                                            double* __restrict__ W) {
@@ -324,17 +333,17 @@ __global__ void __launch_bounds__(THREADS) gemm_f64_shortk(Problem p, bool long_
     if (b != staged) {
       for (int i = threadIdx.x; i < nS * K; i += THREADS) {
         const int sr = i / K, k = i - sr * K;
-        sval[sr][k] = Sp[p.es * (axis_offset(Srows, p.g, Q, sr) + axis_offset(Scols, p.g, Q, k))];
+        sval[sr][k] = Sp[p.es * (aoff(Srows, p.g, Q, sr) + aoff(Scols, p.g, Q, k))];
       }
-      for (int k = threadIdx.x; k < K; k += THREADS) lco[k] = axis_offset(Lcols, p.g, Q, k);
-      for (int sr = threadIdx.x; sr < nS; sr += THREADS) wso[sr] = axis_offset(Ws, p.g, Q, sr);
+      for (int k = threadIdx.x; k < K; k += THREADS) lco[k] = aoff(Lcols, p.g, Q, k);
+      for (int sr = threadIdx.x; sr < nS; sr += THREADS) wso[sr] = aoff(Ws, p.g, Q, sr);
       staged = b;
     }
     if (tabulated) {
       const int64_t n_o = (lend - 1) / I - o0 + 1;
       for (int64_t j = threadIdx.x; j < n_o; j += THREADS) {
-        ob_l[j] = axis_offset(Lrows, p.g, Q, (o0 + j) * I);
-        ob_w[j] = axis_offset(Wl, p.g, Q, (o0 + j) * I);
+        ob_l[j] = aoff(Lrows, p.g, Q, (o0 + j) * I);
+        ob_w[j] = aoff(Wl, p.g, Q, (o0 + j) * I);
       }
     }
     __syncthreads();
@@ -354,8 +363,8 @@ __global__ void __launch_bounds__(THREADS) gemm_f64_shortk(Problem p, bool long_
           ++o;
         }
       } else {
-        loff = axis_offset(Lrows, p.g, Q, l);
-        woff = axis_offset(Wl, p.g, Q, l);
+        loff = aoff(Lrows, p.g, Q, l);
+        woff = aoff(Wl, p.g, Q, l);
       }
       double acc[NS];
 #pragma unroll
@@ -380,7 +389,7 @@ int sm_count() {
 }
 
 // Zero the entries of W that a split-K launch accumulates into.
-__global__ void zero_w_entries(Problem p, double* __restrict__ W) {
+__global__ void zero_w_entries(const __grid_constant__ Problem p, double* __restrict__ W) {
   int64_t total = (int64_t)p.n_q * p.M * p.N;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -388,7 +397,7 @@ __global__ void zero_w_entries(Problem p, double* __restrict__ W) {
     int64_t r = i - b * p.M * p.N;
     int64_t m = r / p.N, n = r % p.N;
     int Q = batch_irrep(p, (int)b);
-    W[p.es * (axis_offset(p.w.rows, p.g, Q, m) + axis_offset(p.w.cols, p.g, Q, n))] = 0.0;
+    W[p.es * (aoff(p.w.rows, p.g, Q, m) + aoff(p.w.cols, p.g, Q, n))] = 0.0;
   }
 }
 
