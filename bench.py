@@ -1,19 +1,22 @@
 """Benchmark: useful TFLOP/s of the irrep-aligned contraction, split-BF16 vs FP64.
 
-Workload (default): the MPS transfer step under Z_8 symmetry,
-  E'[g,d] = sum_{a,b,s} E[a,b] A[a,s,g] A[b,s,d],
-evaluated as two irrep-aligned contractions X = einsum('ab,asg->bsg', E, A) and
-E' = einsum('bsg,bsd->gd', X, A), with bond dimension 8 sectors x 128 and
-physical dimension 8 sectors x 2 (seeded synthetic N(0,1) reduced forms).
-One step = both contractions, standard reduced forms in and out.
+Workload (default): the coupled-cluster particle-particle ladder under Z_8
+symmetry, w[a,b,i,j] = sum_{c,d} v[a,b,c,d] t[c,d,i,j], virtual modes 8
+sectors x 32, occupied modes 8 sectors x 8 (seeded synthetic reduced forms:
+v ~ N(0,1)/16, 4.3 GB; t ~ N(0,1)*1e-2): one aligned GEMM batch of 8 irreps
+with M = K = 8192, N = 512 (549.8 GFLOP of symmetry-reduced work).  One step =
+the whole contraction, standard reduced forms in and out.
+--workload mps: the MPS transfer step under Z_8, E'[g,d] = sum E[a,b] A[a,s,g]
+A[b,s,d], as two aligned contractions X = einsum('ab,asg->bsg', E, A) and
+E' = einsum('bsg,bsd->gd', X, A) (bond 8 sectors x 128, physical 8 x 2).
 
 Metric: useful TFLOP/s = symmetry-reduced GEMM flops (2 * n_Q * M * N * K per
-contraction) / device time of the step.  The split-BF16 form is the headline
-value; the FP64 form and the relative errors of both against the CPU float64
-oracle are reported beside it.
+contraction) / device time of the step (median over the timed steps).  The
+split-BF16 form is the headline value; the FP64 form and the relative errors
+of both against the CPU float64 oracle are reported beside it.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                       [--workload mps|cc_ladder] [--precision split_bf16|fp64|tf32]
+                       [--workload cc_ladder|mps|...] [--precision split_bf16|fp64|tf32]
 Multi-GPU (torchrun): replicas only; each rank runs the whole workload.
 """
 from __future__ import annotations
@@ -68,7 +71,8 @@ def cc_contraction(args):
 def cc_workload(args):
     c = cc_contraction(args)
     g = c.moduli[0]
-    name = f"cc_ladder_Z{g}_virt{g}x{c.u.dims[0]}_occ{g}x{c.u.dims[-1]} (w=v.t)"
+    # v[a,b,c,d] has four virtual modes; t[c,d,i,j] ends with the occupied ones
+    name = f"cc_ladder_Z{g}_virt{g}x{c.u.dims[0]}_occ{g}x{c.v.dims[-1]} (w=v.t)"
     return name, WL.draw(c.u, c.moduli), WL.draw(c.v, c.moduli)
 
 
@@ -125,7 +129,7 @@ class Clocks:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}",
                                           f"--query-gpu={self.FIELDS}", "--format=csv,noheader",
-                                          "-lms", "100"], stdout=self.fh,
+                                          "-lms", "50"], stdout=self.fh,
                                          stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -353,7 +357,8 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
     for pl in plans:
         pl.check_device_error()
-    ms = max_over_ranks(statistics.mean(times), world, dev)
+    ms = max_over_ranks(statistics.median(times), world, dev)
+    ms_mean = max_over_ranks(statistics.mean(times), world, dev)
     value = replicas_value(flops, ms, world)
 
     # per-kernel phases (averaged over profiled steps outside the timed region)
@@ -377,7 +382,7 @@ def run_ours(args, rank, world):
     if args.precision != "fp64" and not args.no_fp64:
         plans64, step64, _ = make("fp64")
         t64, _ = timed(step64, max(2, min(args.steps, 5)), 1)
-        ms64 = statistics.mean(t64)
+        ms64 = statistics.median(t64)
         fp64 = {"value": round(world * flops / (ms64 * 1e-3) / 1e12, 4), "ms_per_step": round(ms64, 4)}
         if rank == 0:
             got = step64().cpu().numpy()
@@ -394,7 +399,7 @@ def run_ours(args, rank, world):
         o = step(*dins)
         hout.copy_(o, non_blocking=True)
     t_e2e, _ = timed(e2e_step, args.steps, args.warmup)
-    ms_e2e = max_over_ranks(statistics.mean(t_e2e), world, dev)
+    ms_e2e = max_over_ranks(statistics.median(t_e2e), world, dev)
 
     pk = peaks()
     roofs = rooflines(args, plans, prep, gemm, pk)
@@ -409,6 +414,8 @@ def run_ours(args, rank, world):
         "steps": args.steps,
         "warmup": args.warmup,
         "ms_per_step": round(ms, 4),
+        "ms_per_step_mean": round(ms_mean, 4),
+        "timing": "median over the timed steps (CUDA events on the launching stream)",
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
@@ -705,19 +712,29 @@ def run_small(args, rank, world):
 
 
 def run_reference(args, rank, world):
-    """The oracle on the host cores, on the same workload and metric."""
+    """The oracle on the host cores, on the same workload and metric: the
+    block loop (Algorithm 1 generalised) of the whole step, one full step per
+    timed step (about 1.5 s for the CC ladder on 16 cores, 10 ms for the MPS
+    step)."""
     if rank != 0:
         return None
+    import oracle as O
     if args.workload == "mps":
         name, a, b = mps_workload()
         g = WL.MPS_G
-        import oracle as O
         p1 = O.plan(WL.MPS_STEP1, O.Group((g,)), O.Sym(*spec(WL.MPS_E)), O.Sym(*spec(WL.MPS_A)))
         p2 = O.plan(WL.MPS_STEP2, O.Group((g,)), p1.sym_w, O.Sym(*spec(WL.MPS_A)))
-        flops = 2.0 * sum(len(O.q_set(p)) * np.prod(O.aligned_dims(p)[1:]) for p in (p1, p2))
+        plans = (p1, p2)
+        c = None
+    elif args.workload == "cc_ladder":
+        name, a, b = cc_workload(args)
+        c = cc_contraction(args)
+        plans = (O.plan(c.einsum, O.Group(c.moduli), O.Sym(*spec(c.u)), O.Sym(*spec(c.v))),)
     else:
-        raise SystemExit("reference arm: mps workload only")
-    run = oracle_step(args.workload, a, b)
+        return {"impl": "reference", "unavailable": f"reference arm times the cc_ladder and mps "
+                                                    f"workloads only (asked: {args.workload})"}
+    flops = 2.0 * sum(len(O.q_set(p)) * np.prod(O.aligned_dims(p)[1:]) for p in plans)
+    run = oracle_step(args.workload, a, b, c=c)
     for _ in range(args.warmup):
         run()
     ts = []
@@ -725,7 +742,7 @@ def run_reference(args, rank, world):
         t0 = time.perf_counter()
         run()
         ts.append(time.perf_counter() - t0)
-    ms = statistics.mean(ts) * 1e3
+    ms = statistics.median(ts) * 1e3
     value = flops / (ms * 1e-3) / 1e12
     return {
         "impl": "reference",
@@ -735,7 +752,7 @@ def run_reference(args, rank, world):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": name, "precision": "fp64 (CPU oracle, block loop)"},
         "cpu_baseline": {"value": round(value, 6), "unit": "TFLOP/s", "cores": _CORES,
-                         "kind": "oracle", "sample": "whole step per timed step"},
+                         "kind": "oracle", "sample": "one whole step per timed step, median"},
         "e2e": {"value": round(value, 6), "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -747,8 +764,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["mps", "cc_ladder", "sweep", "table", "z3", "peps"],
-                    default="mps")
+    ap.add_argument("--workload", choices=["cc_ladder", "mps", "sweep", "table", "z3", "peps"],
+                    default="cc_ladder")
     ap.add_argument("--case", default="CC1_a", help="table: a Table-2 case (" + ", ".join(WL.TABLE2) + ")")
     ap.add_argument("--sweep-g", type=int, default=16, help="G of the sweep workload (config 5)")
     ap.add_argument("--sweep-dims", default="512,128",

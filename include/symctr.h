@@ -120,6 +120,11 @@ typedef struct {
                                    one pass per group of irreps that fits (Q-streaming) */
   uint64_t table_bytes;         /* device buffer symctr_plan_attach_tables takes (0: the
                                    plan has no offset tables, e.g. the float64 form) */
+  int32_t tensor_core;          /* 1: the GEMM of the precision form runs on tcgen05;
+                                   0: it runs on the float64 CUDA-core kernels (the float64
+                                   form, or an aligned GEMM below 32 x 32 x 16 in M x N x K,
+                                   e.g. a GEMV, where the tensor-core forms would gain
+                                   nothing; the result is then exact to float64 rounding) */
 } symctr_plan_info;
 
 /* Build a plan for W = einsum(spec, U, V).
@@ -203,14 +208,18 @@ SYMCTR_API symctr_status symctr_contract_complex(const symctr_plan* plan, int co
  * allocate device memory (they are handed only their input and output buffers,
  * or run where no allocator may be called).  The paper has no counterpart: this
  * is a deployment convenience.  The scratch is one static device array of
- * 64 MiB that every GPU loading this code holds until exit; plans whose
- * workspace_bytes exceed it get SYMCTR_ERR_WORKSPACE.  All calls share that
- * array: calls that overlap on the GPU race (use one stream).  The first call on
- * a device looks up the array's address (cudaGetSymbolAddress, device current)
- * and should come before any stream capture.  Device-side failures are recorded
- * in the array and not reported; no memory is allocated or freed (the first
- * contraction of a plan, through either entry point, page-locks the plan's own
- * host offset tables). */
+ * 64 MiB that every GPU loading this code holds until exit.  Plans whose
+ * workspace_bytes_min exceeds it get SYMCTR_ERR_WORKSPACE; plans whose
+ * workspace_bytes exceeds it but whose workspace_bytes_min fits run in several
+ * passes over the irreps Q.  All calls share that array: calls that overlap on
+ * the GPU race (use one stream).  The first call on a device looks up the
+ * array's address (cudaGetSymbolAddress, device current) and should come
+ * before any stream capture; that cached address does not survive
+ * cudaDeviceReset or a switch to another context on the device.  Device-side
+ * failures are recorded in the array's first word: symctr_check_device_error
+ * with a NULL workspace reads and clears it.  No memory is allocated or freed
+ * (the first contraction of a plan, through either entry point, page-locks the
+ * plan's own host offset tables). */
 SYMCTR_API symctr_status symctr_contract_static_scratch(const symctr_plan* plan,
                                                         const double* u_red, const double* v_red,
                                                         double* w_red, void* stream);
@@ -227,6 +236,8 @@ SYMCTR_API symctr_status symctr_contract_backward(const symctr_plan* plan, const
                                        void* workspace, size_t workspace_bytes, void* stream);
 
 /* Synchronise `stream`, read the device error word from `workspace` and clear it.
+ * workspace = NULL reads the word of symctr_contract_static_scratch's static
+ * array on the current device.
  * Returns SYMCTR_OK, SYMCTR_ERR_DEVICE_TIMEOUT, SYMCTR_ERR_NONFINITE or SYMCTR_ERR_CUDA. */
 SYMCTR_API symctr_status symctr_check_device_error(const symctr_plan* plan, void* workspace, void* stream);
 
@@ -262,8 +273,9 @@ SYMCTR_API const char* symctr_status_string(symctr_status status);
 SYMCTR_API const char* symctr_last_error_detail(void);
 
 /* Release a plan (NULL is ignored).  If its offset tables were page-locked,
- * this first waits for all work on the current device (cudaDeviceSynchronize),
- * since copies from them may still be queued. */
+ * this first waits, on each stream that used them, for the last contraction
+ * (or table attachment) that read them; no other work is waited for.  A plan
+ * must not be destroyed while another host thread is issuing calls with it. */
 SYMCTR_API void symctr_plan_destroy(symctr_plan* plan);
 
 #ifdef __cplusplus

@@ -72,7 +72,7 @@ __all__ = [
     "expand", "restrict", "contract_dense_einsum", "contract_dense_loops",
     "contract_blockloop", "contract_element", "contract_element_lazy", "align_u", "align_v",
     "mapback_w", "align_w", "q_set", "contract_aligned", "delta", "grad_u", "grad_v",
-    "central_difference", "count_stored_blocks", "aligned_dims",
+    "central_difference", "count_stored_blocks", "aligned_dims", "aligned_index",
 ]
 
 
@@ -609,6 +609,81 @@ def contract_aligned(p: Plan, u_red, v_red) -> np.ndarray:
     vh = align_v(p, v_red)
     wh = np.matmul(uh, np.transpose(vh, (0, 2, 1)))
     return mapback_w(p, wh)
+
+
+# ---------------------------------------------------------------------------
+# O5b: the reduced-form position of single aligned entries (the App. A.4
+# layouts of Alg. 2's aligned forms, evaluated entry by entry), for checks
+# that sample a few rows and columns of an aligned problem too large to form
+# ---------------------------------------------------------------------------
+
+def _comps_arr(group: Group, q):
+    """Components of (arrays of) flattened labels, first modulus first."""
+    q = np.asarray(q, dtype=np.int64)
+    out = []
+    for m in reversed(group.moduli):
+        out.append(q % m)
+        q = q // m
+    return list(reversed(out))
+
+
+def _label_arr(group: Group, comps):
+    q = np.zeros(np.broadcast(*comps).shape if len(comps) > 1 else np.shape(comps[0]), dtype=np.int64)
+    for c, m in zip(comps, group.moduli):
+        q = q * m + np.mod(c, m)
+    return q
+
+
+def _group_digits(p: Plan, labels: List[str], coeffs: List[int], target, r):
+    """Sector and block digits of aligned index r over the modes `labels`
+    (sector digits of all but the last mode, then every block digit, C
+    order); the last mode's sector solves sum coeffs * q == target, where
+    target is a list of component arrays.  Returns ({label: sector},
+    {label: block})."""
+    G = p.group
+    n = len(labels)
+    if n == 0:
+        return {}, {}
+    shape = [G.order] * (n - 1) + [p.dim(c) for c in labels]
+    digits = np.unravel_index(np.asarray(r, dtype=np.int64), shape)
+    sec = {c: digits[i] for i, c in enumerate(labels[:-1])}
+    blk = {c: digits[n - 1 + i] for i, c in enumerate(labels)}
+    rest = [0] * len(G.moduli)
+    for c, k in zip(labels[:-1], coeffs[:-1]):
+        for j, x in enumerate(_comps_arr(G, sec[c])):
+            rest[j] = rest[j] + k * x
+    last = coeffs[-1]   # +-1: its own inverse
+    sec[labels[-1]] = _label_arr(G, [last * (t - x) for t, x in zip(target, rest)])
+    return sec, blk
+
+
+def aligned_index(p: Plan, operand: int, Q: int, r, c) -> Tuple[np.ndarray, ...]:
+    """Reduced-form index of U_hat[Q, r, c] (operand 0: r = m over the free
+    modes of U, c = kappa over the contracted ones), V_hat[Q, r, c] (1: r = n
+    over the free modes of V, c = kappa) or W_hat[Q, r, c] (2: r = m, c = n),
+    as a tuple of integer arrays broadcast over r and c.  The implicit
+    sectors follow Alg. 2's three deltas: sum c^U_{F_U} q + Q == Z_U,
+    sum c^U_C q == Q, sum c^V_{F_V} q + sigma Q == Z_V."""
+    G = p.group
+    cu = dict(zip(p.lu, p.sym_u.signs))
+    cv = dict(zip(p.lv, p.sym_v.signs))
+    qc = _comps_arr(G, Q)
+    zu = [np.int64(z) for z in G.norm(p.sym_u.charge)]
+    zv = [np.int64(z) for z in G.norm(p.sym_v.charge)]
+    t_fu = [a - b for a, b in zip(zu, qc)]
+    t_c = qc
+    t_fv = [a - p.sigma * b for a, b in zip(zv, qc)]
+    groups = {0: ((p.FU, [cu[x] for x in p.FU], t_fu), (p.C, [cu[x] for x in p.C], t_c), p.lu),
+              1: ((p.FV, [cv[x] for x in p.FV], t_fv), (p.C, [cu[x] for x in p.C], t_c), p.lv),
+              2: ((p.FU, [cu[x] for x in p.FU], t_fu), (p.FV, [cv[x] for x in p.FV], t_fv), p.lw)}
+    (rl, rk, rt), (cl, ck, ct), labels = groups[operand]
+    r, c = np.broadcast_arrays(np.asarray(r, dtype=np.int64), np.asarray(c, dtype=np.int64))
+    sec, blk = _group_digits(p, rl, rk, rt, r)
+    s2, b2 = _group_digits(p, cl, ck, ct, c)
+    sec.update(s2)
+    blk.update(b2)
+    full = np.zeros(r.shape, dtype=np.int64)
+    return tuple(full + sec[x] for x in labels[:-1]) + tuple(full + blk[x] for x in labels)
 
 
 # ---------------------------------------------------------------------------

@@ -62,6 +62,7 @@ class PlanInfo(ctypes.Structure):
         ("useful_flops", ctypes.c_double), ("transform_bytes", ctypes.c_double),
         ("workspace_bytes", ctypes.c_uint64), ("workspace_bytes_backward", ctypes.c_uint64),
         ("workspace_bytes_min", ctypes.c_uint64), ("table_bytes", ctypes.c_uint64),
+        ("tensor_core", ctypes.c_int32),
     ]
 
 
@@ -194,17 +195,39 @@ class Plan:
         self._tables = None
         self._tables_ready = info.table_bytes == 0
         self._lock = threading.Lock()
+        # streams (other than the allocating one) on which the plan's device
+        # buffers were used: the caching allocator waits for their work before
+        # it reuses the memory of a freed buffer (Tensor.record_stream)
+        self._seen = set()
 
     def __del__(self):
         try:
             if getattr(self, "_h", None) is not None and _LIB is not None:
-                if getattr(self, "_tables", None) is not None:
-                    # kernels issued on any stream may still read the tables
-                    torch.cuda.synchronize(self._tables.device)
+                # the device buffers (tables, workspace) are torch tensors whose
+                # uses on other streams were recorded; nothing to wait for here
                 _LIB.symctr_plan_destroy(self._h)
                 self._h = None
         except Exception:
             pass
+
+    def _used_on(self, stream, *bufs):
+        """Record that `bufs` (the plan's own buffers) are used on `stream`."""
+        key = stream.cuda_stream
+        if key in self._seen:
+            return
+        for b in bufs:
+            if b is not None:
+                b.record_stream(stream)
+        self._seen.add(key)
+
+    @staticmethod
+    def _same_device(*ts):
+        """All tensors on the current CUDA device (the library launches there)."""
+        dev = torch.cuda.current_device()
+        for t in ts:
+            if t is not None and t.get_device() != dev:
+                raise ValueError(f"tensor on cuda:{t.get_device()} but the current device is "
+                                 f"cuda:{dev}; use torch.cuda.device(...) around the call")
 
     # -- device tables -------------------------------------------------------
     def attach_tables(self, device=None):
@@ -223,6 +246,7 @@ class Plan:
                     s.synchronize()
                 self._tables = buf
                 self._tables_ready = True
+                self._seen = set()
 
     # -- workspace -----------------------------------------------------------
     def workspace(self, backward: bool = False, device=None) -> torch.Tensor:
@@ -230,6 +254,7 @@ class Plan:
                    if backward else 0, 256)
         if self._ws is None or self._ws.numel() < need:
             self._ws = torch.empty(need, dtype=torch.uint8, device=device or "cuda")
+            self._seen = set()   # the new buffer's streams are recorded afresh
         return self._ws
 
     # -- checks --------------------------------------------------------------
@@ -257,11 +282,15 @@ class Plan:
             out = torch.empty(self.shape_w, dtype=torch.float64, device=u.device)
         elif not self._ok64(out, self._size_w):
             self._dev64(out, self.shape_w, "out")
+        self._same_device(u, v, out, workspace)
         if not self._tables_ready:
             self.attach_tables(u.device)
         ws = workspace if workspace is not None else self.workspace(device=u.device)
+        cs = torch.cuda.current_stream()
+        if cs.cuda_stream not in self._seen:
+            self._used_on(cs, self._tables, self._ws)
         _check(_LIB.symctr_contract(self._h, u.data_ptr(), v.data_ptr(), out.data_ptr(), ws.data_ptr(),
-                                    ws.numel(), torch.cuda.current_stream().cuda_stream))
+                                    ws.numel(), cs.cuda_stream))
         return out
 
     def contract_complex(self, u: torch.Tensor, v: torch.Tensor, out: Optional[torch.Tensor] = None,
@@ -278,9 +307,11 @@ class Plan:
             out = torch.empty(self.shape_w, dtype=torch.complex128, device=u.device)
         if out.dtype != torch.complex128 or tuple(out.shape) != tuple(self.shape_w) or not out.is_contiguous():
             raise ValueError("out must be a contiguous complex128 tensor of the output shape")
+        self._same_device(u, v, out, workspace)
         if not self._tables_ready:
             self.attach_tables(u.device)
         ws = workspace if workspace is not None else self.workspace(device=u.device)
+        self._used_on(torch.cuda.current_stream(), self._tables, self._ws)
         _check(load().symctr_contract_complex(self._h, int(conj_u), int(conj_v), _ptr(u), _ptr(v),
                                               _ptr(out), _ptr(ws), ws.numel(), _stream()))
         return out
@@ -297,21 +328,33 @@ class Plan:
         if out is None:
             out = torch.empty(self.shape_w, dtype=torch.float64, device=u.device)
         self._dev64(out, self.shape_w, "out")
+        # the library picks the static array of the current device: every
+        # tensor must live there
+        self._same_device(u, v, out)
         # no table buffer is attached here (that would allocate device memory);
         # tables attached by an earlier contract() are used
+        if self._tables is not None:
+            self._used_on(torch.cuda.current_stream(), self._tables)
         _check(load().symctr_contract_static_scratch(self._h, _ptr(u), _ptr(v), _ptr(out),
                                                      _stream()))
         return out
+
+    def check_static_scratch_error(self):
+        """Read and clear the device error word of contract_static_scratch's static
+        array on the current device (synchronises the current stream)."""
+        _check(load().symctr_check_device_error(self._h, None, _stream()))
 
     def backward(self, grad_w: torch.Tensor, u: torch.Tensor, v: torch.Tensor,
                  need_u: bool = True, need_v: bool = True,
                  workspace: Optional[torch.Tensor] = None):
         self._dev64(grad_w, self.shape_w, "grad_w")
+        self._same_device(grad_w, u, v, workspace)
         gu = torch.empty(self.shape_u, dtype=torch.float64, device=u.device) if need_u else None
         gv = torch.empty(self.shape_v, dtype=torch.float64, device=u.device) if need_v else None
         if not self._tables_ready:
             self.attach_tables(u.device)
         ws = workspace if workspace is not None else self.workspace(True, u.device)
+        self._used_on(torch.cuda.current_stream(), self._tables, self._ws)
         _check(load().symctr_contract_backward(self._h, _ptr(grad_w), _ptr(u), _ptr(v), _ptr(gu),
                                                _ptr(gv), _ptr(ws), ws.numel(), _stream()))
         return gu, gv
@@ -323,6 +366,7 @@ class Plan:
         al = [(i.n_q, i.M, i.K), (i.n_q, i.N, i.K), (i.n_q, i.M, i.N)][operand]
         src_shape, dst_shape = (red, al) if direction > 0 else (al, red)
         self._dev64(src, src_shape, "src")
+        self._same_device(src)
         dst = torch.empty(dst_shape, dtype=torch.float64, device=src.device)
         _check(load().symctr_align(self._h, operand, direction, _ptr(src), _ptr(dst), _stream()))
         return dst

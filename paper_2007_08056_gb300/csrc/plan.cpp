@@ -147,6 +147,15 @@ struct symctr_plan {
   mutable std::once_flag pin_once;
   mutable bool pinned = false;
   mutable const int64_t* dtab = nullptr;   // device view of the page-locked tables
+  // the last contraction that read the page-locked tables, per (device,
+  // stream): destroying the plan waits for these events only
+  struct Use {
+    int dev;
+    cudaStream_t st;
+    cudaEvent_t ev;
+  };
+  mutable std::mutex use_mu;
+  mutable std::vector<Use> uses;
   // caller-owned device copy of htab (symctr_plan_attach_tables) and its device
   const int64_t* dev_tab = nullptr;
   int dev_tab_device = -1;
@@ -471,6 +480,25 @@ symctr_status cuda_status(cudaError_t e, const char* where) {
   return fail(SYMCTR_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
+// Kernels and copies queued on `st` read the plan's page-locked tables: record
+// the point after which the plan may release them (one event per device and
+// stream, re-recorded by every such call).
+symctr_status mark_table_use(const symctr_plan* P, cudaStream_t st) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_status(e, "current device");
+  std::lock_guard<std::mutex> lock(P->use_mu);
+  cudaEvent_t ev = nullptr;
+  for (const auto& u : P->uses)
+    if (u.dev == dev && u.st == st) ev = u.ev;
+  if (!ev) {
+    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_status(e, "table-use event");
+    P->uses.push_back({dev, st, ev});
+  }
+  return cuda_status(cudaEventRecord(ev, st), "table-use event");
+}
+
 // How one real contraction reads and writes: element stride (2 when the
 // pointers address the real or imaginary parts of interleaved complex data),
 // output mode W = (-)R or W += (-)R, whether the workspace's error word
@@ -630,6 +658,7 @@ symctr_status run_contract_body(const symctr_plan* P, const double* u, const dou
     if (e != cudaSuccess) return cuda_status(e, split ? "gemm_split" : "gemm_tf32");
   }
   if (P->prof) cudaEventRecord(P->ev[2], st);
+  if (!attached && P->pinned) return mark_table_use(P, st);
   return SYMCTR_OK;
 }
 
@@ -644,6 +673,8 @@ symctr_status contract_into_workspace(const symctr_plan* P, const double* u, con
 }
 
 uint64_t plan_workspace_bytes(const symctr_plan* P) { return P ? P->ws_bytes : 0; }
+
+uint64_t plan_workspace_bytes_min(const symctr_plan* P) { return P ? P->ws_bytes_min : 0; }
 
 symctr_status record_error(symctr_status st, const char* detail) { return fail(st, detail); }
 
@@ -668,6 +699,10 @@ static symctr_status attach_tables(symctr_plan* P, uint8_t* buf, int dev, cudaSt
     cudaError_t e = cudaMemcpyAsync(buf, P->htab.data(), P->htab.size() * sizeof(int64_t),
                                     cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_status(e, "attach offset tables");
+    if (P->pinned) {
+      symctr_status r = mark_table_use(P, st);
+      if (r != SYMCTR_OK) return r;
+    }
     P->dev_tab = (const int64_t*)buf;
     P->dev_tab_device = dev;
   }
@@ -731,6 +766,7 @@ symctr_status symctr_plan_query(const symctr_plan* P, symctr_plan_info* o) {
   if (P->bwd_v && P->bwd_v->ws_bytes > wb) wb = P->bwd_v->ws_bytes;
   o->workspace_bytes_backward = wb;
   o->table_bytes = all_table_bytes(P);
+  o->tensor_core = P->tensor_core ? 1 : 0;
   return SYMCTR_OK;
 }
 
@@ -827,7 +863,12 @@ symctr_status symctr_contract_complex(const symctr_plan* P, int conj_u, int conj
 
 symctr_status symctr_check_device_error(const symctr_plan* P, void* ws, void* stream) {
   (void)P;
-  if (!ws) return fail(SYMCTR_ERR_NULLPTR, "NULL workspace");
+  if (!ws) {
+    // the static scratch array of symctr_contract_static_scratch on this device
+    symctr_status st = SYMCTR_OK;
+    ws = static_scratch_address(&st);
+    if (!ws) return st;
+  }
   cudaStream_t st = (cudaStream_t)stream;
   unsigned h = 0;
   cudaError_t e = cudaMemcpyAsync(&h, ws, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
@@ -902,9 +943,15 @@ void symctr_plan_destroy(symctr_plan* P) {
   if (!P) return;
   symctr_profile_enable(P, 0);
   if (P->pinned) {
-    // copies of the page-locked tables may still be queued on some stream
-    cudaDeviceSynchronize();
+    // wait for the last contraction that read the page-locked tables on each
+    // stream that used them (nothing else on the device is waited for)
+    for (const auto& u : P->uses) {
+      cudaEventSynchronize(u.ev);
+      cudaEventDestroy(u.ev);
+    }
+    P->uses.clear();
     cudaHostUnregister((void*)P->htab.data());
+    cudaGetLastError();
   }
   symctr_plan_destroy(P->bwd_u);
   symctr_plan_destroy(P->bwd_v);

@@ -231,7 +231,11 @@ inline int split_k_ranges(const Problem& p, int64_t kpad) {
 symctr_status contract_into_workspace(const symctr_plan* P, const double* u, const double* v,
                                       double* w, void* ws, size_t ws_bytes, cudaStream_t st);
 uint64_t plan_workspace_bytes(const symctr_plan* P);
+uint64_t plan_workspace_bytes_min(const symctr_plan* P);
 symctr_status record_error(symctr_status st, const char* detail);
+// Device address of the static scratch array on the current device (looked
+// up once per device, defined in static_scratch.cu), or NULL with *st set.
+void* static_scratch_address(symctr_status* st);
 
 // Shape test: the tensor-core forms need a GEMM-shaped problem.
 inline bool tensor_core_shape(const Problem& p) { return p.M >= 32 && p.N >= 32 && p.K >= 16; }

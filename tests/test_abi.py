@@ -152,3 +152,32 @@ def test_attach_tables_argument_checks():
     p64 = sc.Plan(WL.MPS_STEP1, (8,), spec(WL.MPS_E), spec(WL.MPS_A), "fp64")
     assert p64.info.table_bytes == 0
     assert lib.symctr_plan_attach_tables(p64._h, ctypes.c_void_p(4096), 0, None) == 0
+
+
+def test_engine_of_each_form_is_reported():
+    """plan.info.tensor_core: the tensor-core forms run on tcgen05 for
+    GEMM-shaped problems; GEMV shapes and the float64 form use the float64
+    CUDA-core kernels."""
+    c = WL.CC_LADDER
+    spec = lambda t: (t.signs, t.charge, t.dims)
+    for prec, want in (("split_bf16", 1), ("tf32", 1), ("fp64", 0)):
+        assert sc.Plan(c.einsum, c.moduli, spec(c.u), spec(c.v), prec).info.tensor_core == want
+    peps = sc.Plan(WL.PEPS_Y, WL.PEPS_MODULI, spec(WL.PEPS_T), spec(WL.PEPS_ENV), "split_bf16")
+    assert peps.info.M == 2 and peps.info.tensor_core == 0
+
+
+class _FakeTensor:
+    def __init__(self, dev):
+        self.dev = dev
+
+    def get_device(self):
+        return self.dev
+
+
+def test_tensors_on_another_device_are_rejected(monkeypatch):
+    """The library launches on the current device; a tensor elsewhere is
+    refused before anything is launched (checked without a GPU)."""
+    monkeypatch.setattr(sc.torch.cuda, "current_device", lambda: 0)
+    sc.Plan._same_device(_FakeTensor(0), None, _FakeTensor(0))
+    with pytest.raises(ValueError):
+        sc.Plan._same_device(_FakeTensor(0), _FakeTensor(1))

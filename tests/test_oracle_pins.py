@@ -367,6 +367,33 @@ def test_alignment_is_a_permutation(case):
     assert np.array_equal(O.mapback_w(p, O.align_w(p, w)), w)
 
 
+@pytest.mark.parametrize("s,t,v", [(1, 1, 1), (2, 1, 2), (2, 2, 2), (0, 2, 1), (1, 0, 2),
+                                   (2, 1, 0), (3, 1, 1), (1, 3, 1)])
+def test_aligned_index_matches_dense_delta_route(s, t, v):
+    """Entry-by-entry positions of the aligned forms (aligned_index) against
+    the dense generalized-Kronecker-delta route of Alg. 2 (align_u, align_v,
+    mapback_w): every entry of U_hat, V_hat and W_hat, over every Q of the
+    Q set, with shuffled mode orders, random charges, sigma = +-1 and a
+    product group."""
+    rng = np.random.default_rng(500 + 100 * s + 10 * t + v)
+    for G, sigma, moduli in [(3, -1, None), (4, 1, None), (6, -1, (2, 3))]:
+        if G ** (s + t + v) > 3000:
+            continue
+        p, u, vv = random_case(s, t, v, G, rng, sigma, moduli)
+        Gn, M, N, K = O.aligned_dims(p)
+        uh, vh = O.align_u(p, u), O.align_v(p, vv)
+        wh = rng.standard_normal((Gn, M, N))
+        w = O.mapback_w(p, wh)
+        for Q in O.q_set(p):
+            m, n, k = np.arange(M)[:, None], np.arange(N)[:, None], np.arange(K)[None, :]
+            if p.lu:
+                assert np.array_equal(u[O.aligned_index(p, 0, Q, m, k)], uh[Q])
+            if p.lv:
+                assert np.array_equal(vv[O.aligned_index(p, 1, Q, n, k)], vh[Q])
+            if p.lw:
+                assert np.array_equal(w[O.aligned_index(p, 2, Q, m, np.arange(N)[None, :])], wh[Q])
+
+
 # --------------------------------------------------------------------------
 # gradients
 # --------------------------------------------------------------------------
