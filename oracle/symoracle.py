@@ -8,13 +8,25 @@ What the paper fixes, and how each route below follows it
 ----------------------------------------------------------
 * A tensor with cyclic group symmetry is an order-2N "unfolded" tensor
   t[i1 I1, ..., iN IN] that vanishes unless sum_mu c_mu I_mu == Z (mod G)
-  (Eq. ex1 and the unfolded rule of Sec. 1; general form Eq. symtsr, with
-  coefficients c_mu = +-1 here).  The full index of a mode is x = q*D + b
-  (q = sector / irrep label, b = index inside the block).
+  (Eq. ex1 and the unfolded rule of Sec. 1; general form Eq. symtsr).  In
+  the general form mode mu has H_mu sectors (H_mu divides G) and coefficient
+  c_mu = +-G/H_mu; Sym.sectors gives H_mu (default G, i.e. c_mu = +-1).
+  Product groups keep H_mu = G on every mode.
+* Block sizes: uniform per mode (D_mu), or non-uniform d_mu(q) <= D_mu per
+  sector (Sym.sector_dims), held in blocks padded with zeros to D_mu (Sec. 1:
+  non-uniform blocks are padded to a fixed size).  The dense tensor of a mode
+  is compact: sector q occupies full indices off(q) .. off(q) + d(q) - 1,
+  off(q) = sum_{q' < q} d(q'); with uniform blocks x = q*D + b.
+  Padding entries of a reduced form are not part of the tensor: every route
+  reads them as zero, and results hold zeros there.
 * Its standard reduced form drops one sector index (Sec. 2.1 and its
   footnote; Eq. redform).  Reading used here: the LAST mode's sector is the
-  implicit one, so the stored array has shape [G]*(N-1) + [D_0..D_{N-1}],
-  and q_{N-1} = c_{N-1} * (Z - sum_{mu<N-1} c_mu q_mu).
+  implicit one, so the stored array has shape [H_0..H_{N-2}] + [D_0..D_{N-1}]
+  ([G]*(N-1) + dims with c = +-1), and q_{N-1} solves
+  c_{N-1} q_{N-1} == Z - sum_{mu<N-1} c_mu q_mu (mod G).  With a sub-group
+  coefficient on the last mode some explicit sector tuples leave no
+  solution: those entries of the reduced form are not part of the tensor
+  either (read as zero, written as zero).
 * Product groups Z_m1 x ... x Z_mr (Sec. 3): a label is a tuple, flattened
   mixed-radix with the first modulus most significant; all charge
   arithmetic is componentwise.
@@ -34,6 +46,8 @@ O5 aligned, dense deltas : Algorithm 2 with the transformations done, as
                            contractions with dense generalized Kronecker
                            delta tensors (Sec. 3), the aligned contraction
                            as a batched matmul.
+O5b aligned entries      : the reduced-form position of single entries of the
+                           aligned forms (for sampled checks of large cases).
 O6 gradients             : adjoint contractions, again by the block loop.
 O7 finite differences    : central differences of a scalar loss (FP64).
 
@@ -73,6 +87,7 @@ __all__ = [
     "contract_blockloop", "contract_element", "contract_element_lazy", "align_u", "align_v",
     "mapback_w", "align_w", "q_set", "contract_aligned", "delta", "grad_u", "grad_v",
     "central_difference", "count_stored_blocks", "aligned_dims", "aligned_index",
+    "aligned_valid", "full_dims", "sanitize",
 ]
 
 
@@ -123,40 +138,112 @@ class Group:
         comps = [sign * (a - b) for a, b in zip(self.norm(z), rest)]
         return self.label(comps)
 
+    def solve_coef(self, coef: int, sectors: int, coeffs, labels, z) -> Optional[int]:
+        """Sector q in [0, sectors) with coef*q + sum coeffs*labels == z, where
+        coef = +-G/sectors (Eq. symtsr), or None when no such q exists."""
+        if abs(coef) == 1:
+            return self.solve(coef, coeffs, labels, z)
+        if len(self.moduli) != 1:
+            raise ValueError("sub-group coefficients need a single cyclic factor")
+        G = self.order
+        step = G // sectors
+        rest = self.charge(coeffs, labels)[0]
+        r = ((1 if coef > 0 else -1) * (self.norm(z)[0] - rest)) % G
+        return r // step if r % step == 0 else None
+
 
 @dataclass(frozen=True)
 class Sym:
-    """Conservation law and block sizes of one tensor."""
+    """Conservation law and block sizes of one tensor.
+    signs       : +-1 per mode (the sign of c_mu).
+    charge      : remainder Z, one entry per modulus.
+    dims        : block size D_mu per mode (the padded size when sectors differ).
+    sectors     : H_mu per mode (divides G; c_mu = sign * G / H_mu), or None
+                  for H_mu = G on every mode.
+    sector_dims : per mode, the true block size d_mu(q) <= D_mu of each of its
+                  H_mu sectors, or None for uniform blocks."""
     signs: Tuple[int, ...]
     charge: Tuple[int, ...]
     dims: Tuple[int, ...]
+    sectors: Optional[Tuple[int, ...]] = None
+    sector_dims: Optional[Tuple[Tuple[int, ...], ...]] = None
 
     @property
     def order(self) -> int:
         return len(self.dims)
+
+    @property
+    def general(self) -> bool:
+        return self.sectors is not None or self.sector_dims is not None
+
+    def nsec(self, group: Group, mu: int) -> int:
+        return group.order if self.sectors is None else int(self.sectors[mu])
+
+    def coef(self, group: Group, mu: int) -> int:
+        return int(self.signs[mu]) * (group.order // self.nsec(group, mu))
+
+    def coefs(self, group: Group) -> Tuple[int, ...]:
+        return tuple(self.coef(group, mu) for mu in range(self.order))
+
+    def bdim(self, mu: int, q: int) -> int:
+        """True block size of sector q of mode mu."""
+        return int(self.dims[mu]) if self.sector_dims is None else int(self.sector_dims[mu][q])
+
+
+def _sym_check(group: Group, sym: Sym):
+    for mu in range(sym.order):
+        h = sym.nsec(group, mu)
+        if h < 1 or group.order % h:
+            raise ValueError("sector counts must divide the group order")
+        if h != group.order and len(group.moduli) != 1:
+            raise ValueError("sub-group coefficients need a single cyclic factor")
+        if sym.sector_dims is not None:
+            if len(sym.sector_dims[mu]) != h or not all(0 <= d <= sym.dims[mu] for d in sym.sector_dims[mu]):
+                raise ValueError("sector_dims: one size in [0, D] per sector")
 
 
 def reduced_shape(group: Group, sym: Sym) -> Tuple[int, ...]:
     n = sym.order
     if n == 0:
         return ()
-    return tuple([group.order] * (n - 1) + list(sym.dims))
+    return tuple([sym.nsec(group, mu) for mu in range(n - 1)] + list(sym.dims))
+
+
+def full_dims(group: Group, sym: Sym) -> Tuple[int, ...]:
+    """Dims of the dense (unfolded, compact) tensor: sum over sectors of d(q)."""
+    return tuple(sum(sym.bdim(mu, q) for q in range(sym.nsec(group, mu))) for mu in range(sym.order))
+
+
+def _offsets(group: Group, sym: Sym, mu: int) -> List[int]:
+    off, acc = [], 0
+    for q in range(sym.nsec(group, mu)):
+        off.append(acc)
+        acc += sym.bdim(mu, q)
+    return off
 
 
 def count_stored_blocks(group: Group, sym: Sym) -> Tuple[int, int]:
     """(#allowed blocks, #blocks of the dense tensor), by enumeration."""
     n = sym.order
-    allowed = sum(1 for qs in itertools.product(range(group.order), repeat=n)
-                  if group.conserves(sym.signs, qs, sym.charge))
-    return allowed, group.order ** n
+    hs = [sym.nsec(group, mu) for mu in range(n)]
+    allowed = sum(1 for qs in itertools.product(*[range(h) for h in hs])
+                  if group.conserves(sym.coefs(group), qs, sym.charge))
+    return allowed, int(np.prod(hs)) if hs else 1
 
 
 # ---------------------------------------------------------------------------
 # O1 / O2: reduced form <-> dense tensor (Eq. symtsr / Eq. redform)
 # ---------------------------------------------------------------------------
 
-def _block(qs, dims):
-    return tuple(slice(q * d, (q + 1) * d) for q, d in zip(qs, dims))
+def _block(group: Group, sym: Sym, qs, offs=None):
+    """Slices of the dense tensor holding the block of sector tuple qs."""
+    offs = offs or [_offsets(group, sym, mu) for mu in range(sym.order)]
+    return tuple(slice(offs[mu][q], offs[mu][q] + sym.bdim(mu, q)) for mu, q in enumerate(qs))
+
+
+def _valid(sym: Sym, qs):
+    """Slices of a padded block that hold its true entries."""
+    return tuple(slice(0, sym.bdim(mu, q)) for mu, q in enumerate(qs))
 
 
 def _as_real_or_complex(a) -> np.ndarray:
@@ -165,39 +252,61 @@ def _as_real_or_complex(a) -> np.ndarray:
     return a.astype(np.complex128 if np.iscomplexobj(a) else np.float64, copy=False)
 
 
+def _sectors(group: Group, sym: Sym):
+    return itertools.product(*[range(sym.nsec(group, mu)) for mu in range(sym.order)])
+
+
 def expand(group: Group, sym: Sym, red: np.ndarray) -> np.ndarray:
-    """Dense tensor T[x] = red[q_0..q_{N-2}, b_0..b_{N-1}] if the sectors
-    conserve charge, else 0, with q = x div D and b = x mod D."""
+    """Dense tensor T: the block of every sector tuple (q_0..q_{N-1}) whose
+    charge sum_mu c_mu q_mu == Z is red[q_0..q_{N-2}] cut to its true sizes,
+    placed at the sectors' compact offsets; every other entry is 0."""
     red = _as_real_or_complex(red)
+    _sym_check(group, sym)
     if red.shape != reduced_shape(group, sym):
         raise ValueError(f"reduced shape {red.shape} != {reduced_shape(group, sym)}")
     n = sym.order
     if n == 0:
         ok = group.conserves((), (), sym.charge)
         return red.copy() if ok else np.zeros((), dtype=red.dtype)
-    dense = np.zeros([group.order * d for d in sym.dims], dtype=red.dtype)
-    for qs in itertools.product(range(group.order), repeat=n):
-        if group.conserves(sym.signs, qs, sym.charge):
-            dense[_block(qs, sym.dims)] = red[qs[:-1]]
+    dense = np.zeros(full_dims(group, sym), dtype=red.dtype)
+    offs = [_offsets(group, sym, mu) for mu in range(n)]
+    coefs = sym.coefs(group)
+    for qs in _sectors(group, sym):
+        if group.conserves(coefs, qs, sym.charge):
+            dense[_block(group, sym, qs, offs)] = red[qs[:-1]][_valid(sym, qs)]
     return dense
 
 
 def restrict(group: Group, sym: Sym, dense: np.ndarray) -> Tuple[np.ndarray, float]:
-    """Inverse of expand.  Also returns max |entry| over forbidden blocks."""
+    """Inverse of expand (padding and the entries of sector tuples with no
+    solution are 0).  Also returns max |entry| over forbidden blocks."""
     dense = _as_real_or_complex(dense)
+    _sym_check(group, sym)
     n = sym.order
     if n == 0:
         ok = group.conserves((), (), sym.charge)
         return (dense.copy() if ok else np.zeros((), dtype=dense.dtype)), (0.0 if ok else float(abs(dense)))
     red = np.zeros(reduced_shape(group, sym), dtype=dense.dtype)
     worst = 0.0
-    for qs in itertools.product(range(group.order), repeat=n):
-        blk = dense[_block(qs, sym.dims)]
-        if group.conserves(sym.signs, qs, sym.charge):
-            red[qs[:-1]] = blk
+    offs = [_offsets(group, sym, mu) for mu in range(n)]
+    coefs = sym.coefs(group)
+    for qs in _sectors(group, sym):
+        blk = dense[_block(group, sym, qs, offs)]
+        if group.conserves(coefs, qs, sym.charge):
+            red[qs[:-1]][_valid(sym, qs)] = blk
         elif blk.size:
             worst = max(worst, float(np.max(np.abs(blk))))
     return red, worst
+
+
+def sanitize(group: Group, sym: Sym, red) -> np.ndarray:
+    """The reduced form with every entry that is not part of the tensor
+    (padding, sector tuples without a solution) set to 0; the array itself
+    when the tensor has neither."""
+    red = _as_real_or_complex(red)
+    if not sym.general:
+        return red
+    return restrict(group, sym, expand(group, sym, red))[0]
 
 
 # ---------------------------------------------------------------------------
@@ -249,37 +358,57 @@ class Plan:
             return self.sym_u.dims[self.lu.index(lab)]
         return self.sym_v.dims[self.lv.index(lab)]
 
+    def nsec(self, lab: str) -> int:
+        """Sector count H of the mode labelled lab."""
+        if lab in self.lu:
+            return self.sym_u.nsec(self.group, self.lu.index(lab))
+        return self.sym_v.nsec(self.group, self.lv.index(lab))
+
 
 def plan(spec: str, group: Group, sym_u: Sym, sym_v: Sym) -> Plan:
     lu, lv, lw = parse_einsum(spec)
     if len(lu) != sym_u.order or len(lv) != sym_v.order:
         raise ValueError("operand order mismatch")
+    _sym_check(group, sym_u)
+    _sym_check(group, sym_v)
     C = [c for c in lu if c in lv]
     FU = [c for c in lu if c not in lv]
     FV = [c for c in lv if c not in lu]
     sig = None
     for c in C:
-        cu, cv = sym_u.signs[lu.index(c)], sym_v.signs[lv.index(c)]
-        if sym_u.dims[lu.index(c)] != sym_v.dims[lv.index(c)]:
+        i, j = lu.index(c), lv.index(c)
+        if sym_u.dims[i] != sym_v.dims[j]:
             raise ValueError(f"dimension mismatch on contracted mode {c}")
-        r = cu * cv
+        if sym_u.nsec(group, i) != sym_v.nsec(group, j):
+            raise ValueError(f"sector count mismatch on contracted mode {c}")
+        if [sym_u.bdim(i, q) for q in range(sym_u.nsec(group, i))] != \
+                [sym_v.bdim(j, q) for q in range(sym_v.nsec(group, j))]:
+            raise ValueError(f"sector size mismatch on contracted mode {c}")
+        r = sym_u.signs[i] * sym_v.signs[j]
         if sig is None:
             sig = r
         elif sig != r:
             raise ValueError("contracted signs must agree up to one global sign")
     if sig is None:
         sig = -1
-    signs_w, dims_w = [], []
+    signs_w, dims_w, sec_w, sd_w = [], [], [], []
     for c in lw:
         if c in FU:
-            signs_w.append(sym_u.signs[lu.index(c)])
-            dims_w.append(sym_u.dims[lu.index(c)])
+            i = lu.index(c)
+            signs_w.append(sym_u.signs[i])
+            src, mu = sym_u, i
         else:
-            signs_w.append(-sig * sym_v.signs[lv.index(c)])
-            dims_w.append(sym_v.dims[lv.index(c)])
+            j = lv.index(c)
+            signs_w.append(-sig * sym_v.signs[j])
+            src, mu = sym_v, j
+        dims_w.append(src.dims[mu])
+        sec_w.append(src.nsec(group, mu))
+        sd_w.append(tuple(src.bdim(mu, q) for q in range(src.nsec(group, mu))))
     zw = group.norm([a - sig * b for a, b in zip(group.norm(sym_u.charge),
                                                   group.norm(sym_v.charge))])
-    sym_w = Sym(tuple(signs_w), zw, tuple(dims_w))
+    general = sym_u.general or sym_v.general
+    sym_w = Sym(tuple(signs_w), zw, tuple(dims_w),
+                tuple(sec_w) if general else None, tuple(sd_w) if general else None)
     return Plan(lu, lv, lw, FU, C, FV, sig, sym_u, sym_v, sym_w, group)
 
 
@@ -301,8 +430,8 @@ def contract_dense_loops(p: Plan, u_red, v_red) -> np.ndarray:
     Returns the dense output tensor."""
     U = expand(p.group, p.sym_u, u_red)
     V = expand(p.group, p.sym_v, v_red)
-    G = p.group.order
-    full = {c: G * p.dim(c) for c in set(p.lu + p.lv)}
+    full = dict(zip(p.lu, U.shape))
+    full.update(zip(p.lv, V.shape))
     W = np.zeros([full[c] for c in p.lw], dtype=np.float64)
     for widx in itertools.product(*[range(full[c]) for c in p.lw]):
         env = dict(zip(p.lw, widx))
@@ -327,15 +456,17 @@ def contract_blockloop(p: Plan, u_red, v_red, counter: Optional[list] = None) ->
     """Loop over the sectors of W's explicit modes and of all contracted
     modes but the last; derive the last contracted sector from U's law and
     W's implicit sector from W's law (Algorithm 1 for s=t=v=2); multiply the
-    two blocks (numpy.tensordot) and accumulate into W's reduced form."""
+    two blocks (numpy.tensordot) and accumulate into W's reduced form.  A
+    sector equation without a solution (sub-group coefficients) skips the
+    tuple; padded blocks take part with their padding read as zero."""
     G = p.group
-    u_red = _as_real_or_complex(u_red)
-    v_red = _as_real_or_complex(v_red)
+    u_red = sanitize(G, p.sym_u, u_red)
+    v_red = sanitize(G, p.sym_v, v_red)
     w_red = np.zeros(reduced_shape(G, p.sym_w), dtype=np.result_type(u_red, v_red))
     lw = p.lw
-    wsig = dict(zip(lw, p.sym_w.signs))
-    usig = dict(zip(p.lu, p.sym_u.signs))
-    vsig = dict(zip(p.lv, p.sym_v.signs))
+    wco = dict(zip(lw, p.sym_w.coefs(G)))
+    uco = dict(zip(p.lu, p.sym_u.coefs(G)))
+    vco = dict(zip(p.lv, p.sym_v.coefs(G)))
     explicit_w = list(lw[:-1])
     c_free = p.C[:-1]
     # contracted axes of the U and V blocks, in the order of p.C
@@ -343,25 +474,31 @@ def contract_blockloop(p: Plan, u_red, v_red, counter: Optional[list] = None) ->
     ax_v = [p.lv.index(c) for c in p.C]
     out_labels = [c for c in p.lu if c not in p.C] + [c for c in p.lv if c not in p.C]
     perm = [out_labels.index(c) for c in lw]
-    for qw in itertools.product(range(G.order), repeat=len(explicit_w)):
+    for qw in itertools.product(*[range(p.nsec(c)) for c in explicit_w]):
         sec = dict(zip(explicit_w, qw))
         if lw:
             last = lw[-1]
-            sec[last] = G.solve(wsig[last], [wsig[c] for c in explicit_w], qw,
-                                p.sym_w.charge)
-        for qc in itertools.product(range(G.order), repeat=len(c_free)):
+            q = G.solve_coef(wco[last], p.nsec(last), [wco[c] for c in explicit_w], qw,
+                             p.sym_w.charge)
+            if q is None:
+                continue
+            sec[last] = q
+        for qc in itertools.product(*[range(p.nsec(c)) for c in c_free]):
             sec.update(zip(c_free, qc))
             if p.C:
                 cl = p.C[-1]
                 known = [c for c in p.lu if c != cl]
-                sec[cl] = G.solve(usig[cl], [usig[c] for c in known],
-                                  [sec[c] for c in known], p.sym_u.charge)
+                q = G.solve_coef(uco[cl], p.nsec(cl), [uco[c] for c in known],
+                                 [sec[c] for c in known], p.sym_u.charge)
+                if q is None:
+                    continue
+                sec[cl] = q
             else:
                 # nothing contracted: both operand laws must hold separately
-                if not G.conserves([usig[c] for c in p.lu], [sec[c] for c in p.lu],
+                if not G.conserves([uco[c] for c in p.lu], [sec[c] for c in p.lu],
                                    p.sym_u.charge):
                     continue
-            if not G.conserves([vsig[c] for c in p.lv], [sec[c] for c in p.lv],
+            if not G.conserves([vco[c] for c in p.lv], [sec[c] for c in p.lv],
                                p.sym_v.charge):
                 continue
             ub = u_red[_red_index(sec, p.lu)] if p.lu else u_red
@@ -380,31 +517,49 @@ def contract_blockloop(p: Plan, u_red, v_red, counter: Optional[list] = None) ->
     return w_red
 
 
+def _w_sectors(p: Plan, w_index):
+    """Sectors and block indices of W's entry w_index, or None when the entry
+    is not part of W (no solution for the implicit sector, or padding)."""
+    G = p.group
+    lw = p.lw
+    nw = len(lw)
+    if nw == 0:
+        return ({}, {}) if G.conserves((), (), p.sym_w.charge) else None
+    wco = p.sym_w.coefs(G)
+    sec = dict(zip(lw[:-1], w_index[:nw - 1]))
+    blk = dict(zip(lw, w_index[nw - 1:]))
+    q = G.solve_coef(wco[-1], p.nsec(lw[-1]), wco[:-1], [sec[c] for c in lw[:-1]],
+                     p.sym_w.charge)
+    if q is None:
+        return None
+    sec[lw[-1]] = q
+    if any(blk[c] >= p.sym_w.bdim(i, sec[c]) for i, c in enumerate(lw)):
+        return None
+    return sec, blk
+
+
+def _sym_of(p: Plan, lab: str) -> Tuple[Sym, int]:
+    return (p.sym_u, p.lu.index(lab)) if lab in p.lu else (p.sym_v, p.lv.index(lab))
+
+
 def contract_element(p: Plan, u_red, v_red, w_index: Tuple[int, ...]) -> float:
     """One entry of W's reduced form, straight from Eq. ctr: fix W's sectors
     and block indices, sum over every allowed contracted sector tuple and
     every contracted block index."""
     G = p.group
-    lw = p.lw
-    nw = len(lw)
-    wsig = dict(zip(lw, p.sym_w.signs))
-    usig = dict(zip(p.lu, p.sym_u.signs))
-    vsig = dict(zip(p.lv, p.sym_v.signs))
-    if nw == 0:
-        if not G.conserves((), (), p.sym_w.charge):
-            return 0.0
-        sec, blk = {}, {}
-    else:
-        sec = dict(zip(lw[:-1], w_index[:nw - 1]))
-        blk = dict(zip(lw, w_index[nw - 1:]))
-        sec[lw[-1]] = G.solve(wsig[lw[-1]], [wsig[c] for c in lw[:-1]],
-                              [sec[c] for c in lw[:-1]], p.sym_w.charge)
+    found = _w_sectors(p, w_index)
+    if found is None:
+        return 0.0
+    sec, blk = found
+    u_red = sanitize(G, p.sym_u, u_red)
+    v_red = sanitize(G, p.sym_v, v_red)
+    uco, vco = p.sym_u.coefs(G), p.sym_v.coefs(G)
     total = 0.0
-    for qc in itertools.product(range(G.order), repeat=len(p.C)):
+    for qc in itertools.product(*[range(p.nsec(c)) for c in p.C]):
         sec.update(zip(p.C, qc))
-        if not G.conserves([usig[c] for c in p.lu], [sec[c] for c in p.lu], p.sym_u.charge):
+        if not G.conserves(uco, [sec[c] for c in p.lu], p.sym_u.charge):
             continue
-        if not G.conserves([vsig[c] for c in p.lv], [sec[c] for c in p.lv], p.sym_v.charge):
+        if not G.conserves(vco, [sec[c] for c in p.lv], p.sym_v.charge):
             continue
         ub = np.asarray(u_red)[_red_index(sec, p.lu)] if p.lu else np.asarray(u_red)
         vb = np.asarray(v_red)[_red_index(sec, p.lv)] if p.lv else np.asarray(v_red)
@@ -426,31 +581,24 @@ def contract_element_lazy(p: Plan, u_get, v_get, w_index: Tuple[int, ...]) -> fl
     u_get(index) / v_get(index) return the reduced-form sub-array at `index`,
     a tuple of ints and full slices in the reduced form's axis order."""
     G = p.group
-    lw = p.lw
-    nw = len(lw)
-    wsig = dict(zip(lw, p.sym_w.signs))
-    usig = dict(zip(p.lu, p.sym_u.signs))
-    vsig = dict(zip(p.lv, p.sym_v.signs))
-    if nw == 0:
-        if not G.conserves((), (), p.sym_w.charge):
-            return 0.0
-        sec, blk = {}, {}
-    else:
-        sec = dict(zip(lw[:-1], w_index[:nw - 1]))
-        blk = dict(zip(lw, w_index[nw - 1:]))
-        sec[lw[-1]] = G.solve(wsig[lw[-1]], [wsig[c] for c in lw[:-1]],
-                              [sec[c] for c in lw[:-1]], p.sym_w.charge)
+    found = _w_sectors(p, w_index)
+    if found is None:
+        return 0.0
+    sec, blk = found
+    uco, vco = p.sym_u.coefs(G), p.sym_v.coefs(G)
     cu = [c for c in p.lu if c in p.C]
     cv = [c for c in p.lv if c in p.C]
     total = 0.0
-    for qc in itertools.product(range(G.order), repeat=len(p.C)):
+    for qc in itertools.product(*[range(p.nsec(c)) for c in p.C]):
         sec.update(zip(p.C, qc))
-        if not G.conserves([usig[c] for c in p.lu], [sec[c] for c in p.lu], p.sym_u.charge):
+        if not G.conserves(uco, [sec[c] for c in p.lu], p.sym_u.charge):
             continue
-        if not G.conserves([vsig[c] for c in p.lv], [sec[c] for c in p.lv], p.sym_v.charge):
+        if not G.conserves(vco, [sec[c] for c in p.lv], p.sym_v.charge):
             continue
-        ui = _red_index(sec, p.lu) + tuple(blk[c] if c in blk else slice(None) for c in p.lu)
-        vi = _red_index(sec, p.lv) + tuple(blk[c] if c in blk else slice(None) for c in p.lv)
+        # the contracted block indices run over the true sizes of their sectors
+        cut = {c: slice(0, _sym_of(p, c)[0].bdim(_sym_of(p, c)[1], sec[c])) for c in p.C}
+        ui = _red_index(sec, p.lu) + tuple(blk[c] if c in blk else cut[c] for c in p.lu)
+        vi = _red_index(sec, p.lv) + tuple(blk[c] if c in blk else cut[c] for c in p.lv)
         us = np.asarray(u_get(ui), dtype=np.float64)
         vs = np.asarray(v_get(vi), dtype=np.float64)
         vs = np.transpose(vs, [cv.index(c) for c in cu]) if cv else vs
@@ -462,11 +610,14 @@ def contract_element_lazy(p: Plan, u_get, v_get, w_index: Tuple[int, ...]) -> fl
 # O5: Algorithm 2 with dense generalized Kronecker deltas
 # ---------------------------------------------------------------------------
 
-def delta(group: Group, coeffs: Sequence[int], z: Sequence[int]) -> np.ndarray:
-    """Dense generalized Kronecker delta: 1 where sum coeffs*q == z."""
+def delta(group: Group, coeffs: Sequence[int], z: Sequence[int],
+          extents: Optional[Sequence[int]] = None) -> np.ndarray:
+    """Dense generalized Kronecker delta: 1 where sum coeffs*q == z, each q
+    running over its extent (default G)."""
     n = len(coeffs)
-    d = np.zeros([group.order] * n, dtype=np.float64)
-    for qs in itertools.product(range(group.order), repeat=n):
+    ext = [group.order] * n if extents is None else [int(e) for e in extents]
+    d = np.zeros(ext, dtype=np.float64)
+    for qs in itertools.product(*[range(e) for e in ext]):
         if group.conserves(coeffs, qs, z):
             d[qs] = 1.0
     return d
@@ -484,13 +635,16 @@ class _Letters:
 
 
 def aligned_dims(p: Plan) -> Tuple[int, int, int, int]:
-    """(G, M, N, K) of the canonical aligned forms."""
+    """(G, M, N, K) of the canonical aligned forms: per group of modes, the
+    sector counts of all but its last mode times every block size."""
     G = p.group.order
 
     def size(mods):
         if not mods:
             return 1
-        n = G ** (len(mods) - 1)
+        n = 1
+        for c in mods[:-1]:
+            n *= p.nsec(c)
         for c in mods:
             n *= p.dim(c)
         return n
@@ -500,12 +654,20 @@ def aligned_dims(p: Plan) -> Tuple[int, int, int, int]:
 def _deltas(p: Plan):
     G = p.group
     zero = tuple(0 for _ in G.moduli)
-    cu = dict(zip(p.lu, p.sym_u.signs))
-    cv = dict(zip(p.lv, p.sym_v.signs))
-    d1 = delta(G, [cu[c] for c in p.FU] + [1], p.sym_u.charge)
-    d2 = delta(G, [cu[c] for c in p.C] + [-1], zero)
-    d3 = delta(G, [cv[c] for c in p.FV] + [p.sigma], p.sym_v.charge)
+    cu = dict(zip(p.lu, p.sym_u.coefs(G)))
+    cv = dict(zip(p.lv, p.sym_v.coefs(G)))
+
+    def ext(mods):
+        return [p.nsec(c) for c in mods] + [G.order]
+    d1 = delta(G, [cu[c] for c in p.FU] + [1], p.sym_u.charge, ext(p.FU))
+    d2 = delta(G, [cu[c] for c in p.C] + [-1], zero, ext(p.C))
+    d3 = delta(G, [cv[c] for c in p.FV] + [p.sigma], p.sym_v.charge, ext(p.FV))
     return d1, d2, d3
+
+
+def _own_delta(p: Plan, sym: Sym, labels: str):
+    G = p.group
+    return delta(G, list(sym.coefs(G)), sym.charge, [p.nsec(c) for c in labels])
 
 
 def _align(p: Plan, red, labels: str, sym: Sym, free: List[str], d_free, d2):
@@ -515,9 +677,9 @@ def _align(p: Plan, red, labels: str, sym: Sym, free: List[str], d_free, d2):
     L = _Letters()
     Q = L("Q")
     n = len(labels)
-    own = delta(G, list(sym.signs), sym.charge) if n else None
+    own = _own_delta(p, sym, labels) if n else None
     red_sub = "".join(L("q" + c) for c in labels[:-1]) + "".join(L("b" + c) for c in labels)
-    ops, subs = [np.asarray(red, dtype=np.float64)], [red_sub]
+    ops, subs = [sanitize(G, sym, np.asarray(red, dtype=np.float64))], [red_sub]
     if n:
         ops.append(own)
         subs.append("".join(L("q" + c) for c in labels))
@@ -542,8 +704,8 @@ def align_u(p: Plan, u_red) -> np.ndarray:
 def align_v(p: Plan, v_red) -> np.ndarray:
     """V_hat[Q, n, kappa] (Alg. 2, input transformation of V), kappa-major rows."""
     _, d2, d3 = _deltas(p)
-    # delta2 is written with U's contracted signs; V's law uses sigma * those,
-    # so the same delta selects the same Q for V's contracted sectors.
+    # delta2 is written with U's contracted coefficients; V's law uses sigma
+    # times those, so the same delta selects the same Q for V's contracted sectors.
     return _align(p, v_red, p.lv, p.sym_v, p.FV, d3, d2)
 
 
@@ -554,15 +716,15 @@ def mapback_w(p: Plan, w_hat) -> np.ndarray:
     L = _Letters()
     Q = L("Q")
     Gn, M, N, K = aligned_dims(p)
-    shp = [Gn] + [Gn] * max(p.s - 1, 0) + [p.dim(c) for c in p.FU] \
-        + [Gn] * max(p.t - 1, 0) + [p.dim(c) for c in p.FV]
+    shp = [Gn] + [p.nsec(c) for c in p.FU[:-1]] + [p.dim(c) for c in p.FU] \
+        + [p.nsec(c) for c in p.FV[:-1]] + [p.dim(c) for c in p.FV]
     what = np.asarray(w_hat, dtype=np.float64).reshape(shp)
     w_sub = (Q + "".join(L("q" + c) for c in p.FU[:-1]) + "".join(L("b" + c) for c in p.FU)
              + "".join(L("q" + c) for c in p.FV[:-1]) + "".join(L("b" + c) for c in p.FV))
     ops = [what, d1, d3]
     subs = [w_sub, "".join(L("q" + c) for c in p.FU) + Q, "".join(L("q" + c) for c in p.FV) + Q]
     if p.lw:
-        ops.append(delta(G, list(p.sym_w.signs), p.sym_w.charge))
+        ops.append(_own_delta(p, p.sym_w, p.lw))
         subs.append("".join(L("q" + c) for c in p.lw))
     out = "".join(L("q" + c) for c in p.lw[:-1]) + "".join(L("b" + c) for c in p.lw)
     res = np.einsum(",".join(subs) + "->" + out, *ops, optimize=True)
@@ -578,10 +740,10 @@ def align_w(p: Plan, w_red) -> np.ndarray:
     d1, _, d3 = _deltas(p)
     L = _Letters()
     Q = L("Q")
-    ops = [np.asarray(w_red, dtype=np.float64)]
+    ops = [sanitize(G, p.sym_w, np.asarray(w_red, dtype=np.float64))]
     subs = ["".join(L("q" + c) for c in p.lw[:-1]) + "".join(L("b" + c) for c in p.lw)]
     if p.lw:
-        ops.append(delta(G, list(p.sym_w.signs), p.sym_w.charge))
+        ops.append(_own_delta(p, p.sym_w, p.lw))
         subs.append("".join(L("q" + c) for c in p.lw))
     ops += [d1, d3]
     subs += ["".join(L("q" + c) for c in p.FU) + Q, "".join(L("q" + c) for c in p.FV) + Q]
@@ -639,34 +801,44 @@ def _group_digits(p: Plan, labels: List[str], coeffs: List[int], target, r):
     (sector digits of all but the last mode, then every block digit, C
     order); the last mode's sector solves sum coeffs * q == target, where
     target is a list of component arrays.  Returns ({label: sector},
-    {label: block})."""
+    {label: block}, valid), valid marking the indices whose equation has a
+    solution and whose block digits lie inside their sectors' true sizes."""
     G = p.group
     n = len(labels)
+    r = np.asarray(r, dtype=np.int64)
     if n == 0:
-        return {}, {}
-    shape = [G.order] * (n - 1) + [p.dim(c) for c in labels]
-    digits = np.unravel_index(np.asarray(r, dtype=np.int64), shape)
+        # no modes: the equation reads 0 == target
+        ok = all(int(np.mod(t, m)) == 0 for t, m in zip(target, G.moduli))
+        return {}, {}, np.full(r.shape, ok, dtype=bool)
+    shape = [p.nsec(c) for c in labels[:-1]] + [p.dim(c) for c in labels]
+    digits = np.unravel_index(r, shape)
     sec = {c: digits[i] for i, c in enumerate(labels[:-1])}
     blk = {c: digits[n - 1 + i] for i, c in enumerate(labels)}
     rest = [0] * len(G.moduli)
     for c, k in zip(labels[:-1], coeffs[:-1]):
         for j, x in enumerate(_comps_arr(G, sec[c])):
             rest[j] = rest[j] + k * x
-    last = coeffs[-1]   # +-1: its own inverse
-    sec[labels[-1]] = _label_arr(G, [last * (t - x) for t, x in zip(target, rest)])
-    return sec, blk
+    last, h = coeffs[-1], p.nsec(labels[-1])
+    valid = np.ones(r.shape, dtype=bool)
+    if abs(last) == 1:   # its own inverse
+        sec[labels[-1]] = _label_arr(G, [last * (t - x) for t, x in zip(target, rest)])
+    else:                # last * q == t - rest with last = +-G/h: needs a multiple of G/h
+        step = G.order // h
+        rhs = np.mod((1 if last > 0 else -1) * (target[0] - rest[0]), G.order)
+        valid = valid & (rhs % step == 0)
+        sec[labels[-1]] = np.where(valid, rhs // step, 0)
+    for c in labels:
+        sym, mu = _sym_of(p, c)
+        if sym.sector_dims is not None:
+            sizes = np.asarray(sym.sector_dims[mu], dtype=np.int64)
+            valid = valid & (blk[c] < sizes[sec[c]])
+    return sec, blk, valid
 
 
-def aligned_index(p: Plan, operand: int, Q: int, r, c) -> Tuple[np.ndarray, ...]:
-    """Reduced-form index of U_hat[Q, r, c] (operand 0: r = m over the free
-    modes of U, c = kappa over the contracted ones), V_hat[Q, r, c] (1: r = n
-    over the free modes of V, c = kappa) or W_hat[Q, r, c] (2: r = m, c = n),
-    as a tuple of integer arrays broadcast over r and c.  The implicit
-    sectors follow Alg. 2's three deltas: sum c^U_{F_U} q + Q == Z_U,
-    sum c^U_C q == Q, sum c^V_{F_V} q + sigma Q == Z_V."""
+def _aligned_entries(p: Plan, operand: int, Q: int, r, c):
     G = p.group
-    cu = dict(zip(p.lu, p.sym_u.signs))
-    cv = dict(zip(p.lv, p.sym_v.signs))
+    cu = dict(zip(p.lu, p.sym_u.coefs(G)))
+    cv = dict(zip(p.lv, p.sym_v.coefs(G)))
     qc = _comps_arr(G, Q)
     zu = [np.int64(z) for z in G.norm(p.sym_u.charge)]
     zv = [np.int64(z) for z in G.norm(p.sym_v.charge)]
@@ -678,12 +850,30 @@ def aligned_index(p: Plan, operand: int, Q: int, r, c) -> Tuple[np.ndarray, ...]
               2: ((p.FU, [cu[x] for x in p.FU], t_fu), (p.FV, [cv[x] for x in p.FV], t_fv), p.lw)}
     (rl, rk, rt), (cl, ck, ct), labels = groups[operand]
     r, c = np.broadcast_arrays(np.asarray(r, dtype=np.int64), np.asarray(c, dtype=np.int64))
-    sec, blk = _group_digits(p, rl, rk, rt, r)
-    s2, b2 = _group_digits(p, cl, ck, ct, c)
+    sec, blk, ok_r = _group_digits(p, rl, rk, rt, r)
+    s2, b2, ok_c = _group_digits(p, cl, ck, ct, c)
     sec.update(s2)
     blk.update(b2)
     full = np.zeros(r.shape, dtype=np.int64)
-    return tuple(full + sec[x] for x in labels[:-1]) + tuple(full + blk[x] for x in labels)
+    idx = tuple(full + sec[x] for x in labels[:-1]) + tuple(full + blk[x] for x in labels)
+    return idx, ok_r & ok_c
+
+
+def aligned_index(p: Plan, operand: int, Q: int, r, c) -> Tuple[np.ndarray, ...]:
+    """Reduced-form index of U_hat[Q, r, c] (operand 0: r = m over the free
+    modes of U, c = kappa over the contracted ones), V_hat[Q, r, c] (1: r = n
+    over the free modes of V, c = kappa) or W_hat[Q, r, c] (2: r = m, c = n),
+    as a tuple of integer arrays broadcast over r and c.  The implicit
+    sectors follow Alg. 2's three deltas: sum c^U_{F_U} q + Q == Z_U,
+    sum c^U_C q == Q, sum c^V_{F_V} q + sigma Q == Z_V.  Entries that are not
+    part of the tensor (aligned_valid is false) get an index inside the array."""
+    return _aligned_entries(p, operand, Q, r, c)[0]
+
+
+def aligned_valid(p: Plan, operand: int, Q: int, r, c) -> np.ndarray:
+    """False where the aligned entry is absent: an implicit sector equation
+    without a solution (sub-group coefficients) or a padding position."""
+    return _aligned_entries(p, operand, Q, r, c)[1]
 
 
 # ---------------------------------------------------------------------------

@@ -552,3 +552,203 @@ def test_conjugate_operand_carries_the_negated_law():
             want, forb = O.restrict(p.group, pc.sym_w, W)
             assert forb == 0.0
             assert rel(got, want) <= 1e-13
+
+
+# --------------------------------------------------------------------------
+# generalized symmetry (Eq. symtsr): sub-group coefficients c = +-G/H and
+# non-uniform sector sizes held in zero-padded blocks (Sec. 1)
+# --------------------------------------------------------------------------
+
+def _divisors(n):
+    return [d for d in range(1, n + 1) if n % d == 0]
+
+
+def random_general_case(s, t, v, G, rng, sigma, pad=True, sub=True):
+    """A random contraction whose modes have random sector counts H | G and,
+    with pad, random true block sizes d(q) in [0, D] (some modes uniform)."""
+    labels = iter("abcdefghijklmnop")
+    FU = [next(labels) for _ in range(s)]
+    C = [next(labels) for _ in range(v)]
+    FV = [next(labels) for _ in range(t)]
+    lu = "".join(rng.permutation(FU + C)) if FU or C else ""
+    lv = "".join(rng.permutation(C + FV)) if C or FV else ""
+    lw = "".join(rng.permutation(FU + FV)) if (FU or FV) else ""
+    g = O.Group((G,))
+    H = {c: (int(rng.choice(_divisors(G))) if sub else G) for c in lu + lv}
+    D = {c: int(rng.integers(1, 4)) for c in lu + lv}
+    SD = {}
+    for c in lu + lv:
+        if pad and rng.random() < 0.7:
+            SD[c] = tuple(int(rng.integers(0, D[c] + 1)) for _ in range(H[c]))
+        else:
+            SD[c] = tuple([D[c]] * H[c])
+    su_signs = {c: int(rng.choice([-1, 1])) for c in lu}
+    sv_signs = {c: (sigma * su_signs[c] if c in C else int(rng.choice([-1, 1]))) for c in lv}
+    zu, zv = (int(rng.integers(0, G)),), (int(rng.integers(0, G)),)
+
+    def sym(lab, signs, z):
+        return O.Sym(tuple(signs[c] for c in lab), z, tuple(D[c] for c in lab),
+                     tuple(H[c] for c in lab), tuple(SD[c] for c in lab))
+    su, sv = sym(lu, su_signs, zu), sym(lv, sv_signs, zv)
+    p = O.plan(f"{lu},{lv}->{lw}", g, su, sv)
+    u = rng.standard_normal(O.reduced_shape(g, su))
+    vv = rng.standard_normal(O.reduced_shape(g, sv))
+    return p, u, vv
+
+
+GEN_STV = [(1, 1, 1), (2, 1, 1), (1, 2, 2), (2, 2, 1), (0, 2, 1), (1, 0, 2), (2, 1, 0), (3, 1, 1),
+           (0, 0, 2)]
+
+
+@pytest.mark.parametrize("s,t,v", GEN_STV)
+def test_general_routes_agree_with_compact_dense_bruteforce(s, t, v):
+    """Sub-group coefficients and padded non-uniform blocks: the block loop
+    (O4), the dense-delta aligned route (O5) and entry-by-entry Eq. ctr agree
+    with the dense einsum over the compact unfolded tensors (O3), whose
+    forbidden blocks are exactly zero."""
+    rng = np.random.default_rng(900 + 100 * s + 10 * t + v)
+    for G, sigma in [(4, -1), (6, 1), (8, -1), (12, 1)]:
+        if G ** (s + t + v) > 30000:
+            continue
+        for _ in range(2):
+            p, u, vv = random_general_case(s, t, v, G, rng, sigma)
+            w3, forb = O.contract_dense_einsum(p, u, vv)
+            assert forb == 0.0
+            w4 = O.contract_blockloop(p, u, vv)
+            w5 = O.contract_aligned(p, u, vv)
+            assert rel(w4, w3) <= 1e-13
+            assert rel(w5, w3) <= 1e-13
+            if w3.ndim:
+                for _ in range(4):
+                    ix = tuple(int(rng.integers(0, d)) for d in w3.shape)
+                    e = O.contract_element(p, u, vv, ix)
+                    el = O.contract_element_lazy(p, lambda i: u[i], lambda i: vv[i], ix)
+                    assert abs(e - w3[ix]) <= 1e-12 * (1 + abs(w3[ix]))
+                    assert abs(el - w3[ix]) <= 1e-12 * (1 + abs(w3[ix]))
+
+
+def test_dense_loops_match_einsum_general():
+    rng = np.random.default_rng(77)
+    for (s, t, v) in [(1, 1, 1), (2, 1, 1), (1, 1, 2)]:
+        p, u, vv = random_general_case(s, t, v, 6, rng, -1)
+        W = O.contract_dense_loops(p, u, vv)
+        Wr, _ = O.restrict(p.group, p.sym_w, W)
+        assert rel(Wr, O.contract_blockloop(p, u, vv)) <= 1e-13
+
+
+def test_subgroup_modes_relabel_to_the_smaller_cyclic_group():
+    """Every mode with H sectors and coefficient +-G/H, remainders multiples
+    of G/H: the law sum (G/H) c q == (G/H) z (mod G) is the Z_H law sum c q == z
+    (mod H), so the reduced forms and the result equal those of the Z_H
+    contraction with +-1 coefficients."""
+    rng = np.random.default_rng(31)
+    for G, h in [(8, 4), (12, 3), (6, 2), (8, 2)]:
+        k = G // h
+        for spec_, su_s, sv_s in [("abkl,klij->abij", (1, 1, -1, -1), (1, 1, -1, -1)),
+                                  ("iak,kjb->ijab", (1, -1, 1), (1, 1, -1))]:
+            lu, rest = spec_.split(",")
+            lv = rest.split("->")[0]
+            du = tuple(int(rng.integers(1, 4)) for _ in lu)
+            dv = tuple(du[lu.index(c)] if c in lu else int(rng.integers(1, 4)) for c in lv)
+            zu, zv = int(rng.integers(0, h)), int(rng.integers(0, h))
+            gen = O.plan(spec_, O.Group((G,)),
+                         O.Sym(su_s, (k * zu,), du, tuple([h] * len(lu))),
+                         O.Sym(sv_s, (k * zv,), dv, tuple([h] * len(lv))))
+            small = O.plan(spec_, O.Group((h,)), O.Sym(su_s, (zu,), du), O.Sym(sv_s, (zv,), dv))
+            assert O.reduced_shape(gen.group, gen.sym_u) == O.reduced_shape(small.group, small.sym_u)
+            u = rng.standard_normal(O.reduced_shape(small.group, small.sym_u))
+            v = rng.standard_normal(O.reduced_shape(small.group, small.sym_v))
+            assert np.array_equal(O.contract_blockloop(gen, u, v), O.contract_blockloop(small, u, v))
+
+
+def test_uniform_sector_sizes_are_the_plain_form():
+    """sector_dims all equal to D (and H = G) describe the plain tensor: the
+    same result, bit for bit."""
+    rng = np.random.default_rng(32)
+    for c in WL.small_cases()[:6]:
+        p = mk(c)
+        G = p.group.order
+        full = lambda sym: O.Sym(sym.signs, sym.charge, sym.dims, tuple([G] * sym.order),
+                                 tuple(tuple([d] * G) for d in sym.dims))
+        if len(p.group.moduli) != 1:
+            continue
+        pg = O.plan(c.einsum, p.group, full(p.sym_u), full(p.sym_v))
+        u, v = WL.draw_pair(c)
+        assert np.array_equal(O.contract_blockloop(pg, u, v), O.contract_blockloop(p, u, v))
+
+
+def test_padding_is_read_as_zero_and_written_as_zero():
+    """Garbage in the padding of the inputs changes nothing; the padding of
+    the output and its entries without a solution are zero (Sec. 1: blocks are
+    padded with zeros)."""
+    rng = np.random.default_rng(33)
+    for (s, t, v) in [(2, 1, 1), (1, 2, 2), (2, 2, 1)]:
+        p, u, vv = random_general_case(s, t, v, 8, rng, 1)
+        w = O.contract_blockloop(p, u, vv)
+        cu, cv = O.sanitize(p.group, p.sym_u, u), O.sanitize(p.group, p.sym_v, vv)
+        assert np.array_equal(O.contract_blockloop(p, cu, cv), w)
+        noise_u = np.where(cu == 0, rng.standard_normal(u.shape) * 1e3, cu)
+        noise_v = np.where(cv == 0, rng.standard_normal(vv.shape) * 1e3, cv)
+        assert np.array_equal(O.contract_blockloop(p, noise_u, noise_v), w)
+        assert np.array_equal(O.sanitize(p.group, p.sym_w, w), w)
+
+
+@pytest.mark.parametrize("s,t,v", [(1, 1, 1), (2, 1, 2), (2, 2, 1), (0, 2, 1), (1, 0, 2), (2, 1, 0)])
+def test_general_aligned_index_matches_dense_delta_route(s, t, v):
+    """aligned_index / aligned_valid against align_u, align_v, mapback_w for
+    sub-group coefficients and padding: valid entries sit where the dense
+    route puts them, absent ones are zero in the dense route's aligned forms."""
+    rng = np.random.default_rng(1500 + 100 * s + 10 * t + v)
+    for G, sigma in [(4, 1), (6, -1), (8, 1)]:
+        if G ** (s + t + v) > 5000:
+            continue
+        p, u, vv = random_general_case(s, t, v, G, rng, sigma)
+        Gn, M, N, K = O.aligned_dims(p)
+        uh, vh = O.align_u(p, u), O.align_v(p, vv)
+        wh = rng.standard_normal((Gn, M, N))
+        w = O.mapback_w(p, wh)
+        for Q in range(G):
+            m, n, k = np.arange(M)[:, None], np.arange(N)[:, None], np.arange(K)[None, :]
+            for op, red, al, r in ((0, u, uh, m), (1, vv, vh, n)):
+                if not (p.lu if op == 0 else p.lv):
+                    continue
+                ok = O.aligned_valid(p, op, Q, r, k)
+                assert np.array_equal(np.where(ok, red[O.aligned_index(p, op, Q, r, k)], 0.0), al[Q])
+            if p.lw:
+                nn = np.arange(N)[None, :]
+                ok = O.aligned_valid(p, 2, Q, m, nn)
+                got = w[O.aligned_index(p, 2, Q, m, nn)]
+                assert np.array_equal(got[ok], wh[Q][ok])
+
+
+def test_general_adjoint_identity():
+    """<W(U, V), Y> = <U, gU(Y)> = <V, gV(Y)> with sub-group coefficients and
+    padding (the gradients are the adjoint contractions, O6)."""
+    rng = np.random.default_rng(34)
+    for (s, t, v) in [(1, 1, 1), (2, 1, 2), (2, 2, 1)]:
+        p, u, vv = random_general_case(s, t, v, 6, rng, -1)
+        u, vv = O.sanitize(p.group, p.sym_u, u), O.sanitize(p.group, p.sym_v, vv)
+        y = O.sanitize(p.group, p.sym_w, rng.standard_normal(O.reduced_shape(p.group, p.sym_w)))
+        w = O.contract_blockloop(p, u, vv)
+        a = float(np.sum(w * y))
+        b = float(np.sum(u * O.grad_u(p, y, vv)))
+        c = float(np.sum(vv * O.grad_v(p, u, y)))
+        assert abs(a - b) <= 1e-12 * (1 + abs(a)) and abs(a - c) <= 1e-12 * (1 + abs(a))
+
+
+def test_planted_wrong_subgroup_solve_is_caught(monkeypatch):
+    """Plant a plausible mistake in the sub-group solve (forgetting that
+    c q == r (mod G) with c = G/H needs r divisible by G/H and q = r / (G/H)):
+    the brute-force pin against the compact dense einsum catches it."""
+    def wrong(self, coef, sectors, coeffs, labels, z):
+        rest = self.charge(coeffs, labels)[0]
+        return ((1 if coef > 0 else -1) * (self.norm(z)[0] - rest)) % sectors
+    rng = np.random.default_rng(35)
+    cases = [random_general_case(2, 1, 1, 8, rng, -1) for _ in range(4)]
+    monkeypatch.setattr(O.Group, "solve_coef", wrong)
+    caught = 0
+    for p, u, vv in cases:
+        w3, _ = O.contract_dense_einsum(p, u, vv)
+        if rel(O.contract_blockloop(p, u, vv), w3) > 1e-6:
+            caught += 1
+    assert caught > 0
