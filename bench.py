@@ -492,7 +492,7 @@ def run_complex(args, rank, world):
             ev_e.record()
             ev_e.synchronize()
             ts.append(ev_s.elapsed_time(ev_e))
-        return statistics.mean(ts)
+        return statistics.median(ts)
 
     ms = max_over_ranks(timed(step), world, dev)
     p2.check_device_error()
@@ -523,9 +523,11 @@ def run_device(args, rank, world):
     """Workloads whose operands are drawn on the device: config 5 (the
     CC-ladder contraction at virtual 512 / occupied 128 with sector dims 512/G
     and 128/G, up to 275 GB at G = 2; --sweep-dims 256,64 gives the secondary
-    sweep at the CC ladder's dimensions) and the Table-2 instances of the Table-1
-    contraction families.  The error is taken on entries the oracle computes
-    one by one.  Forward, and with --backward the adjoint pair as well."""
+    sweep at the CC ladder's dimensions), the Table-2 instances of the Table-1
+    contraction families and the generic (s, t, v) contractions of Sec. 5.1.1
+    (G = 4, about 80e9 useful flops each).  The error is taken on entries the
+    oracle computes one by one.  Forward, and with --backward the adjoint pair
+    as well.  Step times are medians over the timed steps."""
     import torch
     import oracle as O
     import paper_2007_08056_gb300 as sc
@@ -537,6 +539,10 @@ def run_device(args, rank, world):
         virt, occ = (int(x) for x in args.sweep_dims.split(","))
         c = WL.cc_ladder(G, virt, occ)
         seed = 5000 + G if (virt, occ) == (512, 128) else 5100 + G
+    elif args.workload == "generic":
+        c = WL.generic_contraction(*args.stv_point)
+        G = c.moduli[0]
+        seed = c.u.seed
     else:
         c = WL.TABLE2[args.case]
         G = c.moduli[0]
@@ -576,7 +582,7 @@ def run_device(args, rank, world):
             ev_e.record()
             ev_e.synchronize()
             ts.append(ev_s.elapsed_time(ev_e))
-        return statistics.mean(ts)
+        return statistics.median(ts)
 
     ms = max_over_ranks(timed(lambda: p.contract(U, V, out=W, workspace=ws)), world, dev)
     # phase times from one profiled call outside the timed steps (the events
@@ -651,7 +657,7 @@ def run_small(args, rank, world):
             ev_e.record()
             ev_e.synchronize()
             ts.append(ev_s.elapsed_time(ev_e))
-        return statistics.mean(ts)
+        return statistics.median(ts)
 
     if args.workload == "z3":
         c = WL.Z3_ORDER4
@@ -764,8 +770,12 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["cc_ladder", "mps", "sweep", "table", "z3", "peps"],
+    ap.add_argument("--workload", choices=["cc_ladder", "mps", "sweep", "table", "generic", "z3",
+                                           "peps"],
                     default="cc_ladder")
+    ap.add_argument("--stv", default="all",
+                    help="generic: S,T,V (free modes of U, of V, contracted modes) or 'all' (the 27 "
+                         "points with s, t, v in 1..3), G = 4, about 80e9 useful flops each")
     ap.add_argument("--case", default="CC1_a", help="table: a Table-2 case (" + ", ".join(WL.TABLE2) + ")")
     ap.add_argument("--sweep-g", type=int, default=16, help="G of the sweep workload (config 5)")
     ap.add_argument("--sweep-dims", default="512,128",
@@ -795,7 +805,18 @@ def main():
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         torch.distributed.init_process_group("nccl")
-    if args.workload in ("sweep", "table"):
+    if args.workload == "generic":
+        points = WL.GENERIC_STV if args.stv == "all" else [tuple(int(x) for x in args.stv.split(","))]
+        for pt in points:
+            args.stv_point = pt
+            line = run_device(args, rank, world)
+            line["stv"] = list(pt)
+            if rank == 0:
+                print(json.dumps(line), flush=True)
+            import torch
+            torch.cuda.empty_cache()
+        line = None
+    elif args.workload in ("sweep", "table"):
         line = run_device(args, rank, world)
     elif args.workload in ("z3", "peps"):
         line = run_small(args, rank, world)
@@ -803,7 +824,7 @@ def main():
         line = run_complex(args, rank, world)
     else:
         line = run_ours(args, rank, world)
-    if rank == 0:
+    if rank == 0 and line is not None:
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch

@@ -107,7 +107,8 @@ typedef struct {
   int64_t dims_w[SYMCTR_MAX_ORDER];
   int64_t numel_u, numel_v, numel_w;   /* elements of the standard reduced forms */
   int64_t M, N, K;              /* aligned GEMM extents per irrep Q */
-  int32_t n_q;                  /* irreps Q that carry work (0, 1 or G) */
+  int32_t n_q;                  /* irreps Q that carry work (0, 1 or G; general plans: the
+                                   irreps of a progression, see q_first / q_step) */
   int32_t q_single;             /* the irrep when n_q == 1, else -1 */
   int64_t aligned_numel_u;      /* n_q * M * K */
   int64_t aligned_numel_v;      /* n_q * N * K */
@@ -125,7 +126,44 @@ typedef struct {
                                    form, or an aligned GEMM below 32 x 32 x 16 in M x N x K,
                                    e.g. a GEMV, where the tensor-core forms would gain
                                    nothing; the result is then exact to float64 rounding) */
+  int32_t general;              /* 1: some mode has fewer than G sectors or non-uniform
+                                   sector sizes (symctr_plan_create_general) */
+  int32_t q_first, q_step;      /* batch b of the aligned forms is irrep
+                                   Q = q_first + b * q_step (mod G), b < n_q (q_step = 0
+                                   when n_q <= 1; 0 and 1 for every plan of
+                                   symctr_plan_create with n_q = G) */
+  int32_t sectors_w[SYMCTR_MAX_ORDER]; /* sector count of each mode of W */
+  int32_t single_read_prep;     /* split form: bit 0 (U) / bit 1 (V) set when that operand's
+                                   aligned rows are long contiguous runs and its slices are
+                                   prepared by the single-read kernel (one HBM read) */
 } symctr_plan_info;
+
+/* One operand in the general form of Eq. symtsr, for symctr_plan_create_general.
+ *  signs       : [order] sign of each mode's coefficient (+1 / -1).
+ *  charge      : [n_moduli] remainder Z.
+ *  dims        : [order] block size D of each mode; with non-uniform sectors the
+ *                padded size (every block is stored padded to D).
+ *  sectors     : [order] sector count H of each mode (H divides G; the mode's
+ *                sectors are 0..H-1 and its coefficient is sign * G / H, so its
+ *                charges form the subgroup of order H), or NULL for H = G on every
+ *                mode.  H < G needs a single cyclic factor (n_moduli = 1).
+ *  sector_dims : the true block size d(q) in [0, D] of every sector, mode after
+ *                mode ([H_0 + ... + H_{order-1}] entries), or NULL for uniform
+ *                blocks (Sec. 1: non-uniform blocks are padded with zeros to a
+ *                fixed size).
+ * The standard reduced form is then a float64 array of shape
+ * [H_0, ..., H_{N-2}] + [D_0, ..., D_{N-1}] (sector of the last mode implicit,
+ * solving c_{N-1} q_{N-1} == Z - sum_{mu<N-1} c_mu q_mu (mod G)).  Entries that
+ * are not part of the tensor -- padding positions b >= d(q), and explicit sector
+ * tuples for which that equation has no solution -- are read as zero (whatever
+ * they hold) and written as zero. */
+typedef struct {
+  const int8_t* signs;
+  const int32_t* charge;
+  const int64_t* dims;
+  const int32_t* sectors;
+  const int64_t* sector_dims;
+} symctr_operand;
 
 /* Build a plan for W = einsum(spec, U, V).
  *  einsum   : "u_labels,v_labels->w_labels" (letters; each label at most once per
@@ -145,6 +183,25 @@ SYMCTR_API symctr_status symctr_plan_create(const char* einsum, int n_moduli, co
                                  const int64_t* dims_u, const int64_t* dims_v,
                                  const int8_t* signs_w_or_null, const int32_t* charge_w_or_null,
                                  symctr_precision prec, int n_slices, symctr_plan** out);
+
+/* symctr_plan_create for operands in the general form of Eq. symtsr: modes with
+ * H | G sectors and coefficient +-G/H, and non-uniform sector sizes held in
+ * zero-padded blocks (symctr_operand).  Contracted modes must agree in D, H and
+ * sector sizes.  W's modes inherit them from the operand modes they come from,
+ * and its law is derived as in symctr_plan_create (signs_w / charge_w optional
+ * checks).  Every precision form runs with the same kernels as for plain
+ * plans; the index maps of the aligned forms are always read from the offset
+ * tables (absent rows and columns marked there), and W is zeroed as a whole
+ * before each contraction.  Returns as symctr_plan_create (SYMCTR_ERR_SHAPE
+ * for a sector count that does not divide G or a size outside [0, D],
+ * SYMCTR_ERR_UNSUPPORTED for H < G with a product group).  Host only. */
+SYMCTR_API symctr_status symctr_plan_create_general(const char* einsum, int n_moduli,
+                                                   const int32_t* moduli, const symctr_operand* u,
+                                                   const symctr_operand* v,
+                                                   const int8_t* signs_w_or_null,
+                                                   const int32_t* charge_w_or_null,
+                                                   symctr_precision prec, int n_slices,
+                                                   symctr_plan** out);
 
 /* Fill *out with the plan's derived quantities.  Host only. */
 SYMCTR_API symctr_status symctr_plan_query(const symctr_plan* plan, symctr_plan_info* out);
@@ -175,7 +232,9 @@ SYMCTR_API symctr_status symctr_plan_attach_tables(symctr_plan* plan, void* tabl
  *  direction : +1 standard reduced form (src) -> aligned form (dst);
  *              -1 aligned form (src) -> standard reduced form (dst; entries whose
  *              irrep Q carries no work are written as 0).
- *  Aligned sizes are aligned_numel_{u,v,w}; reduced sizes numel_{u,v,w}. */
+ *  Aligned sizes are aligned_numel_{u,v,w}; reduced sizes numel_{u,v,w}; a side
+ *  with no entries may be NULL.  General plans: absent aligned entries are
+ *  written as 0 (+1) or skipped (-1, the reduced form being zeroed first). */
 SYMCTR_API symctr_status symctr_align(const symctr_plan* plan, int operand, int direction,
                            const double* src, double* dst, void* stream);
 

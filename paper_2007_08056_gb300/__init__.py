@@ -62,7 +62,18 @@ class PlanInfo(ctypes.Structure):
         ("useful_flops", ctypes.c_double), ("transform_bytes", ctypes.c_double),
         ("workspace_bytes", ctypes.c_uint64), ("workspace_bytes_backward", ctypes.c_uint64),
         ("workspace_bytes_min", ctypes.c_uint64), ("table_bytes", ctypes.c_uint64),
-        ("tensor_core", ctypes.c_int32),
+        ("tensor_core", ctypes.c_int32), ("general", ctypes.c_int32),
+        ("q_first", ctypes.c_int32), ("q_step", ctypes.c_int32),
+        ("sectors_w", ctypes.c_int32 * MAX_ORDER), ("single_read_prep", ctypes.c_int32),
+    ]
+
+
+class Operand(ctypes.Structure):
+    """symctr_operand: one operand in the general form of Eq. symtsr."""
+    _fields_ = [
+        ("signs", ctypes.POINTER(ctypes.c_int8)), ("charge", ctypes.POINTER(ctypes.c_int32)),
+        ("dims", ctypes.POINTER(ctypes.c_int64)), ("sectors", ctypes.POINTER(ctypes.c_int32)),
+        ("sector_dims", ctypes.POINTER(ctypes.c_int64)),
     ]
 
 
@@ -90,6 +101,10 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
                                        i64p, i64p, i8p, i32p, ctypes.c_int, ctypes.c_int,
                                        ctypes.POINTER(P)]
     lib.symctr_plan_query.argtypes = [P, ctypes.POINTER(PlanInfo)]
+    lib.symctr_plan_create_general.argtypes = [ctypes.c_char_p, ctypes.c_int, i32p,
+                                               ctypes.POINTER(Operand), ctypes.POINTER(Operand),
+                                               i8p, i32p, ctypes.c_int, ctypes.c_int,
+                                               ctypes.POINTER(P)]
     lib.symctr_align.argtypes = [P, ctypes.c_int, ctypes.c_int, P, P, P]
     lib.symctr_contract.argtypes = [P, P, P, P, P, ctypes.c_size_t, P]
     lib.symctr_contract_backward.argtypes = [P, P, P, P, P, P, P, ctypes.c_size_t, P]
@@ -109,7 +124,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.symctr_plan_attach_tables.argtypes = [P, P, ctypes.c_size_t, P]
     lib.symctr_plan_destroy.argtypes = [P]
     lib.symctr_plan_destroy.restype = None
-    for f in ("symctr_plan_create", "symctr_plan_query", "symctr_align", "symctr_contract",
+    for f in ("symctr_plan_create", "symctr_plan_create_general", "symctr_plan_query",
+              "symctr_align", "symctr_contract",
               "symctr_contract_backward", "symctr_check_device_error", "symctr_profile_enable",
               "symctr_profile_read", "symctr_contract_static_scratch",
               "symctr_selftest_bounded_wait", "symctr_contract_complex",
@@ -140,18 +156,44 @@ def _stream():
 
 @dataclass(frozen=True)
 class SymSpec:
-    """Conservation law of one operand: per-mode signs, remainder, sector dims."""
+    """Conservation law of one operand: per-mode signs, remainder, block sizes;
+    optionally (Eq. symtsr) the sector count H of each mode (coefficient
+    sign * G / H; None: H = G) and the true size of each sector's block
+    (non-uniform blocks padded to dims; None: uniform)."""
     signs: Tuple[int, ...]
     charge: Tuple[int, ...]
     dims: Tuple[int, ...]
+    sectors: Optional[Tuple[int, ...]] = None
+    sector_dims: Optional[Tuple[Tuple[int, ...], ...]] = None
+
+    @property
+    def general(self) -> bool:
+        return self.sectors is not None or self.sector_dims is not None
 
 
 def _spec(x) -> SymSpec:
     if isinstance(x, SymSpec):
         return x
-    signs, charge, dims = x
+    signs, charge, dims = x[:3]
+    sectors = tuple(int(h) for h in x[3]) if len(x) > 3 and x[3] is not None else None
+    sdims = (tuple(tuple(int(d) for d in m) for m in x[4])
+             if len(x) > 4 and x[4] is not None else None)
     return SymSpec(tuple(int(s) for s in signs), tuple(int(c) for c in charge),
-                   tuple(int(d) for d in dims))
+                   tuple(int(d) for d in dims), sectors, sdims)
+
+
+def _operand(spec: SymSpec, keep: list) -> Operand:
+    """symctr_operand for a spec (the arrays are kept alive in `keep`)."""
+    arrs = [_arr(ctypes.c_int8, spec.signs), _arr(ctypes.c_int32, spec.charge),
+            _arr(ctypes.c_int64, spec.dims),
+            _arr(ctypes.c_int32, spec.sectors) if spec.sectors is not None else None,
+            (_arr(ctypes.c_int64, [d for m in spec.sector_dims for d in m])
+             if spec.sector_dims is not None else None)]
+    keep.extend(a for a in arrs if a is not None)
+    cast = lambda a, t: ctypes.cast(a, ctypes.POINTER(t)) if a is not None else None
+    return Operand(cast(arrs[0], ctypes.c_int8), cast(arrs[1], ctypes.c_int32),
+                   cast(arrs[2], ctypes.c_int64), cast(arrs[3], ctypes.c_int32),
+                   cast(arrs[4], ctypes.c_int64))
 
 
 class Plan:
@@ -167,27 +209,51 @@ class Plan:
         su, sv = self.sym_u, self.sym_v
         sw = _spec(sym_w) if sym_w is not None else None
         handle = ctypes.c_void_p()
-        st = lib.symctr_plan_create(
-            einsum.encode(), len(self.moduli), _arr(ctypes.c_int32, self.moduli),
-            _arr(ctypes.c_int8, su.signs), _arr(ctypes.c_int32, su.charge),
-            _arr(ctypes.c_int8, sv.signs), _arr(ctypes.c_int32, sv.charge),
-            _arr(ctypes.c_int64, su.dims), _arr(ctypes.c_int64, sv.dims),
-            None if sw is None else _arr(ctypes.c_int8, sw.signs),
-            None if sw is None else _arr(ctypes.c_int32, sw.charge),
-            PRECISIONS[precision], int(n_slices), ctypes.byref(handle))
+        if su.general or sv.general:
+            keep = []
+            ou, ov = _operand(su, keep), _operand(sv, keep)
+            st = lib.symctr_plan_create_general(
+                einsum.encode(), len(self.moduli), _arr(ctypes.c_int32, self.moduli),
+                ctypes.byref(ou), ctypes.byref(ov),
+                None if sw is None else _arr(ctypes.c_int8, sw.signs),
+                None if sw is None else _arr(ctypes.c_int32, sw.charge),
+                PRECISIONS[precision], int(n_slices), ctypes.byref(handle))
+        else:
+            st = lib.symctr_plan_create(
+                einsum.encode(), len(self.moduli), _arr(ctypes.c_int32, self.moduli),
+                _arr(ctypes.c_int8, su.signs), _arr(ctypes.c_int32, su.charge),
+                _arr(ctypes.c_int8, sv.signs), _arr(ctypes.c_int32, sv.charge),
+                _arr(ctypes.c_int64, su.dims), _arr(ctypes.c_int64, sv.dims),
+                None if sw is None else _arr(ctypes.c_int8, sw.signs),
+                None if sw is None else _arr(ctypes.c_int32, sw.charge),
+                PRECISIONS[precision], int(n_slices), ctypes.byref(handle))
         _check(st)
         self._h = handle
         info = PlanInfo()
         _check(lib.symctr_plan_query(self._h, ctypes.byref(info)))
         self.info = info
         G = info.group_order
+        general = bool(info.general)
+        lhs, lw = einsum.replace(" ", "").split("->")
+        lu, lv = lhs.split(",")
+
+        def origin(c):   # the operand spec and mode a label of W comes from
+            return (su, lu.index(c)) if c in lu else (sv, lv.index(c))
+        sd_w = None
+        if general and (su.sector_dims is not None or sv.sector_dims is not None):
+            sd_w = tuple(tuple(sp.sector_dims[mu]) if sp.sector_dims is not None
+                         else (sp.dims[mu],) * int(info.sectors_w[i])
+                         for i, (sp, mu) in enumerate(origin(c) for c in lw))
         self.sym_w = SymSpec(tuple(info.signs_w[i] for i in range(info.order_w)),
                              tuple(info.charge_w[i] for i in range(info.n_moduli)),
-                             tuple(info.dims_w[i] for i in range(info.order_w)))
+                             tuple(info.dims_w[i] for i in range(info.order_w)),
+                             tuple(info.sectors_w[i] for i in range(info.order_w)) if general else None,
+                             sd_w)
 
         def shape(spec: SymSpec):
             n = len(spec.dims)
-            return tuple([G] * (n - 1) + list(spec.dims)) if n else ()
+            hs = list(spec.sectors) if spec.sectors is not None else [G] * n
+            return tuple(hs[:n - 1] + list(spec.dims)) if n else ()
         self.shape_u, self.shape_v, self.shape_w = shape(su), shape(sv), shape(self.sym_w)
         self._size_u, self._size_v, self._size_w = (torch.Size(self.shape_u), torch.Size(self.shape_v),
                                                      torch.Size(self.shape_w))
@@ -394,12 +460,13 @@ class Plan:
         return float(self.info.useful_flops)
 
     def q_values(self):
+        """The irrep of each batch of the aligned forms."""
         i = self.info
         if i.n_q == 0:
             return []
         if i.n_q == 1:
             return [i.q_single]
-        return list(range(i.group_order))
+        return [(i.q_first + b * i.q_step) % i.group_order for b in range(i.n_q)]
 
 
 class SymContract(torch.autograd.Function):

@@ -36,8 +36,10 @@ __host__ __device__ inline bool map_rows_fast(const AxisMap& rows) {
   return rows.n > 0 && rows.bstride[rows.n - 1] == 1;
 }
 
+// General plans pass their offset tables (t.urow != NULL): offsets come from
+// them, -1 marking an absent aligned row or column (read as zero, not stored).
 __global__ void __launch_bounds__(THREADS) gemm_f64_tiled(const __grid_constant__ Problem p, int ksplit, bool u_rows_fast,
-                                                          bool v_rows_fast,
+                                                          bool v_rows_fast, const Tables t,
                                                           const double* __restrict__ U,
                                                           const double* __restrict__ V,
                                                           double* __restrict__ W) {
@@ -58,14 +60,15 @@ __global__ void __launch_bounds__(THREADS) gemm_f64_tiled(const __grid_constant_
     int Q = batch_irrep(p, (int)b);
     int64_t kbeg = ks * kchunk, kend = kbeg + kchunk < p.K ? kbeg + kchunk : p.K;
     __syncthreads();
+    const bool tab = t.urow != nullptr;
     if (tid < BM) {
       int64_t m = m0 + tid;
-      uoff[tid] = m < p.M ? aoff(p.u.rows, p.g, Q, m) : 0;
-      woffr[tid] = m < p.M ? aoff(p.w.rows, p.g, Q, m) : 0;
+      uoff[tid] = m >= p.M ? 0 : tab ? t.urow[b * p.M + m] : aoff(p.u.rows, p.g, Q, m);
+      woffr[tid] = m >= p.M ? 0 : tab ? t.wrow[b * p.M + m] : aoff(p.w.rows, p.g, Q, m);
     } else if (tid < BM + BN) {
       int64_t n = n0 + tid - BM;
-      voff[tid - BM] = n < p.N ? aoff(p.v.rows, p.g, Q, n) : 0;
-      woffc[tid - BM] = n < p.N ? aoff(p.w.cols, p.g, Q, n) : 0;
+      voff[tid - BM] = n >= p.N ? 0 : tab ? t.vrow[b * p.N + n] : aoff(p.v.rows, p.g, Q, n);
+      woffc[tid - BM] = n >= p.N ? 0 : tab ? t.wcol[b * p.N + n] : aoff(p.w.cols, p.g, Q, n);
     }
     double acc[4][4];
 #pragma unroll
@@ -76,10 +79,10 @@ __global__ void __launch_bounds__(THREADS) gemm_f64_tiled(const __grid_constant_
       __syncthreads();
       if (tid < BK) {
         int64_t k = k0 + tid;
-        kuoff[tid] = k < kend ? aoff(p.u.cols, p.g, Q, k) : 0;
+        kuoff[tid] = k >= kend ? 0 : tab ? t.ucol[b * p.K + k] : aoff(p.u.cols, p.g, Q, k);
       } else if (tid >= 32 && tid < 32 + BK) {
         int64_t k = k0 + tid - 32;
-        kvoff[tid - 32] = k < kend ? aoff(p.v.cols, p.g, Q, k) : 0;
+        kvoff[tid - 32] = k >= kend ? 0 : tab ? t.vcol[b * p.K + k] : aoff(p.v.cols, p.g, Q, k);
       }
       __syncthreads();
 #pragma unroll
@@ -88,7 +91,8 @@ __global__ void __launch_bounds__(THREADS) gemm_f64_tiled(const __grid_constant_
         int mm = u_rows_fast ? e % BM : e / BK;
         int kk = u_rows_fast ? e / BM : e % BK;
         double x = 0.0;
-        if (m0 + mm < p.M && k0 + kk < kend) x = U[p.es * (uoff[mm] + kuoff[kk])];
+        if (m0 + mm < p.M && k0 + kk < kend && uoff[mm] >= 0 && kuoff[kk] >= 0)
+          x = U[p.es * (uoff[mm] + kuoff[kk])];
         As[kk][mm] = x;
       }
 #pragma unroll
@@ -97,7 +101,8 @@ __global__ void __launch_bounds__(THREADS) gemm_f64_tiled(const __grid_constant_
         int nn = v_rows_fast ? e % BN : e / BK;
         int kk = v_rows_fast ? e / BN : e % BK;
         double x = 0.0;
-        if (n0 + nn < p.N && k0 + kk < kend) x = V[p.es * (voff[nn] + kvoff[kk])];
+        if (n0 + nn < p.N && k0 + kk < kend && voff[nn] >= 0 && kvoff[kk] >= 0)
+          x = V[p.es * (voff[nn] + kvoff[kk])];
         Bs[kk][nn] = x;
       }
       __syncthreads();
@@ -117,11 +122,11 @@ __global__ void __launch_bounds__(THREADS) gemm_f64_tiled(const __grid_constant_
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       int mm = tr + 16 * i;
-      if (m0 + mm >= p.M) continue;
+      if (m0 + mm >= p.M || woffr[mm] < 0) continue;
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         int nn = tc + 16 * j;
-        if (n0 + nn >= p.N) continue;
+        if (n0 + nn >= p.N || woffc[nn] < 0) continue;
         double* dst = W + p.es * (woffr[mm] + woffc[nn]);
         if (ksplit > 1) atomicAdd(dst, signed_result(p, acc[i][j]));
         else store_w(p, dst, acc[i][j]);
@@ -404,11 +409,12 @@ __global__ void zero_w_entries(const __grid_constant__ Problem p, double* __rest
 }  // namespace
 
 cudaError_t launch_gemm_f64(const Problem& p, const double* u, const double* v, double* w,
-                            cudaStream_t st) {
+                            const Tables* tables, cudaStream_t st) {
   if (p.n_q == 0 || p.M == 0 || p.N == 0) return cudaSuccess;
   const int sms = sm_count();
   const int64_t target = (int64_t)sms * 2;
-  bool skinny = p.M < 16 || p.N < 16;
+  // general plans take the tiled kernel with their tables (every shape)
+  bool skinny = !tables && (p.M < 16 || p.N < 16);
   if (skinny && (p.M <= SKINNY_MAX || p.N <= SKINNY_MAX)) {
     bool long_is_u = p.N <= SKINNY_MAX ? true : false;
     // both sides short: an item reads one long-side row and every short-side
@@ -461,14 +467,17 @@ cudaError_t launch_gemm_f64(const Problem& p, const double* u, const double* v, 
   int64_t tiles = ((p.M + BM - 1) / BM) * ((p.N + BN - 1) / BN) * p.n_q;
   int ksplit = 1;
   while (tiles * ksplit < target && p.K / (ksplit * 2) >= 512) ksplit *= 2;
-  if (ksplit > 1 && !p.accumulate) {
+  // (a general plan's W is zeroed as a whole before its contraction)
+  if (ksplit > 1 && !p.accumulate && !tables) {
     zero_w_entries<<<sms * 4, 256, 0, st>>>(p, w);
     ++g_kernel_launches;
   }
+  Tables t{};
+  if (tables) t = *tables;
   int64_t blocks = tiles * ksplit;
   int64_t cap = (int64_t)sms * 4;
   gemm_f64_tiled<<<(int)(blocks < cap ? blocks : cap), THREADS, 0, st>>>(
-      p, ksplit, map_rows_fast(p.u.rows), map_rows_fast(p.v.rows), u, v, w);
+      p, ksplit, map_rows_fast(p.u.rows), map_rows_fast(p.v.rows), t, u, v, w);
   ++g_kernel_launches;
   return cudaGetLastError();
 }

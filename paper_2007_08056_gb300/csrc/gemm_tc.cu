@@ -363,22 +363,24 @@ __device__ __forceinline__ void f32_to_f64_batch(const uint32_t (&u)[B], double 
 // Map-back stores of a batch of results of one column (rows m_first, + rstep,
 // ...): plain stores, or (complex products) adds, with the problem's sign; the
 // output mode is uniform, so the plain path loads nothing from W.
+// Rows or columns with offset -1 (general plans: absent from W) are not stored.
 template <int B, bool GEN>
 __device__ __forceinline__ void store_batch(const Problem& p, double* w, const int64_t (&ro)[B],
                                             int64_t co, const double (&d)[B], int64_t m_first,
                                             int rstep) {
+  if (co < 0) return;
   if constexpr (!GEN) {
 #pragma unroll
     for (int j = 0; j < B; ++j)
-      if (m_first + rstep * j < p.M) w[ro[j] + co] = d[j];
+      if (m_first + rstep * j < p.M && ro[j] >= 0) w[ro[j] + co] = d[j];
   } else if (!p.accumulate) {
 #pragma unroll
     for (int j = 0; j < B; ++j)
-      if (m_first + rstep * j < p.M) w[(int64_t)p.es * (ro[j] + co)] = signed_result(p, d[j]);
+      if (m_first + rstep * j < p.M && ro[j] >= 0) w[(int64_t)p.es * (ro[j] + co)] = signed_result(p, d[j]);
   } else {
 #pragma unroll
     for (int j = 0; j < B; ++j)
-      if (m_first + rstep * j < p.M) w[(int64_t)p.es * (ro[j] + co)] += signed_result(p, d[j]);
+      if (m_first + rstep * j < p.M && ro[j] >= 0) w[(int64_t)p.es * (ro[j] + co)] += signed_result(p, d[j]);
   }
 }
 

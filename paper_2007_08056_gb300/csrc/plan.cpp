@@ -53,8 +53,8 @@ struct Layout {
   bool ok = true;
 };
 
-Layout make_layout(const Problem& pr, bool tensor_core, symctr_precision prec, int n_slices,
-                   int64_t kpad) {
+Layout make_layout(const Problem& pr, bool tensor_core, bool general, symctr_precision prec,
+                   int n_slices, int64_t kpad) {
   Layout L;
   uint64_t off = 256;
   auto region = [&](int64_t bytes) {
@@ -62,7 +62,10 @@ Layout make_layout(const Problem& pr, bool tensor_core, symctr_precision prec, i
     off += (uint64_t)round_up(bytes, 256);
     return at;
   };
-  if (tensor_core) {
+  if (!tensor_core && general) {
+    // the float64 form of a general plan reads its tables only
+    L.off_tab = region(tables_entries(pr) * 8);
+  } else if (tensor_core) {
     const int64_t nq = pr.n_q;
     L.off_tab = region(tables_entries(pr) * 8);
     int64_t ra = 0, rb = 0;
@@ -92,11 +95,22 @@ struct Tensor {
   int sign[SYMCTR_MAX_ORDER];
   int z;  // flattened remainder
   int64_t dim[SYMCTR_MAX_ORDER];
+  // sector count H of each mode (H | G; the coefficient is sign * G / H,
+  // Eq. symtsr) and the true block size of each sector when the blocks are
+  // non-uniform (padded to dim; empty: uniform)
+  int H[SYMCTR_MAX_ORDER];
+  std::vector<int64_t> sd[SYMCTR_MAX_ORDER];
   int order() const { return (int)labels.size(); }
+  bool general(int G) const {
+    for (int i = 0; i < order(); ++i)
+      if (H[i] != G || !sd[i].empty()) return true;
+    return false;
+  }
 };
 
-// Reduced-form strides of one tensor: sector axes of modes 0..N-2, then blocks.
-void reduced_strides(const Tensor& t, int G, int64_t* sstride, int64_t* bstride) {
+// Reduced-form strides of one tensor: sector axes of modes 0..N-2 (H_i
+// sectors each), then blocks.
+void reduced_strides(const Tensor& t, int64_t* sstride, int64_t* bstride) {
   int n = t.order();
   int64_t acc = 1;
   for (int i = n - 1; i >= 0; --i) {
@@ -109,16 +123,69 @@ void reduced_strides(const Tensor& t, int G, int64_t* sstride, int64_t* bstride)
       continue;
     }
     sstride[i] = acc;
-    acc *= G;
+    acc *= t.H[i];
   }
 }
 
-int64_t reduced_numel(const Tensor& t, int G) {
+int64_t reduced_numel(const Tensor& t) {
   int n = t.order();
   int64_t acc = 1;
   for (int i = 0; i < n; ++i) mul_ok(acc, t.dim[i], &acc);
-  for (int i = 0; i + 1 < n; ++i) mul_ok(acc, G, &acc);
+  for (int i = 0; i + 1 < n; ++i) mul_ok(acc, t.H[i], &acc);
   return acc;
+}
+
+// One side (rows or columns) of an aligned operand in the general form: the
+// modes' sector counts, coefficient signs, strides and true block sizes.
+// Host only: general plans read their index maps from the offset tables.
+struct GenAxis {
+  int n = 0;
+  int H[SYMCTR_MAX_ORDER], sign[SYMCTR_MAX_ORDER];
+  int64_t D[SYMCTR_MAX_ORDER], sstride[SYMCTR_MAX_ORDER], bstride[SYMCTR_MAX_ORDER];
+  const std::vector<int64_t>* sd[SYMCTR_MAX_ORDER];
+  int qa = 1, z = 0;
+  int64_t size = 1;
+};
+
+// Reduced-form offset of aligned index r at irrep Q, or -1 when the entry is
+// absent: the last mode's sector equation sum_i c_i q_i == qa Q + z (mod G),
+// c_i = sign_i G / H_i, has no solution (it needs a multiple of G / H_last),
+// or a block index lies beyond its sector's true size (padding).  Product
+// groups have H = G on every mode and solve componentwise.
+int64_t gen_offset(const GenAxis& a, const GroupDesc& g, int Q, int64_t r) {
+  const int target = g_add(g, g_signed(g, a.qa, Q), a.z);
+  if (a.n == 0) return target == 0 ? 0 : -1;
+  int64_t b[SYMCTR_MAX_ORDER];
+  int q[SYMCTR_MAX_ORDER];
+  for (int i = a.n - 1; i >= 0; --i) {
+    b[i] = r % a.D[i];
+    r /= a.D[i];
+  }
+  for (int i = a.n - 2; i >= 0; --i) {
+    q[i] = (int)(r % a.H[i]);
+    r /= a.H[i];
+  }
+  const int last = a.n - 1;
+  if (g.n == 1) {
+    const int G = g.order;
+    int partial = 0;
+    for (int i = 0; i < last; ++i) partial = (partial + a.sign[i] * (G / a.H[i]) * q[i]) % G;
+    const int rhs = ((target - partial) % G + G) % G;
+    const int x = ((a.sign[last] * rhs) % G + G) % G;
+    const int step = G / a.H[last];
+    if (x % step != 0) return -1;
+    q[last] = x / step;
+  } else {
+    int partial = 0;
+    for (int i = 0; i < last; ++i) partial = g_add(g, partial, g_signed(g, a.sign[i], q[i]));
+    q[last] = g_signed(g, a.sign[last], g_add(g, target, g_neg(g, partial)));
+  }
+  int64_t off = 0;
+  for (int i = 0; i < a.n; ++i) {
+    if (a.sd[i] && b[i] >= (*a.sd[i])[q[i]]) return -1;
+    off += (int64_t)q[i] * a.sstride[i] + b[i] * a.bstride[i];
+  }
+  return off;
 }
 
 }  // namespace
@@ -136,13 +203,20 @@ struct symctr_plan {
   // workspace: all irreps in one pass, or the smallest pass (one irrep)
   uint64_t ws_bytes = 256, ws_bytes_min = 256;
   bool tensor_core = false;
+  // sub-group coefficients or padded sectors on some mode: every form reads
+  // its index maps from the offset tables (absent entries -1)
+  bool general = false;
+  // split form: run length of the single-read preparation of U and V (0: the
+  // operand takes the two-phase preparation)
+  int64_t row_run[2] = {0, 0};
   symctr_plan* bwd_u = nullptr;
   symctr_plan* bwd_v = nullptr;
   bool prof = false;
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   mutable int last_launches = 0;
-  // offset tables of all irreps (tensor-core forms), computed once on the host
-  // in the workspace layout of a single pass; page-locked on first use
+  // offset tables of all irreps (tensor-core forms and general plans),
+  // computed once on the host in the workspace layout of a single pass;
+  // page-locked on first use
   std::vector<int64_t> htab;
   mutable std::once_flag pin_once;
   mutable bool pinned = false;
@@ -183,12 +257,12 @@ void g_comps(const GroupDesc& g, int q, int32_t* comps) {
   }
 }
 
-AxisMap make_axis(const Tensor& t, const std::vector<int>& modes, const int* law_sign, int G,
-                  int qa, int z) {
+AxisMap make_axis(const Tensor& t, const std::vector<int>& modes, const int* law_sign, int qa,
+                  int z) {
   AxisMap a;
   std::memset(&a, 0, sizeof(a));
   int64_t ss[SYMCTR_MAX_ORDER], bs[SYMCTR_MAX_ORDER];
-  reduced_strides(t, G, ss, bs);
+  reduced_strides(t, ss, bs);
   a.n = (int)modes.size();
   int64_t size = 1;
   for (int i = 0; i < a.n; ++i) {
@@ -198,7 +272,7 @@ AxisMap make_axis(const Tensor& t, const std::vector<int>& modes, const int* law
     a.sstride[i] = ss[mu];
     a.bstride[i] = bs[mu];
     size *= t.dim[mu];
-    if (i + 1 < a.n) size *= G;
+    if (i + 1 < a.n) size *= t.H[mu];
   }
   a.size = size;
   a.qa = qa;
@@ -206,13 +280,80 @@ AxisMap make_axis(const Tensor& t, const std::vector<int>& modes, const int* law
   return a;
 }
 
-symctr_status build(const char* einsum, int n_moduli, const int32_t* moduli, const int8_t* su,
-                    const int32_t* zu, const int8_t* sv, const int32_t* zv, const int64_t* du,
-                    const int64_t* dv, const int8_t* sw, const int32_t* zw, symctr_precision prec,
+GenAxis make_gen_axis(const Tensor& t, const std::vector<int>& modes, const int* law_sign, int qa,
+                      int z) {
+  GenAxis a;
+  int64_t ss[SYMCTR_MAX_ORDER], bs[SYMCTR_MAX_ORDER];
+  reduced_strides(t, ss, bs);
+  a.n = (int)modes.size();
+  for (int i = 0; i < a.n; ++i) {
+    int mu = modes[i];
+    a.H[i] = t.H[mu];
+    a.sign[i] = law_sign[i];
+    a.D[i] = t.dim[mu];
+    a.sstride[i] = ss[mu];
+    a.bstride[i] = bs[mu];
+    a.sd[i] = t.sd[mu].empty() ? nullptr : &t.sd[mu];
+    a.size *= t.dim[mu];
+    if (i + 1 < a.n) a.size *= t.H[mu];
+  }
+  a.qa = qa;
+  a.z = z;
+  return a;
+}
+
+// One operand as the plan builder receives it (see symctr_operand).
+struct OpDesc {
+  const int8_t* signs = nullptr;
+  const int32_t* charge = nullptr;
+  const int64_t* dims = nullptr;
+  const int32_t* sectors = nullptr;      // NULL: G sectors on every mode
+  const int64_t* sector_dims = nullptr;  // NULL: uniform blocks
+};
+
+// An OpDesc view of a tensor of a plan, with its own storage (backward plans).
+struct OwnedDesc {
+  int8_t signs[SYMCTR_MAX_ORDER];
+  int32_t charge[SYMCTR_MAX_MODULI];
+  int64_t dims[SYMCTR_MAX_ORDER];
+  int32_t sectors[SYMCTR_MAX_ORDER];
+  std::vector<int64_t> sd;
+  OpDesc desc;
+  OwnedDesc(const Tensor& t, const GroupDesc& g) {
+    bool any_sd = false;
+    for (int i = 0; i < t.order(); ++i) {
+      signs[i] = (int8_t)t.sign[i];
+      dims[i] = t.dim[i];
+      sectors[i] = t.H[i];
+      any_sd = any_sd || !t.sd[i].empty();
+    }
+    if (any_sd)
+      for (int i = 0; i < t.order(); ++i)
+        for (int q = 0; q < t.H[i]; ++q) sd.push_back(t.sd[i].empty() ? t.dim[i] : t.sd[i][q]);
+    g_comps(g, t.z, charge);
+    desc.signs = signs;
+    desc.charge = charge;
+    desc.dims = dims;
+    desc.sectors = sectors;
+    desc.sector_dims = any_sd ? sd.data() : nullptr;
+  }
+};
+
+int64_t gcd64(int64_t a, int64_t b) {
+  while (b) {
+    int64_t t = a % b;
+    a = b;
+    b = t;
+  }
+  return a;
+}
+
+symctr_status build(const char* einsum, int n_moduli, const int32_t* moduli, const OpDesc& du_,
+                    const OpDesc& dv_, const int8_t* sw, const int32_t* zw, symctr_precision prec,
                     int n_slices, bool with_backward, symctr_plan** out) {
   if (!out) return fail(SYMCTR_ERR_NULLPTR, "out is NULL");
   *out = nullptr;
-  if (!einsum || !moduli || !zu || !zv) return fail(SYMCTR_ERR_NULLPTR, "NULL argument");
+  if (!einsum || !moduli || !du_.charge || !dv_.charge) return fail(SYMCTR_ERR_NULLPTR, "NULL argument");
   if (n_moduli < 1 || n_moduli > SYMCTR_MAX_MODULI)
     return fail(SYMCTR_ERR_UNSUPPORTED, "n_moduli must be in [1, 4]");
   if (prec != SYMCTR_FP64 && prec != SYMCTR_SPLIT_BF16 && prec != SYMCTR_TF32)
@@ -253,8 +394,8 @@ symctr_status build(const char* einsum, int n_moduli, const int32_t* moduli, con
   for (char c : lv)
     if (lu.find(c) == std::string::npos && lw.find(c) == std::string::npos)
       return fail(SYMCTR_ERR_EINSUM, "free label of V missing from the output");
-  if ((!su || !du) && !lu.empty()) return fail(SYMCTR_ERR_NULLPTR, "signs_u/dims_u NULL");
-  if ((!sv || !dv) && !lv.empty()) return fail(SYMCTR_ERR_NULLPTR, "signs_v/dims_v NULL");
+  if ((!du_.signs || !du_.dims) && !lu.empty()) return fail(SYMCTR_ERR_NULLPTR, "signs_u/dims_u NULL");
+  if ((!dv_.signs || !dv_.dims) && !lv.empty()) return fail(SYMCTR_ERR_NULLPTR, "signs_v/dims_v NULL");
 
   symctr_plan* P = new (std::nothrow) symctr_plan();
   if (!P) return fail(SYMCTR_ERR_ARGUMENT, "out of host memory");
@@ -275,24 +416,46 @@ symctr_status build(const char* einsum, int n_moduli, const int32_t* moduli, con
   P->g.order = (int)G;
   const GroupDesc& g = P->g;
 
-  // ---- operands ----
+  // ---- operands: signs, block sizes, sector counts (Eq. symtsr), sector sizes ----
   P->u.labels = lu;
   P->v.labels = lv;
   P->w.labels = lw;
-  for (int i = 0; i < (int)lu.size(); ++i) {
-    if (su[i] != 1 && su[i] != -1) return bail(SYMCTR_ERR_SIGNS, "signs must be +1/-1");
-    if (du[i] < 1 || du[i] > (1 << 30)) return bail(SYMCTR_ERR_SHAPE, "sector dim out of range");
-    P->u.sign[i] = su[i];
-    P->u.dim[i] = du[i];
+  auto load = [&](Tensor& t, const OpDesc& d, const char* name) -> std::string {
+    int64_t at = 0;
+    for (int i = 0; i < t.order(); ++i) {
+      if (d.signs[i] != 1 && d.signs[i] != -1) return std::string("signs must be +1/-1 (") + name + ")";
+      if (d.dims[i] < 1 || d.dims[i] > (1 << 30)) return std::string("sector dim out of range (") + name + ")";
+      t.sign[i] = d.signs[i];
+      t.dim[i] = d.dims[i];
+      t.H[i] = d.sectors ? d.sectors[i] : (int)G;
+      if (t.H[i] < 1 || t.H[i] > G || G % t.H[i] != 0)
+        return std::string("sector counts must divide the group order (") + name + ")";
+      if (t.H[i] != G && n_moduli != 1)
+        return std::string("unsupported: sub-group coefficients need a single cyclic factor (") + name + ")";
+      if (d.sector_dims) {
+        bool uniform = true;
+        for (int q = 0; q < t.H[i]; ++q) {
+          const int64_t x = d.sector_dims[at + q];
+          if (x < 0 || x > t.dim[i]) return std::string("sector sizes must lie in [0, D] (") + name + ")";
+          uniform = uniform && x == t.dim[i];
+        }
+        if (!uniform) t.sd[i].assign(d.sector_dims + at, d.sector_dims + at + t.H[i]);
+        at += t.H[i];
+      }
+    }
+    return "";
+  };
+  {
+    std::string m = load(P->u, du_, "U");
+    if (m.empty()) m = load(P->v, dv_, "V");
+    if (!m.empty())
+      return bail(m.rfind("unsupported", 0) == 0 ? SYMCTR_ERR_UNSUPPORTED
+                  : m.rfind("signs", 0) == 0     ? SYMCTR_ERR_SIGNS
+                                                 : SYMCTR_ERR_SHAPE,
+                  m);
   }
-  for (int i = 0; i < (int)lv.size(); ++i) {
-    if (sv[i] != 1 && sv[i] != -1) return bail(SYMCTR_ERR_SIGNS, "signs must be +1/-1");
-    if (dv[i] < 1 || dv[i] > (1 << 30)) return bail(SYMCTR_ERR_SHAPE, "sector dim out of range");
-    P->v.sign[i] = sv[i];
-    P->v.dim[i] = dv[i];
-  }
-  P->u.z = g_label(g, zu);
-  P->v.z = g_label(g, zv);
+  P->u.z = g_label(g, du_.charge);
+  P->v.z = g_label(g, dv_.charge);
 
   // ---- mode classes and sigma ----
   int sigma = 0;
@@ -303,8 +466,8 @@ symctr_status build(const char* einsum, int n_moduli, const int32_t* moduli, con
       continue;
     }
     P->C.push_back(i);
-    if (P->u.dim[i] != P->v.dim[j])
-      return bail(SYMCTR_ERR_SHAPE, std::string("sector dims differ on contracted mode ") + lu[i]);
+    if (P->u.dim[i] != P->v.dim[j] || P->u.H[i] != P->v.H[j] || P->u.sd[i] != P->v.sd[j])
+      return bail(SYMCTR_ERR_SHAPE, std::string("sectors or their sizes differ on contracted mode ") + lu[i]);
     int r = P->u.sign[i] * P->v.sign[j];
     if (sigma == 0) sigma = r;
     else if (sigma != r)
@@ -326,14 +489,21 @@ symctr_status build(const char* einsum, int n_moduli, const int32_t* moduli, con
   auto derive = [&](int sg) {
     for (int i = 0; i < (int)lw.size(); ++i) {
       size_t a = lu.find(lw[i]);
+      const Tensor* src;
+      int mu;
       if (a != std::string::npos) {
         P->w.sign[i] = P->u.sign[a];
-        P->w.dim[i] = P->u.dim[a];
+        src = &P->u;
+        mu = (int)a;
       } else {
         size_t b = lv.find(lw[i]);
         P->w.sign[i] = -sg * P->v.sign[b];
-        P->w.dim[i] = P->v.dim[b];
+        src = &P->v;
+        mu = (int)b;
       }
+      P->w.dim[i] = src->dim[mu];
+      P->w.H[i] = src->H[mu];
+      P->w.sd[i] = src->sd[mu];
     }
     P->w.z = g_add(g, P->u.z, g_signed(g, -sg, P->v.z));
   };
@@ -356,11 +526,12 @@ symctr_status build(const char* einsum, int n_moduli, const int32_t* moduli, con
     }
     if (!matches(sw, zw)) return bail(SYMCTR_ERR_CHARGE, "given output law contradicts the derived law");
   }
+  P->general = P->u.general((int)G) || P->v.general((int)G) || P->w.general((int)G);
 
   // ---- sizes ----
-  P->numel_u = reduced_numel(P->u, (int)G);
-  P->numel_v = reduced_numel(P->v, (int)G);
-  P->numel_w = reduced_numel(P->w, (int)G);
+  P->numel_u = reduced_numel(P->u);
+  P->numel_v = reduced_numel(P->v);
+  P->numel_w = reduced_numel(P->w);
   if (P->numel_u >= kLimit || P->numel_v >= kLimit || P->numel_w >= kLimit)
     return bail(SYMCTR_ERR_OVERFLOW, "tensor too large");
 
@@ -384,41 +555,69 @@ symctr_status build(const char* einsum, int n_moduli, const int32_t* moduli, con
   }
   Problem& pr = P->prob;
   pr.g = g;
-  pr.u.rows = make_axis(P->u, P->FU, sgn_fu, (int)G, -1, P->u.z);
-  pr.u.cols = make_axis(P->u, P->C, sgn_cu, (int)G, +1, 0);
-  pr.v.rows = make_axis(P->v, FV_in_V, sgn_fv, (int)G, -sigma, P->v.z);
-  pr.v.cols = make_axis(P->v, C_in_V, sgn_cv, (int)G, sigma, 0);
-  pr.w.rows = make_axis(P->w, FU_in_W, sgn_fu, (int)G, -1, P->u.z);
-  pr.w.cols = make_axis(P->w, FV_in_W, sgn_fv, (int)G, -sigma, P->v.z);
+  pr.u.rows = make_axis(P->u, P->FU, sgn_fu, -1, P->u.z);
+  pr.u.cols = make_axis(P->u, P->C, sgn_cu, +1, 0);
+  pr.v.rows = make_axis(P->v, FV_in_V, sgn_fv, -sigma, P->v.z);
+  pr.v.cols = make_axis(P->v, C_in_V, sgn_cv, sigma, 0);
+  pr.w.rows = make_axis(P->w, FU_in_W, sgn_fu, -1, P->u.z);
+  pr.w.cols = make_axis(P->w, FV_in_W, sgn_fv, -sigma, P->v.z);
   pr.M = pr.u.rows.size;
   pr.N = pr.v.rows.size;
   pr.K = pr.u.cols.size;
+  pr.general = P->general ? 1 : 0;
+  GenAxis gax[6];
+  if (P->general) {
+    gax[0] = make_gen_axis(P->u, P->FU, sgn_fu, -1, P->u.z);
+    gax[1] = make_gen_axis(P->u, P->C, sgn_cu, +1, 0);
+    gax[2] = make_gen_axis(P->v, FV_in_V, sgn_fv, -sigma, P->v.z);
+    gax[3] = make_gen_axis(P->v, C_in_V, sgn_cv, sigma, 0);
+    gax[4] = make_gen_axis(P->w, FU_in_W, sgn_fu, -1, P->u.z);
+    gax[5] = make_gen_axis(P->w, FV_in_W, sgn_fv, -sigma, P->v.z);
+  }
 
   // ---- irreps carrying work ----
-  int nq = 0, qs = -1;
+  std::vector<int> works;
   for (int Q = 0; Q < (int)G; ++Q) {
     bool ok = true;
-    if (P->s == 0) ok = ok && g_add(g, P->u.z, g_neg(g, Q)) == 0;
-    if (P->vv == 0) ok = ok && Q == 0;
-    if (P->t == 0) ok = ok && g_add(g, P->v.z, g_neg(g, g_signed(g, sigma, Q))) == 0;
-    if (ok) {
-      ++nq;
-      qs = Q;
+    if (!P->general) {
+      if (P->s == 0) ok = ok && g_add(g, P->u.z, g_neg(g, Q)) == 0;
+      if (P->vv == 0) ok = ok && Q == 0;
+      if (P->t == 0) ok = ok && g_add(g, P->v.z, g_neg(g, g_signed(g, sigma, Q))) == 0;
+    } else {
+      // some U row, some contracted column and some V row exist at this Q
+      for (int k : {0, 1, 2}) {
+        bool any = false;
+        for (int64_t r = 0; r < gax[k].size && !any; ++r) any = gen_offset(gax[k], g, Q, r) >= 0;
+        ok = ok && any;
+      }
     }
+    if (ok) works.push_back(Q);
   }
-  pr.n_q = nq;
-  pr.q_single = nq == 1 ? qs : -1;
-  if (nq != 0 && nq != 1 && nq != (int)G) return bail(SYMCTR_ERR_ARGUMENT, "internal: Q set");
+  pr.n_q = (int)works.size();
+  pr.q_single = pr.n_q == 1 ? works[0] : -1;
+  pr.q0 = 0;
+  pr.q_step = 1;
+  if (pr.n_q > 1) {
+    // the batches: the progression q0 + b * step (mod G) through all of them
+    // (a coset of a subgroup of Z_G for a single cyclic factor; extra irreps
+    // of an irregular set carry absent rows only)
+    int64_t step = G;
+    for (int q : works) step = gcd64(step, (int64_t)(q - works[0] + G) % G);
+    pr.q0 = works[0];
+    pr.q_step = (int)step;
+    pr.n_q = (int)(G / step);
+    if (!P->general && pr.n_q != (int)G) return bail(SYMCTR_ERR_ARGUMENT, "internal: Q set");
+  }
 
   // ---- precision form and workspace ----
   P->prec = prec;
-  P->tensor_core = prec != SYMCTR_FP64 && nq > 0 && tensor_core_shape(pr);
+  P->tensor_core = prec != SYMCTR_FP64 && pr.n_q > 0 && tensor_core_shape(pr);
   P->n_slices = prec == SYMCTR_SPLIT_BF16 ? (n_slices == 0 ? 5 : n_slices) : 0;
   if (prec == SYMCTR_SPLIT_BF16 && P->n_slices < 2)
     return bail(SYMCTR_ERR_ARGUMENT, "split form needs at least 2 slices");
   P->kpad = round_up(pr.K, kKBlock);
   pr.q_base = 0;
-  if (P->tensor_core) {
+  if (P->tensor_core || (P->general && pr.n_q > 0)) {
     // the six offset tables [U rows | U cols | V rows | V cols | W rows | W cols],
     // each [n_q][extent]: the same function of the plan on every call
     const int64_t total = tables_entries(pr);
@@ -433,37 +632,59 @@ symctr_status build(const char* einsum, int n_moduli, const int32_t* moduli, con
     const int64_t ext[6] = {pr.M, pr.K, pr.N, pr.K, pr.M, pr.N};
     for (int k = 0; k < 6; ++k)
       for (int b = 0; b < pr.n_q; ++b)
-        for (int64_t r = 0; r < ext[k]; ++r) *t++ = axis_offset(*maps[k], pr.g, batch_irrep(pr, b), r);
+        for (int64_t r = 0; r < ext[k]; ++r)
+          *t++ = P->general ? gen_offset(gax[k], pr.g, batch_irrep(pr, b), r)
+                            : axis_offset(*maps[k], pr.g, batch_irrep(pr, b), r);
   }
   {
-    Layout full = make_layout(pr, P->tensor_core, prec, P->n_slices, P->kpad);
+    Layout full = make_layout(pr, P->tensor_core, P->general, prec, P->n_slices, P->kpad);
     if (!full.ok) return bail(SYMCTR_ERR_OVERFLOW, "aligned operand too large");
     P->ws_bytes = full.bytes;
     P->ws_bytes_min = full.bytes;
     if (P->tensor_core && pr.q_single < 0 && pr.n_q > 1) {
       Problem one = pr;
       one.n_q = 1;
-      P->ws_bytes_min = make_layout(one, true, prec, P->n_slices, P->kpad).bytes;
+      P->ws_bytes_min = make_layout(one, true, P->general, prec, P->n_slices, P->kpad).bytes;
+    }
+  }
+
+  // Single-read preparation (split form): an operand whose aligned rows are
+  // column-contiguous runs of at least 128 entries, at most kRowStreamMaxK
+  // long, every run start and row offset even (16-byte bulk copies), and
+  // large enough (>= 32 MB) to be bandwidth-bound.
+  if (P->tensor_core && prec == SYMCTR_SPLIT_BF16 && !P->general) {
+    const AxisMap* rows[2] = {&pr.u.rows, &pr.v.rows};
+    const AxisMap* cols[2] = {&pr.u.cols, &pr.v.cols};
+    const int64_t R[2] = {pr.M, pr.N};
+    const int64_t* rtab[2] = {P->htab.data(), P->htab.data() + (int64_t)pr.n_q * (pr.M + pr.K)};
+    const int64_t* ctab[2] = {P->htab.data() + (int64_t)pr.n_q * pr.M,
+                              P->htab.data() + (int64_t)pr.n_q * (pr.M + pr.K + pr.N)};
+    for (int op = 0; op < 2; ++op) {
+      const AxisMap& c = *cols[op];
+      const bool rows_contig = rows[op]->n > 0 && rows[op]->bstride[rows[op]->n - 1] == 1;
+      if (rows_contig || c.n == 0 || c.bstride[c.n - 1] != 1) continue;
+      int64_t L = c.D[c.n - 1];
+      for (int i = c.n - 2; i >= 0 && c.bstride[i] == L; --i) L *= c.D[i];
+      if (L < 128 || L % 2 != 0 || pr.K % L != 0 || pr.K > kRowStreamMaxK) continue;
+      if ((int64_t)pr.n_q * R[op] * pr.K < ((int64_t)4 << 20)) continue;
+      bool even = true;
+      for (int64_t i = 0; i < (int64_t)pr.n_q * R[op] && even; ++i) even = rtab[op][i] % 2 == 0;
+      for (int64_t b = 0; b < pr.n_q && even; ++b)
+        for (int64_t j = 0; j < pr.K && even; j += L) even = ctab[op][b * pr.K + j] % 2 == 0;
+      if (even) P->row_run[op] = L;
     }
   }
 
   if (with_backward) {
     // gU = einsum(lw,lv->lu)(gW, V): result carries U's law.
-    int8_t s_w[SYMCTR_MAX_ORDER], s_u[SYMCTR_MAX_ORDER], s_v[SYMCTR_MAX_ORDER];
-    int32_t z_w[SYMCTR_MAX_MODULI], z_u[SYMCTR_MAX_MODULI], z_v[SYMCTR_MAX_MODULI];
-    for (int i = 0; i < (int)lw.size(); ++i) s_w[i] = (int8_t)P->w.sign[i];
-    for (int i = 0; i < (int)lu.size(); ++i) s_u[i] = (int8_t)P->u.sign[i];
-    for (int i = 0; i < (int)lv.size(); ++i) s_v[i] = (int8_t)P->v.sign[i];
-    g_comps(g, P->w.z, z_w);
-    g_comps(g, P->u.z, z_u);
-    g_comps(g, P->v.z, z_v);
+    OwnedDesc dw(P->w, g), du(P->u, g), dv(P->v, g);
     std::string su_spec = lw + "," + lv + "->" + lu;
     std::string sv_spec = lu + "," + lw + "->" + lv;
-    symctr_status st = build(su_spec.c_str(), n_moduli, moduli, s_w, z_w, s_v, z_v, P->w.dim,
-                             P->v.dim, s_u, z_u, prec, P->n_slices, false, &P->bwd_u);
+    symctr_status st = build(su_spec.c_str(), n_moduli, moduli, dw.desc, dv.desc, du.signs, du.charge,
+                             prec, P->n_slices, false, &P->bwd_u);
     if (st != SYMCTR_OK) return bail(st, "backward plan (dU): " + g_detail);
-    st = build(sv_spec.c_str(), n_moduli, moduli, s_u, z_u, s_w, z_w, P->u.dim, P->w.dim, s_v,
-               z_v, prec, P->n_slices, false, &P->bwd_v);
+    st = build(sv_spec.c_str(), n_moduli, moduli, du.desc, dw.desc, dv.signs, dv.charge, prec,
+               P->n_slices, false, &P->bwd_v);
     if (st != SYMCTR_OK) {
       symctr_plan_destroy(P->bwd_u);
       P->bwd_u = nullptr;
@@ -525,6 +746,74 @@ symctr_status run_contract(const symctr_plan* P, const double* u, const double* 
   return s;
 }
 
+// Page-lock the host tables once, so that their copies are plain DMA reads and
+// small ones can be read in place (without it they are staged through pageable
+// memory, also correct).
+void pin_tables(const symctr_plan* P) {
+  std::call_once(P->pin_once, [P] {
+    if (!P->htab.empty() &&
+        cudaHostRegister((void*)P->htab.data(), P->htab.size() * sizeof(int64_t),
+                         cudaHostRegisterPortable | cudaHostRegisterMapped) == cudaSuccess) {
+      P->pinned = true;
+      void* d = nullptr;
+      if (cudaHostGetDevicePointer(&d, (void*)P->htab.data(), 0) == cudaSuccess) P->dtab = (const int64_t*)d;
+    }
+    cudaGetLastError();
+  });
+}
+
+// Whether the caller-attached device tables live on the current device.
+bool tables_attached(const symctr_plan* P) {
+  if (!P->dev_tab) return false;
+  int dev = -1;
+  return cudaGetDevice(&dev) == cudaSuccess && dev == P->dev_tab_device;
+}
+
+// The tables of one pass (batches q0 .. q0 + pc.n_q - 1): the attached device
+// copy, the small page-locked host tables read in place (reads over the
+// CPU-GPU link are not cached on the GPU, so larger tables, re-read by many
+// tiles, are copied to HBM instead), or a copy into the workspace at off_tab.
+symctr_status pass_tables(const symctr_plan* P, const Problem& pc, int q0, bool attached, char* base,
+                          uint64_t off_tab, cudaStream_t st, Tables* tab) {
+  const Problem& pr = P->prob;
+  const int64_t ext[6] = {pr.M, pr.K, pr.N, pr.K, pr.M, pr.N};
+  const int64_t* in_place = attached ? P->dev_tab
+                            : (P->dtab && P->htab.size() * sizeof(int64_t) <= kMappedTablesMax)
+                                ? P->dtab
+                                : nullptr;
+  if (in_place) {
+    const int64_t* src = in_place;
+    const int64_t** dst[6] = {&tab->urow, &tab->ucol, &tab->vrow, &tab->vcol, &tab->wrow, &tab->wcol};
+    for (int k = 0; k < 6; ++k) {
+      *dst[k] = src + (int64_t)q0 * ext[k];
+      src += (int64_t)pr.n_q * ext[k];
+    }
+    return SYMCTR_OK;
+  }
+  // one copy for a single pass, one per table otherwise
+  int64_t* t0 = (int64_t*)(base + off_tab);
+  tab->urow = t0;
+  tab->ucol = tab->urow + (int64_t)pc.n_q * pc.M;
+  tab->vrow = tab->ucol + (int64_t)pc.n_q * pc.K;
+  tab->vcol = tab->vrow + (int64_t)pc.n_q * pc.N;
+  tab->wrow = tab->vcol + (int64_t)pc.n_q * pc.K;
+  tab->wcol = tab->wrow + (int64_t)pc.n_q * pc.M;
+  cudaError_t e = cudaSuccess;
+  if (pc.n_q == pr.n_q) {
+    e = cudaMemcpyAsync(t0, P->htab.data(), P->htab.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st);
+  } else {
+    const int64_t* src = P->htab.data();
+    int64_t* dst = t0;
+    for (int k = 0; k < 6 && e == cudaSuccess; ++k) {
+      e = cudaMemcpyAsync(dst, src + (int64_t)q0 * ext[k], (size_t)(pc.n_q * ext[k]) * sizeof(int64_t),
+                          cudaMemcpyHostToDevice, st);
+      src += (int64_t)pr.n_q * ext[k];
+      dst += (int64_t)pc.n_q * ext[k];
+    }
+  }
+  return cuda_status(e, "offset tables");
+}
+
 symctr_status run_contract_body(const symctr_plan* P, const double* u, const double* v,
                                 double* w, void* ws, size_t ws_bytes, cudaStream_t st,
                                 const RunMode& mode) {
@@ -542,19 +831,33 @@ symctr_status run_contract_body(const symctr_plan* P, const double* u, const dou
   // header: error word (byte 0) and the prep kernel's grid-barrier counter (byte 64)
   cudaError_t e = mode.clear_err ? cudaMemsetAsync(err, 0, 128, st) : cudaMemsetAsync(base + 64, 0, 64, st);
   if (e != cudaSuccess) return cuda_status(e, "clear workspace header");
-  // Entries of W whose irrep Q carries no work are zero.
+  // Entries of W whose irrep Q carries no work are zero, and so are, in a
+  // general plan, its padding and the entries whose implicit sector has no
+  // solution: those plans zero W as a whole first.
   const int64_t fill_n = mode.fill_n < 0 ? P->numel_w : mode.fill_n;
-  if ((int64_t)pr.n_q * pr.M * pr.N < P->numel_w && fill_n > 0) {
+  if ((P->general || (int64_t)pr.n_q * pr.M * pr.N < P->numel_w) && fill_n > 0) {
     e = launch_fill_zero(w, fill_n, st);
     if (e != cudaSuccess) return cuda_status(e, "zero fill");
   }
   if (pr.n_q == 0) return SYMCTR_OK;
   if (P->prof) cudaEventRecord(P->ev[0], st);
+  const bool attached = tables_attached(P);
+  if (!attached && !P->htab.empty()) pin_tables(P);
   if (!P->tensor_core) {
     if (P->prof) cudaEventRecord(P->ev[1], st);
-    e = launch_gemm_f64(pr, u, v, w, st);
+    if (P->general) {
+      const Layout L = make_layout(pr, false, true, P->prec, P->n_slices, P->kpad);
+      Tables tab;
+      symctr_status s = pass_tables(P, pr, 0, attached, base, L.off_tab, st, &tab);
+      if (s != SYMCTR_OK) return s;
+      e = launch_gemm_f64(pr, u, v, w, &tab, st);
+    } else {
+      e = launch_gemm_f64(pr, u, v, w, nullptr, st);
+    }
     if (P->prof) cudaEventRecord(P->ev[2], st);
-    return cuda_status(e, "gemm_f64");
+    if (e != cudaSuccess) return cuda_status(e, "gemm_f64");
+    if (P->general && !attached && P->pinned) return mark_table_use(P, st);
+    return SYMCTR_OK;
   }
   // Q-streaming: as many irreps per pass as the workspace holds.
   int per_pass = pr.n_q;
@@ -563,30 +866,12 @@ symctr_status run_contract_body(const symctr_plan* P, const double* u, const dou
     for (int c = pr.n_q - 1; c >= 1 && per_pass == 0; --c) {
       Problem pc = pr;
       pc.n_q = c;
-      if (make_layout(pc, true, P->prec, P->n_slices, P->kpad).bytes <= ws_bytes) per_pass = c;
+      if (make_layout(pc, true, P->general, P->prec, P->n_slices, P->kpad).bytes <= ws_bytes) per_pass = c;
     }
     if (per_pass == 0) return fail(SYMCTR_ERR_WORKSPACE, "workspace smaller than workspace_bytes_min");
   }
   unsigned* barrier = (unsigned*)(base + 64);
   const bool split = P->prec == SYMCTR_SPLIT_BF16;
-  // the attached device tables, if they live on the current device
-  bool attached = false;
-  if (P->dev_tab) {
-    int dev = -1;
-    attached = cudaGetDevice(&dev) == cudaSuccess && dev == P->dev_tab_device;
-  }
-  // page-lock the host tables once, so that their copies are plain DMA reads
-  // (without it they are staged through pageable memory, also correct)
-  if (!attached) std::call_once(P->pin_once, [P] {
-    if (!P->htab.empty() &&
-        cudaHostRegister((void*)P->htab.data(), P->htab.size() * sizeof(int64_t),
-                         cudaHostRegisterPortable | cudaHostRegisterMapped) == cudaSuccess) {
-      P->pinned = true;
-      void* d = nullptr;
-      if (cudaHostGetDevicePointer(&d, (void*)P->htab.data(), 0) == cudaSuccess) P->dtab = (const int64_t*)d;
-    }
-    cudaGetLastError();
-  });
   for (int q0 = 0; q0 < pr.n_q; q0 += per_pass) {
     Problem pc = pr;
     if (per_pass < pr.n_q) {
@@ -597,56 +882,26 @@ symctr_status run_contract_body(const symctr_plan* P, const double* u, const dou
         if (e != cudaSuccess) return cuda_status(e, "clear barrier");
       }
     }
-    const Layout L = make_layout(pc, true, P->prec, P->n_slices, P->kpad);
+    const Layout L = make_layout(pc, true, P->general, P->prec, P->n_slices, P->kpad);
     Tables tab;
-    const int64_t ext[6] = {pr.M, pr.K, pr.N, pr.K, pr.M, pr.N};
-    const int64_t* in_place = attached ? P->dev_tab
-                              : (P->dtab && P->htab.size() * sizeof(int64_t) <= kMappedTablesMax)
-                                  ? P->dtab
-                                  : nullptr;
-    if (in_place) {
-      // the attached device copy, or small page-locked host tables read in
-      // place (reads over the CPU-GPU link are not cached on the GPU, so
-      // larger tables, re-read by many tiles, are copied to HBM instead)
-      const int64_t* src = in_place;
-      const int64_t** dst[6] = {&tab.urow, &tab.ucol, &tab.vrow, &tab.vcol, &tab.wrow, &tab.wcol};
-      for (int k = 0; k < 6; ++k) {
-        *dst[k] = src + (int64_t)q0 * ext[k];
-        src += (int64_t)pr.n_q * ext[k];
-      }
-    } else {
-      // copy this pass's part into the workspace: one copy for a single pass,
-      // one per table otherwise
-      int64_t* t0 = (int64_t*)(base + L.off_tab);
-      tab.urow = t0;
-      tab.ucol = tab.urow + (int64_t)pc.n_q * pc.M;
-      tab.vrow = tab.ucol + (int64_t)pc.n_q * pc.K;
-      tab.vcol = tab.vrow + (int64_t)pc.n_q * pc.N;
-      tab.wrow = tab.vcol + (int64_t)pc.n_q * pc.K;
-      tab.wcol = tab.wrow + (int64_t)pc.n_q * pc.M;
-      if (pc.n_q == pr.n_q) {
-        e = cudaMemcpyAsync(t0, P->htab.data(), P->htab.size() * sizeof(int64_t),
-                            cudaMemcpyHostToDevice, st);
-      } else {
-        const int64_t* src = P->htab.data();
-        int64_t* dst = t0;
-        for (int k = 0; k < 6 && e == cudaSuccess; ++k) {
-          e = cudaMemcpyAsync(dst, src + (int64_t)q0 * ext[k], (size_t)(pc.n_q * ext[k]) * sizeof(int64_t),
-                              cudaMemcpyHostToDevice, st);
-          src += (int64_t)pr.n_q * ext[k];
-          dst += (int64_t)pc.n_q * ext[k];
-        }
-      }
-      if (e != cudaSuccess) return cuda_status(e, "offset tables");
-    }
+    symctr_status s = pass_tables(P, pc, q0, attached, base, L.off_tab, st, &tab);
+    if (s != SYMCTR_OK) return s;
     unsigned long long* acc = L.ksplit > 1 ? (unsigned long long*)(base + L.off_acc) : nullptr;
     const int64_t acc_n = L.ksplit > 1 ? (int64_t)pc.n_q * pc.M * pc.N : 0;
     int32_t* ea = split ? (int32_t*)(base + L.off_ea) : nullptr;
     int32_t* eb = split ? (int32_t*)(base + L.off_eb) : nullptr;
     int32_t* part = split && L.off_part ? (int32_t*)(base + L.off_part) : nullptr;
+    // operands with row runs take the single-read kernel (real data only)
+    const bool rs[2] = {split && pr.es == 1 && P->row_run[0] > 0, split && pr.es == 1 && P->row_run[1] > 0};
     e = launch_prep(pc, tab, split, P->n_slices, u, v, base + L.off_a, base + L.off_b, ea, eb, part,
-                    P->kpad, err, barrier, acc, acc_n, st);
+                    P->kpad, err, barrier, acc, acc_n, rs, st);
     if (e != cudaSuccess) return cuda_status(e, "operand preparation");
+    for (int op = 0; op < 2; ++op) {
+      if (!rs[op]) continue;
+      e = launch_rowstream(pc, tab, op, P->n_slices, P->row_run[op], op == 0 ? u : v,
+                           base + (op == 0 ? L.off_a : L.off_b), op == 0 ? ea : eb, P->kpad, err, st);
+      if (e != cudaSuccess) return cuda_status(e, "operand preparation (single read)");
+    }
     if (P->prof && q0 == 0) cudaEventRecord(P->ev[1], st);
     if (split)
       e = launch_gemm_split(pc, tab, P->n_slices, (const uint16_t*)(base + L.off_a),
@@ -720,8 +975,37 @@ symctr_status symctr_plan_create(const char* einsum, int n_moduli, const int32_t
                                  const int64_t* dims_u, const int64_t* dims_v,
                                  const int8_t* signs_w_or_null, const int32_t* charge_w_or_null,
                                  symctr_precision prec, int n_slices, symctr_plan** out) {
-  return build(einsum, n_moduli, moduli, signs_u, charge_u, signs_v, charge_v, dims_u, dims_v,
-               signs_w_or_null, charge_w_or_null, prec, n_slices, true, out);
+  OpDesc du, dv;
+  du.signs = signs_u;
+  du.charge = charge_u;
+  du.dims = dims_u;
+  dv.signs = signs_v;
+  dv.charge = charge_v;
+  dv.dims = dims_v;
+  return build(einsum, n_moduli, moduli, du, dv, signs_w_or_null, charge_w_or_null, prec, n_slices,
+               true, out);
+}
+
+symctr_status symctr_plan_create_general(const char* einsum, int n_moduli, const int32_t* moduli,
+                                         const symctr_operand* u, const symctr_operand* v,
+                                         const int8_t* signs_w_or_null,
+                                         const int32_t* charge_w_or_null, symctr_precision prec,
+                                         int n_slices, symctr_plan** out) {
+  if (out) *out = nullptr;
+  if (!u || !v) return fail(SYMCTR_ERR_NULLPTR, "NULL operand descriptor");
+  OpDesc du, dv;
+  du.signs = u->signs;
+  du.charge = u->charge;
+  du.dims = u->dims;
+  du.sectors = u->sectors;
+  du.sector_dims = u->sector_dims;
+  dv.signs = v->signs;
+  dv.charge = v->charge;
+  dv.dims = v->dims;
+  dv.sectors = v->sectors;
+  dv.sector_dims = v->sector_dims;
+  return build(einsum, n_moduli, moduli, du, dv, signs_w_or_null, charge_w_or_null, prec, n_slices,
+               true, out);
 }
 
 symctr_status symctr_plan_query(const symctr_plan* P, symctr_plan_info* o) {
@@ -767,6 +1051,11 @@ symctr_status symctr_plan_query(const symctr_plan* P, symctr_plan_info* o) {
   o->workspace_bytes_backward = wb;
   o->table_bytes = all_table_bytes(P);
   o->tensor_core = P->tensor_core ? 1 : 0;
+  o->general = P->general ? 1 : 0;
+  o->q_first = pr.q_single >= 0 ? pr.q_single : pr.q0;
+  o->q_step = pr.q_single >= 0 ? 0 : pr.q_step;
+  for (int i = 0; i < P->w.order(); ++i) o->sectors_w[i] = P->w.H[i];
+  o->single_read_prep = (P->row_run[0] > 0 ? 1 : 0) | (P->row_run[1] > 0 ? 2 : 0);
   return SYMCTR_OK;
 }
 
@@ -788,23 +1077,43 @@ symctr_status symctr_plan_attach_tables(symctr_plan* P, void* tables, size_t byt
 
 symctr_status symctr_align(const symctr_plan* P, int operand, int direction, const double* src,
                            double* dst, void* stream) {
-  if (!P || !src || !dst) return fail(SYMCTR_ERR_NULLPTR, "NULL argument");
+  if (!P) return fail(SYMCTR_ERR_NULLPTR, "NULL plan");
   if (operand < 0 || operand > 2 || (direction != 1 && direction != -1))
     return fail(SYMCTR_ERR_ARGUMENT, "operand in {0,1,2}, direction in {+1,-1}");
   const Problem& pr = P->prob;
   cudaStream_t st = (cudaStream_t)stream;
+  const int64_t covered = operand == 0 ? (int64_t)pr.n_q * pr.M * pr.K
+                          : operand == 1 ? (int64_t)pr.n_q * pr.N * pr.K
+                                         : (int64_t)pr.n_q * pr.M * pr.N;
+  const int64_t total = operand == 0 ? P->numel_u : operand == 1 ? P->numel_v : P->numel_w;
+  // an empty side (no irrep carries work: the aligned form has no entries) may be NULL
+  if ((!src && (direction > 0 ? total : covered) > 0) || (!dst && (direction > 0 ? covered : total) > 0))
+    return fail(SYMCTR_ERR_NULLPTR, "NULL argument");
   if (direction == -1) {
-    int64_t covered = operand == 0 ? (int64_t)pr.n_q * pr.M * pr.K
-                    : operand == 1 ? (int64_t)pr.n_q * pr.N * pr.K
-                                   : (int64_t)pr.n_q * pr.M * pr.N;
-    int64_t total = operand == 0 ? P->numel_u : operand == 1 ? P->numel_v : P->numel_w;
-    if (covered < total) {
+    if (P->general || covered < total) {
       cudaError_t e = launch_fill_zero(dst, total, st);
       if (e != cudaSuccess) return cuda_status(e, "zero fill");
     }
   }
   if (pr.n_q == 0) return SYMCTR_OK;
-  return cuda_status(launch_align_f64(pr, operand, direction, src, dst, st), "align");
+  if (!P->general)
+    return cuda_status(launch_align_f64(pr, operand, direction, src, dst, nullptr, st), "align");
+  // general plans: the index maps are the tables (attached, else the
+  // page-locked host tables read in place)
+  Tables tab;
+  const bool attached = tables_attached(P);
+  if (!attached) pin_tables(P);
+  const int64_t* t0 = attached ? P->dev_tab : P->dtab;
+  if (!t0) return fail(SYMCTR_ERR_CUDA, "offset tables could not be mapped; attach them first");
+  tab.urow = t0;
+  tab.ucol = tab.urow + (int64_t)pr.n_q * pr.M;
+  tab.vrow = tab.ucol + (int64_t)pr.n_q * pr.K;
+  tab.vcol = tab.vrow + (int64_t)pr.n_q * pr.N;
+  tab.wrow = tab.vcol + (int64_t)pr.n_q * pr.K;
+  tab.wcol = tab.wrow + (int64_t)pr.n_q * pr.M;
+  symctr_status r = cuda_status(launch_align_f64(pr, operand, direction, src, dst, &tab, st), "align");
+  if (r == SYMCTR_OK && !attached) r = mark_table_use(P, st);
+  return r;
 }
 
 symctr_status symctr_contract(const symctr_plan* P, const double* u, const double* v, double* w,

@@ -109,7 +109,14 @@ struct Problem {
   GroupDesc g;
   int n_q;            // batches (irreps carrying work)
   int q_single;       // the irrep of a single-irrep problem, else -1
-  int q_base;         // first irrep of batch 0 when q_single < 0 (Q-streaming)
+  int q_base;         // batch index of this pass's batch 0 (Q-streaming)
+  int q0 = 0;         // batch b is irrep q0 + b * q_step (mod G) when q_single < 0
+  int q_step = 1;
+  // General symmetry (sub-group coefficients or padded sectors): the index
+  // maps live only in the offset tables, where an absent aligned row or
+  // column (an implicit-sector equation without a solution, or a padding
+  // position) has offset -1; kernels read it as zero and never store it.
+  int general = 0;
   int64_t M, N, K;
   OperandMap u, v, w; // U: rows = free-U, cols = contracted; V: rows = free-V, cols = contracted;
                       // W: rows = free-U, cols = free-V
@@ -137,7 +144,9 @@ __device__ __forceinline__ void store_w(const Problem& p, double* dst, double x)
 }
 #endif
 
-SC_HD int batch_irrep(const Problem& p, int b) { return p.q_single >= 0 ? p.q_single : p.q_base + b; }
+SC_HD int batch_irrep(const Problem& p, int b) {
+  return p.q_single >= 0 ? p.q_single : (p.q0 + (p.q_base + b) * p.q_step) % p.g.order;
+}
 
 // Offset tables of the aligned forms for one contraction pass: row_off /
 // col_off of every (batch, index), int64.  They are computed once per plan on
@@ -191,15 +200,25 @@ constexpr int kKChunk = 64;         // K between exact flushes of the top accumu
 extern thread_local long long g_kernel_launches;
 
 // ---- kernel launchers (return cudaError_t of the launch) ----
+// `tables` (general plans only, else NULL): the offset tables of all batches.
 cudaError_t launch_align_f64(const Problem& p, int operand, int direction, const double* src,
-                             double* dst, cudaStream_t st);
+                             double* dst, const Tables* tables, cudaStream_t st);
 cudaError_t launch_gemm_f64(const Problem& p, const double* u, const double* v, double* w,
-                            cudaStream_t st);
+                            const Tables* tables, cudaStream_t st);
 cudaError_t launch_fill_zero(double* w, int64_t n, cudaStream_t st);
+// skip[op]: operand op is prepared by launch_rowstream instead (NULL: neither)
 cudaError_t launch_prep(const Problem& p, const Tables& t, bool split, int n_slices,
                         const double* u, const double* v, void* ua, void* va, int32_t* eu,
                         int32_t* ev, int32_t* partials, int64_t kpad, unsigned* err, unsigned* barrier,
-                        unsigned long long* zero64, int64_t zero64_n, cudaStream_t st);
+                        unsigned long long* zero64, int64_t zero64_n, const bool* skip,
+                        cudaStream_t st);
+// Single-read split-form preparation of operand op (0 = U, 1 = V) whose
+// aligned rows are runs of `run` contiguous reduced-form entries and at most
+// kRowStreamMaxK long (plan-time eligibility: row_run in plan.cpp).
+constexpr int64_t kRowStreamMaxK = 8192;
+cudaError_t launch_rowstream(const Problem& p, const Tables& t, int op, int n_slices, int64_t run,
+                             const double* src, void* slices, int32_t* exps, int64_t kpad,
+                             unsigned* err, cudaStream_t st);
 cudaError_t launch_bounded_wait_selftest(unsigned* err, long long limit_cycles, cudaStream_t st);
 cudaError_t launch_gemm_split(const Problem& p, const Tables& t, int n_slices, const uint16_t* us,
                               const uint16_t* vs, const int32_t* eu, const int32_t* ev,
@@ -237,7 +256,11 @@ symctr_status record_error(symctr_status st, const char* detail);
 // up once per device, defined in static_scratch.cu), or NULL with *st set.
 void* static_scratch_address(symctr_status* st);
 
-// Shape test: the tensor-core forms need a GEMM-shaped problem.
-inline bool tensor_core_shape(const Problem& p) { return p.M >= 32 && p.N >= 32 && p.K >= 16; }
+// Shape test of the tensor-core forms: both output sides at least 8 long.
+// Below that the aligned GEMM is a GEMV or an outer product; the float64
+// kernels then read each long-side entry once, while the split form would
+// also write its slices and fill 128-row MMA tiles with a few rows.  Any K
+// (padded to 32 with zeros) takes the tensor cores.
+inline bool tensor_core_shape(const Problem& p) { return p.M >= 8 && p.N >= 8 && p.K >= 1; }
 
 }  // namespace symctr

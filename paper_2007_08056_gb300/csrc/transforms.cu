@@ -29,6 +29,7 @@ __host__ inline bool rows_fast(const OperandMap& m) {
 // even one sits at an even offset: the innermost column digit has stride 1 and
 // an even extent, and every other stride of rows and columns is even.
 __host__ inline bool pairs_aligned(const OperandMap& m) {
+  // (never asked for general plans: a padded column pair may be half absent)
   const AxisMap& c = m.cols;
   if (c.n == 0 || c.bstride[c.n - 1] != 1 || (c.D[c.n - 1] & 1)) return false;
   for (int i = 0; i < c.n; ++i) {
@@ -51,6 +52,8 @@ __global__ void fill_zero_kernel(double* __restrict__ w, int64_t n) {
 // accessed along their contiguous axis.
 __global__ void __launch_bounds__(THREADS) align_kernel(Problem p, OperandMap m, int64_t R,
                                                         int64_t Cn, int direction, bool fast_rows,
+                                                        const int64_t* __restrict__ rtab,
+                                                        const int64_t* __restrict__ ctab,
                                                         const double* __restrict__ src,
                                                         double* __restrict__ dst) {
   __shared__ double tile[TILE][TILE + 1];
@@ -64,19 +67,21 @@ __global__ void __launch_bounds__(THREADS) align_kernel(Problem p, OperandMap m,
     int64_t r0 = (rem / ct) * TILE, c0 = (rem % ct) * TILE;
     int Q = batch_irrep(p, (int)b);
     __syncthreads();
+    // general plans: offsets from the tables, -1 marking an absent row/column
     if (threadIdx.x < TILE) {
       int64_t r = r0 + threadIdx.x;
-      roff[threadIdx.x] = r < R ? axis_offset(m.rows, p.g, Q, r) : 0;
+      roff[threadIdx.x] = r < R ? (rtab ? rtab[b * R + r] : axis_offset(m.rows, p.g, Q, r)) : 0;
     } else if (threadIdx.x < 2 * TILE) {
       int64_t c = c0 + threadIdx.x - TILE;
-      coff[threadIdx.x - TILE] = c < Cn ? axis_offset(m.cols, p.g, Q, c) : 0;
+      coff[threadIdx.x - TILE] = c < Cn ? (ctab ? ctab[b * Cn + c] : axis_offset(m.cols, p.g, Q, c)) : 0;
     }
     __syncthreads();
     const int64_t abase = (b * R) * Cn;
     if (direction > 0) {
       for (int k = ty; k < TILE; k += THREADS / 32) {
         int rr = fast_rows ? tx : k, cc = fast_rows ? k : tx;
-        if (r0 + rr < R && c0 + cc < Cn) tile[rr][cc] = src[roff[rr] + coff[cc]];
+        if (r0 + rr < R && c0 + cc < Cn)
+          tile[rr][cc] = (roff[rr] >= 0 && coff[cc] >= 0) ? src[roff[rr] + coff[cc]] : 0.0;
       }
       __syncthreads();
       for (int k = ty; k < TILE; k += THREADS / 32) {
@@ -89,7 +94,8 @@ __global__ void __launch_bounds__(THREADS) align_kernel(Problem p, OperandMap m,
       __syncthreads();
       for (int k = ty; k < TILE; k += THREADS / 32) {
         int rr = fast_rows ? tx : k, cc = fast_rows ? k : tx;
-        if (r0 + rr < R && c0 + cc < Cn) dst[roff[rr] + coff[cc]] = tile[rr][cc];
+        if (r0 + rr < R && c0 + cc < Cn && roff[rr] >= 0 && coff[cc] >= 0)
+          dst[roff[rr] + coff[cc]] = tile[rr][cc];
       }
     }
   }
@@ -228,6 +234,7 @@ struct PrepArgs {
   unsigned* barrier;
   unsigned long long* zero64;  // split-K partial sums, zeroed here
   int64_t zero64_n;
+  bool skip[2];              // operands prepared by the single-read kernel instead
 };
 
 __device__ __forceinline__ void operand_dims(const Problem& p, int op, int64_t* R, int64_t* Cn) {
@@ -265,6 +272,8 @@ __device__ void scan_tile(const PrepArgs& a, int op, uint32_t tile, int64_t* rof
     roff[threadIdx.x] = r < R ? rtab[(int64_t)b * R + r] : 0;
     rmax[threadIdx.x] = 0;
   }
+  // general plans: an absent row (offset -1) or column reads as zero
+  const bool masked = p.general != 0;
   constexpr int PER = SCAN_COLS / (THREADS / 32);
   constexpr int RPW = TILE / (THREADS / 32);   // rows per warp (column paths)
   uint64_t mx = 0;          // fast rows: this thread's row (tx)
@@ -281,7 +290,7 @@ __device__ void scan_tile(const PrepArgs& a, int op, uint32_t tile, int64_t* rof
       const int64_t* co = coff + (c0 - sb);
       if (fast_rows) {
         // lanes walk rows (contiguous), warps walk columns
-        const bool rok = r0 + tx < R;
+        const bool rok = r0 + tx < R && (!masked || roff[tx] >= 0);
         const double* rowp = src + (int64_t)p.es * roff[tx];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -289,7 +298,7 @@ __device__ void scan_tile(const PrepArgs& a, int op, uint32_t tile, int64_t* rof
 #pragma unroll
           for (int i = 0; i < PER / 2; ++i) {
             const int cc = ty + (h * (PER / 2) + i) * (THREADS / 32);
-            x[i] = (rok && c0 + cc < se) ? rowp[(int64_t)p.es * co[cc]] : 0.0;
+            x[i] = (rok && c0 + cc < se && (!masked || co[cc] >= 0)) ? rowp[(int64_t)p.es * co[cc]] : 0.0;
           }
 #pragma unroll
           for (int i = 0; i < PER / 2; ++i) mx = max(mx, abs_bits(x[i]));
@@ -318,13 +327,13 @@ __device__ void scan_tile(const PrepArgs& a, int op, uint32_t tile, int64_t* rof
 #pragma unroll
         for (int h = 0; h < RPW; ++h) {
           const int rr = ty + h * (THREADS / 32);
-          const bool rok = r0 + rr < R;
+          const bool rok = r0 + rr < R && (!masked || roff[rr] >= 0);
           const double* rowp = src + (int64_t)p.es * roff[rr];
           double x[SCAN_COLS / 32];
 #pragma unroll
           for (int i = 0; i < SCAN_COLS / 32; ++i) {
             const int cc = tx + 32 * i;
-            x[i] = (rok && c0 + cc < se) ? rowp[(int64_t)p.es * co[cc]] : 0.0;
+            x[i] = (rok && c0 + cc < se && (!masked || co[cc] >= 0)) ? rowp[(int64_t)p.es * co[cc]] : 0.0;
           }
 #pragma unroll
           for (int i = 0; i < SCAN_COLS / 32; ++i) mxr[h] = max(mxr[h], abs_bits(x[i]));
@@ -482,6 +491,7 @@ __device__ void slice_unit(const PrepArgs& a, int op, uint32_t unit, int64_t* ro
     }
     return;
   }
+  const bool masked = p.general != 0;   // absent rows/columns (offset -1) read as zero
   if (!fast_rows) {
     // lanes walk column pairs, warps walk rows; no shared-memory transpose
     const bool pair = a.pair_ok[op];
@@ -505,16 +515,16 @@ __device__ void slice_unit(const PrepArgs& a, int op, uint32_t unit, int64_t* ro
             x0 = v2.x;
             x1 = v2.y;
           }
-        } else {
-          if (c < Cn) x0 = rowp[(int64_t)p.es * co0];
-          if (c + 1 < Cn) x1 = rowp[(int64_t)p.es * co1];
+        } else if (!masked || roff[rr] >= 0) {
+          if (c < Cn && (!masked || co0 >= 0)) x0 = rowp[(int64_t)p.es * co0];
+          if (c + 1 < Cn && (!masked || co1 >= 0)) x1 = rowp[(int64_t)p.es * co1];
         }
         put_pair<S>(a, op, x0, x1, S > 0 ? rk0[rr] : 0, (brow + r) * kpad + c, slice_stride);
       }
     }
     return;
   }
-  const bool rok = r0 + tx < R;
+  const bool rok = r0 + tx < R && (!masked || roff[tx] >= 0);
   const double* rowp = src + (int64_t)p.es * roff[tx];
 #pragma unroll 1
   for (int sub = 0; sub < SLICE_GROUP; ++sub) {
@@ -526,7 +536,8 @@ __device__ void slice_unit(const PrepArgs& a, int op, uint32_t unit, int64_t* ro
 #pragma unroll
       for (int i = 0; i < SLICE_COLS / (THREADS / 32); ++i) {
         const int cc = ty + i * (THREADS / 32);
-        x[i] = (rok && c0 + cc < Cn) ? rowp[(int64_t)p.es * coff[sub * SLICE_COLS + cc]] : 0.0;
+        const int64_t cof = coff[sub * SLICE_COLS + cc];
+        x[i] = (rok && c0 + cc < Cn && (!masked || cof >= 0)) ? rowp[(int64_t)p.es * cof] : 0.0;
       }
 #pragma unroll
       for (int i = 0; i < SLICE_COLS / (THREADS / 32); ++i) tilebuf[tx][ty + i * (THREADS / 32)] = x[i];
@@ -560,8 +571,8 @@ __global__ void __launch_bounds__(THREADS, 4) prep_kernel(PrepArgs a) {
   const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   for (int64_t i = gtid; i < a.zero64_n; i += gthreads) a.zero64[i] = 0ull;
   if (S > 0) {
-    const uint32_t tiles0 = (uint32_t)(((p.M + TILE - 1) / TILE) * a.parts * p.n_q);
-    const uint32_t tiles1 = (uint32_t)(((p.N + TILE - 1) / TILE) * a.parts * p.n_q);
+    const uint32_t tiles0 = a.skip[0] ? 0u : (uint32_t)(((p.M + TILE - 1) / TILE) * a.parts * p.n_q);
+    const uint32_t tiles1 = a.skip[1] ? 0u : (uint32_t)(((p.N + TILE - 1) / TILE) * a.parts * p.n_q);
     for (uint32_t t = blockIdx.x; t < tiles0 + tiles1; t += gridDim.x) {
       const int op = t < tiles0 ? 0 : 1;
       scan_tile<S>(a, op, op == 0 ? t : t - tiles0, roff, coff, rmax);
@@ -576,11 +587,163 @@ __global__ void __launch_bounds__(THREADS, 4) prep_kernel(PrepArgs a) {
     for (int op = 0; op < 2; ++op) {
       int64_t R, Cn;
       operand_dims(p, op, &R, &Cn);
-      units[op] = (uint32_t)(((R + TILE - 1) / TILE) * ((a.kpad + UCOLS - 1) / UCOLS) * p.n_q);
+      units[op] = a.skip[op] ? 0u : (uint32_t)(((R + TILE - 1) / TILE) * ((a.kpad + UCOLS - 1) / UCOLS) * p.n_q);
     }
     for (uint32_t t = blockIdx.x; t < units[0] + units[1]; t += gridDim.x) {
       const int op = t < units[0] ? 0 : 1;
       slice_unit<S>(a, op, op == 0 ? t : t - units[0], roff, coff, rk0, tilebuf);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Single-read operand preparation (split form).  The exponent of an aligned
+// row must be known before any of its digits, so the two-phase kernel above
+// reads each operand twice.  When a row is made of runs of L contiguous
+// reduced-form entries (the column map's innermost block digits have
+// unit-stride layout) and fits in shared memory, one CTA per SM instead
+// streams whole rows into shared memory with bulk copies (one per run, on an
+// mbarrier, kRsBufs rows in flight), takes the row maximum there and writes
+// the row's digits from there: every operand entry crosses HBM once.
+// ---------------------------------------------------------------------------
+constexpr int RS_THREADS = 256;
+constexpr int kRsBufs = 3;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+struct RowStreamArgs {
+  int64_t R, K, kpad, L;    // rows per batch, columns, padded columns, run length
+  int n_q;
+  const int64_t* rtab;      // [n_q][R] row offsets
+  const int64_t* ctab;      // [n_q][K] column offsets (run starts read at multiples of L)
+  const double* src;
+  uint32_t* dst;            // BF16 digit pairs: [S][n_q][R][kpad / 2]
+  int64_t slice_stride;     // n_q * R * kpad (elements)
+  int32_t* exps;            // [n_q][R] biased row exponents
+  unsigned* err;
+};
+
+// Bounded wait on a bulk-copy barrier (about 2 s of SM clock); false on expiry.
+__device__ __forceinline__ bool rs_wait(uint64_t* bar, uint32_t parity) {
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(100000u)
+        : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > 4000000000ll) return false;
+  }
+}
+
+// Warp 0: queue the bulk copies of row g into buffer `slot` (lane 0 posts the
+// byte count first; lanes then issue one run each, 32 at a time).
+__device__ __forceinline__ void rs_issue(const RowStreamArgs& a, int64_t g, double* buf, uint64_t* bar,
+                                         int lane) {
+  const int64_t b = g / a.R;
+  const int64_t roff = a.rtab[g];
+  if (lane == 0)
+    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"((uint32_t)(a.K * 8))
+                 : "memory");
+  __syncwarp();
+  const int64_t nruns = a.K / a.L;
+  for (int64_t j = lane; j < nruns; j += 32) {
+    const double* from = a.src + roff + a.ctab[b * a.K + j * a.L];
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(buf + j * a.L)),
+        "l"(from), "r"((uint32_t)(a.L * 8)), "r"(smem_u32(bar))
+        : "memory");
+  }
+}
+
+template <int S>
+__global__ void __launch_bounds__(RS_THREADS, 1) rowstream_kernel(const __grid_constant__ RowStreamArgs a) {
+  extern __shared__ __align__(128) uint8_t rs_smem[];
+  __shared__ __align__(8) uint64_t bars[kRsBufs];
+  __shared__ unsigned long long red[RS_THREADS / 32];
+  __shared__ int32_t key_s;
+  __shared__ int abort_s;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t buf_elems = (a.K + 15) / 16 * 16;   // 128-byte aligned buffers
+  double* bufs = (double*)rs_smem;
+  const int64_t rows = (int64_t)a.n_q * a.R;
+  if (tid == 0) {
+    for (int i = 0; i < kRsBufs; ++i)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[i])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    abort_s = 0;
+  }
+  __syncthreads();
+  if (warp == 0)
+    for (int s = 0; s < kRsBufs; ++s) {
+      const int64_t g = blockIdx.x + (int64_t)s * gridDim.x;
+      if (g < rows) rs_issue(a, g, bufs + s * buf_elems, &bars[s], lane);
+    }
+  int it = 0;
+  int64_t g = blockIdx.x;
+  for (; g < rows; g += gridDim.x, ++it) {
+    const int slot = it % kRsBufs;
+    const uint32_t parity = (uint32_t)(it / kRsBufs) & 1u;
+    // every thread observes the copies' completion on the barrier
+    const bool ok = rs_wait(&bars[slot], parity);
+    if (!ok && lane == 0) atomicOr(a.err, (unsigned)DEVERR_TIMEOUT);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) abort_s = 1;
+      __syncthreads();
+      break;
+    }
+    const double* row = bufs + slot * buf_elems;
+    // the row maximum (integer max of the IEEE bit patterns)
+    uint64_t mx = 0;
+    for (int64_t c = tid; c < a.K; c += RS_THREADS) mx = max(mx, abs_bits(row[c]));
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, (uint64_t)__shfl_xor_sync(0xffffffffu, (unsigned long long)mx, o));
+    if (lane == 0) red[warp] = mx;
+    __syncthreads();
+    if (tid == 0) {
+      uint64_t m = 0;
+      for (int w = 0; w < RS_THREADS / 32; ++w) m = max(m, (uint64_t)red[w]);
+      unsigned bad = 0;
+      const int32_t key = row_key<S>(m, bad);
+      if (bad) atomicOr(a.err, (unsigned)DEVERR_NONFINITE);
+      a.exps[g] = key;
+      key_s = key;
+    }
+    __syncthreads();
+    const int k0 = row_k0(key_s, S);
+    // the digits, two adjacent columns per thread and step (zeros beyond K)
+    uint32_t* d = a.dst + g * (a.kpad / 2);
+    for (int64_t c2 = tid; c2 < a.kpad / 2; c2 += RS_THREADS) {
+      const int64_t c = 2 * c2;
+      double x0 = 0.0, x1 = 0.0;
+      if (c + 1 < a.K) {
+        const double2 v2 = *reinterpret_cast<const double2*>(row + c);
+        x0 = v2.x;
+        x1 = v2.y;
+      } else if (c < a.K) {
+        x0 = row[c];
+      }
+      put_slices_pair<S>(x0, x1, k0, d + c2, a.slice_stride / 2);
+    }
+    __syncthreads();   // every thread is done with this buffer
+    const int64_t gn = g + (int64_t)kRsBufs * gridDim.x;
+    if (warp == 0 && gn < rows) rs_issue(a, gn, bufs + slot * buf_elems, &bars[slot], lane);
+  }
+  // the GEMM behind this kernel may start its launch
+  asm volatile("griddepcontrol.launch_dependents;");
+  if (abort_s && tid == 0) {
+    // let the copies still in flight land before the CTA exits (bounded)
+    for (int k = it; k < it + kRsBufs; ++k) {
+      const int64_t gk = blockIdx.x + (int64_t)k * gridDim.x;
+      if (gk >= rows) break;
+      rs_wait(&bars[k % kRsBufs], (uint32_t)(k / kRsBufs) & 1u);
     }
   }
 }
@@ -613,13 +776,65 @@ cudaError_t launch_fill_zero(double* w, int64_t n, cudaStream_t st) {
 }
 
 cudaError_t launch_align_f64(const Problem& p, int operand, int direction, const double* src,
-                             double* dst, cudaStream_t st) {
+                             double* dst, const Tables* t, cudaStream_t st) {
   int64_t R, Cn;
   operand_extent(p, operand, &R, &Cn);
   if (R == 0 || Cn == 0 || p.n_q == 0) return cudaSuccess;
   const OperandMap& m = operand_map(p, operand);
+  const int64_t* rtab = t ? (operand == 0 ? t->urow : operand == 1 ? t->vrow : t->wrow) : nullptr;
+  const int64_t* ctab = t ? (operand == 0 ? t->ucol : operand == 1 ? t->vcol : t->wcol) : nullptr;
   int64_t tiles = ((R + TILE - 1) / TILE) * ((Cn + TILE - 1) / TILE) * p.n_q;
-  align_kernel<<<grid_for(tiles), THREADS, 0, st>>>(p, m, R, Cn, direction, rows_fast(m), src, dst);
+  align_kernel<<<grid_for(tiles), THREADS, 0, st>>>(p, m, R, Cn, direction, rows_fast(m), rtab, ctab,
+                                                     src, dst);
+  ++g_kernel_launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rowstream(const Problem& p, const Tables& t, int op, int n_slices, int64_t run,
+                             const double* src, void* slices, int32_t* exps, int64_t kpad,
+                             unsigned* err, cudaStream_t st) {
+  if (n_slices < 2 || n_slices > kMaxSlices || p.es != 1 || p.general) return cudaErrorInvalidValue;
+  const int64_t R = op == 0 ? p.M : p.N, K = p.K;
+  if (run <= 0 || K % run != 0 || (run * 8) % 16 != 0 || K > kRowStreamMaxK) return cudaErrorInvalidValue;
+  void (*kern)(RowStreamArgs) = nullptr;
+  switch (n_slices) {
+    case 2: kern = rowstream_kernel<2>; break;
+    case 3: kern = rowstream_kernel<3>; break;
+    case 4: kern = rowstream_kernel<4>; break;
+    case 5: kern = rowstream_kernel<5>; break;
+    default: kern = rowstream_kernel<6>; break;
+  }
+  const size_t smem = (size_t)kRsBufs * ((K + 15) / 16 * 16) * sizeof(double);
+  // the attribute is set once per instance and device (kept per host thread)
+  thread_local size_t set_for[kMaxSlices + 1][16] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 16) return cudaErrorInvalidDevice;
+  if (set_for[n_slices][dev] < smem) {
+    e = cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    set_for[n_slices][dev] = smem;
+  }
+  int sms = 0;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  RowStreamArgs a;
+  a.R = R;
+  a.K = K;
+  a.kpad = kpad;
+  a.L = run;
+  a.n_q = p.n_q;
+  a.rtab = op == 0 ? t.urow : t.vrow;
+  a.ctab = op == 0 ? t.ucol : t.vcol;
+  a.src = src;
+  a.dst = (uint32_t*)slices;
+  a.slice_stride = (int64_t)p.n_q * R * kpad;
+  a.exps = exps;
+  a.err = err;
+  const int64_t rows = (int64_t)p.n_q * R;
+  const int grid = (int)(rows < sms ? (rows > 0 ? rows : 1) : sms);
+  kern<<<grid, RS_THREADS, smem, st>>>(a);
   ++g_kernel_launches;
   return cudaGetLastError();
 }
@@ -627,7 +842,8 @@ cudaError_t launch_align_f64(const Problem& p, int operand, int direction, const
 cudaError_t launch_prep(const Problem& p, const Tables& t, bool split, int n_slices,
                         const double* u, const double* v, void* ua, void* va, int32_t* eu,
                         int32_t* ev, int32_t* partials, int64_t kpad, unsigned* err, unsigned* barrier,
-                        unsigned long long* zero64, int64_t zero64_n, cudaStream_t st) {
+                        unsigned long long* zero64, int64_t zero64_n, const bool* skip,
+                        cudaStream_t st) {
   const int S = split ? n_slices : 0;
   if (S < 0 || S > kMaxSlices) return cudaErrorInvalidValue;
   void (*kern)(PrepArgs) = nullptr;
@@ -684,12 +900,14 @@ cudaError_t launch_prep(const Problem& p, const Tables& t, bool split, int n_sli
   a.fast_rows[0] = rows_fast(p.u);
   a.fast_rows[1] = rows_fast(p.v);
   // 16-byte pair loads need adjacent real entries (not interleaved complex ones)
-  a.pair_ok[0] = p.es == 1 && !a.fast_rows[0] && pairs_aligned(p.u);
-  a.pair_ok[1] = p.es == 1 && !a.fast_rows[1] && pairs_aligned(p.v);
+  a.pair_ok[0] = p.es == 1 && !p.general && !a.fast_rows[0] && pairs_aligned(p.u);
+  a.pair_ok[1] = p.es == 1 && !p.general && !a.fast_rows[1] && pairs_aligned(p.v);
   a.err = err;
   a.barrier = barrier;
   a.zero64 = zero64;
   a.zero64_n = zero64_n;
+  a.skip[0] = skip && skip[0];
+  a.skip[1] = skip && skip[1];
   void* params[] = {&a};
   cudaError_t e = cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(THREADS),
                                               params, 0, st);

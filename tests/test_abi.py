@@ -181,3 +181,58 @@ def test_tensors_on_another_device_are_rejected(monkeypatch):
     sc.Plan._same_device(_FakeTensor(0), None, _FakeTensor(0))
     with pytest.raises(ValueError):
         sc.Plan._same_device(_FakeTensor(0), _FakeTensor(1))
+
+
+# --------------------------------------------------------------------------
+# generalized symmetry (Eq. symtsr: H | G sectors, coefficient +-G/H; padded
+# non-uniform sectors): the planner against the oracle's plan
+# --------------------------------------------------------------------------
+
+def _general_cases():
+    import sys
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from test_oracle_pins import random_general_case
+    rng = np.random.default_rng(2024)
+    out = []
+    for (s, t, v) in [(1, 1, 1), (2, 1, 1), (1, 2, 2), (2, 2, 1), (0, 2, 1), (1, 0, 2), (2, 1, 0),
+                      (3, 1, 1)]:
+        for G in (4, 6, 8, 12):
+            out.append(random_general_case(s, t, v, G, rng, int(rng.choice([-1, 1]))))
+    return out
+
+
+def _as_spec(sym):
+    return (sym.signs, sym.charge, sym.dims, sym.sectors, sym.sector_dims)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "split_bf16"])
+def test_general_planner_matches_oracle(precision):
+    for p, _, _ in _general_cases():
+        q = sc.Plan(f"{p.lu},{p.lv}->{p.lw}", p.group.moduli, _as_spec(p.sym_u), _as_spec(p.sym_v),
+                    precision)
+        G, M, N, K = O.aligned_dims(p)
+        assert (q.info.M, q.info.N, q.info.K) == (M, N, K)
+        assert q.info.general == 1 and q.info.sigma == p.sigma
+        assert q.shape_u == O.reduced_shape(p.group, p.sym_u)
+        assert q.shape_w == O.reduced_shape(p.group, p.sym_w)
+        assert q.sym_w.signs == p.sym_w.signs and q.sym_w.charge == p.sym_w.charge
+        assert q.sym_w.sectors == p.sym_w.sectors and q.sym_w.sector_dims == p.sym_w.sector_dims
+        # every form reads the general index maps from tables (none when no irrep carries work)
+        assert q.info.table_bytes > 0 or q.info.n_q == 0
+
+
+def test_general_plan_errors():
+    spec = "ab,bc->ac"
+    ok_u = ((1, -1), (0,), (2, 2), (4, 4))
+    ok_v = ((1, -1), (0,), (2, 2), (4, 2))
+    sc.Plan(spec, (8,), ok_u, ok_v)   # valid
+    cases = [
+        (((1, -1), (0,), (2, 2), (3, 4)), ok_v, (8,), 3),        # 3 does not divide 8
+        (ok_u, ((1, -1), (0,), (2, 2), (2, 2)), (8,), 3),        # contracted b: 4 vs 2 sectors
+        (((1, -1), (0,), (2, 2), (4, 4), ((1, 2, 2, 3), (2, 2, 2, 2))), ok_v, (8,), 3),  # 3 > D
+        (((1, -1), (0,), (2, 2), (2, 6)), ((1, -1), (0,), (2, 2), (6, 6)), (2, 3), 5),   # product group
+    ]
+    for su, sv, mod, want in cases:
+        with pytest.raises(sc.SymctrError) as ei:
+            sc.Plan(spec, mod, su, sv)
+        assert ei.value.status == want, (su, sv)

@@ -113,6 +113,8 @@ def test_config3_cc_ladder_full_size(sc, cc_full, precision):
     c, u, v = cc_full
     p = sc.Plan(c.einsum, c.moduli, spec(c.u), spec(c.v), precision)
     assert (p.info.M, p.info.K, p.info.N) == (8192, 8192, 512)
+    # v (U here) is prepared by the single-read kernel in the split form
+    assert bool(p.info.single_read_prep & 1) == (precision == "split_bf16")
     ud, vd = torch.from_numpy(u).cuda(), torch.from_numpy(v).cuda()
     w = p.contract(ud, vd)
     torch.cuda.synchronize()

@@ -313,3 +313,42 @@ def test_split_bit_exact_on_integer_inputs(sc, k_sectors, D):
     # exact integer products (|sum| <= D * 2^24 < 2^63), rounded once to float64
     want = np.stack([np.matmul(u[q].astype(np.int64), v[q].astype(np.int64)) for q in range(G)])
     assert np.array_equal(got, want.astype(np.float64))
+
+
+def test_single_read_prep_bit_exact_on_integer_inputs(sc):
+    """The single-read preparation (rows streamed into shared memory by bulk
+    copies of contiguous runs) on a shape that takes it: integer inputs of two
+    BF16 digits must give the exact integer product rounded once, bit for bit,
+    as in the two-phase preparation."""
+    G, D_i, D_j, D_k = 2, 1024, 4096, 64
+    su = ((1, -1), (0,), (D_i, D_j))
+    sv = ((1, -1), (0,), (D_j, D_k))
+    rng = np.random.default_rng(611)
+    u = rng.integers(-4096, 4097, size=(G, D_i, D_j)).astype(np.float64)
+    v = rng.integers(-4096, 4097, size=(G, D_j, D_k)).astype(np.float64)
+    u[:, :4, :] = 4096.0
+    u[:, 4:6, :] = -4096.0
+    u[:, 6, :] = 0.0              # an all-zero row
+    p = sc.Plan("ij,jk->ik", (G,), su, sv, "split_bf16")
+    assert p.info.single_read_prep & 1
+    got = host(p.contract(dev(u), dev(v)))
+    p.check_device_error()
+    want = np.stack([np.matmul(u[q].astype(np.int64), v[q].astype(np.int64)) for q in range(G)])
+    assert np.array_equal(got, want.astype(np.float64))
+
+
+def test_single_read_prep_nonfinite_is_reported(sc):
+    """A NaN in an operand prepared by the single-read kernel sets the device
+    error word (and nothing traps)."""
+    G, D_i, D_j, D_k = 2, 1024, 4096, 64
+    p = sc.Plan("ij,jk->ik", (G,), ((1, -1), (0,), (D_i, D_j)), ((1, -1), (0,), (D_j, D_k)),
+                "split_bf16")
+    assert p.info.single_read_prep & 1
+    rng = np.random.default_rng(612)
+    u = rng.standard_normal((G, D_i, D_j))
+    u[1, 77, 1234] = np.nan
+    v = rng.standard_normal((G, D_j, D_k))
+    p.contract(dev(u), dev(v))
+    with pytest.raises(sc.SymctrError) as ei:
+        p.check_device_error()
+    assert ei.value.status == 11

@@ -199,3 +199,38 @@ def small_cases() -> List[Contraction]:
                            TensorSpec((1, -1, 1), (1,), (3, 2, 4), 1.0, 25),
                            TensorSpec((-1, 1), (1,), (4, 2), 1.0, 26)))
     return out
+
+
+# Generic contractions of Eq. ctr (Sec. 5.1.1, sensitivity to contraction
+# type): s free modes of U, t free modes of V, v contracted modes, every mode
+# with G = 4 sectors of the same size D, D chosen so that the contraction's
+# symmetry-reduced work 2 G^(s+t+v-2) D^(s+t+v) is as close as an integer D
+# gets to 80e9 flops.  Signs: U's free modes +1, contracted -1; V's contracted
+# +1 (sigma = -1), free -1; zero remainders.  Entries N(0,1) scaled by
+# 1/sqrt(contracted length).
+GENERIC_G = 4
+GENERIC_FLOPS = 80e9
+GENERIC_STV = [(s, t, v) for s in (1, 2, 3) for t in (1, 2, 3) for v in (1, 2, 3)]
+
+
+def generic_dim(s: int, t: int, v: int, G: int = GENERIC_G, flops: float = GENERIC_FLOPS) -> int:
+    n = s + t + v
+    return max(1, int(round((flops / (2.0 * G ** (n - 2))) ** (1.0 / n))))
+
+
+def generic_contraction(s: int, t: int, v: int, G: int = GENERIC_G,
+                        flops: float = GENERIC_FLOPS) -> Contraction:
+    D = generic_dim(s, t, v, G, flops)
+    letters = iter("abcdefghijklmnop")
+    FU = "".join(next(letters) for _ in range(s))
+    C = "".join(next(letters) for _ in range(v))
+    FV = "".join(next(letters) for _ in range(t))
+    scale = 1.0 / math.sqrt((G * D) ** v)
+    seed = 9000 + 100 * s + 10 * t + v
+    return Contraction(
+        name=f"generic_s{s}t{t}v{v}_G{G}_D{D}",
+        einsum=f"{FU}{C},{C}{FV}->{FU}{FV}",
+        moduli=(G,),
+        u=TensorSpec(tuple([1] * s + [-1] * v), (0,), tuple([D] * (s + v)), scale, seed),
+        v=TensorSpec(tuple([1] * v + [-1] * t), (0,), tuple([D] * (v + t)), 1.0, seed + 1),
+    )
