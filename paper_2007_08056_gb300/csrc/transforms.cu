@@ -603,11 +603,12 @@ __global__ void __launch_bounds__(THREADS, 4) prep_kernel(PrepArgs a) {
 // reduced-form entries (the column map's innermost block digits have
 // unit-stride layout) and fits in shared memory, one CTA per SM instead
 // streams whole rows into shared memory with bulk copies (one per run, on an
-// mbarrier, kRsBufs rows in flight), takes the row maximum there and writes
+// mbarrier, up to kRsMaxBufs rows in flight), takes the row maximum there and writes
 // the row's digits from there: every operand entry crosses HBM once.
 // ---------------------------------------------------------------------------
-constexpr int RS_THREADS = 256;
-constexpr int kRsBufs = 3;
+constexpr int RS_THREADS = 512;
+constexpr int kRsMaxBufs = 6;          // rows in flight per CTA (as shared memory allows)
+constexpr size_t kRsSmem = 200 * 1024;  // shared memory for the row buffers
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -623,6 +624,7 @@ struct RowStreamArgs {
   int64_t slice_stride;     // n_q * R * kpad (elements)
   int32_t* exps;            // [n_q][R] biased row exponents
   unsigned* err;
+  int nbuf;                 // row buffers (<= kRsMaxBufs)
 };
 
 // Bounded wait on a bulk-copy barrier (about 2 s of SM clock); false on expiry.
@@ -667,7 +669,7 @@ __device__ __forceinline__ void rs_issue(const RowStreamArgs& a, int64_t g, doub
 template <int S>
 __global__ void __launch_bounds__(RS_THREADS, 1) rowstream_kernel(const __grid_constant__ RowStreamArgs a) {
   extern __shared__ __align__(128) uint8_t rs_smem[];
-  __shared__ __align__(8) uint64_t bars[kRsBufs];
+  __shared__ __align__(8) uint64_t bars[kRsMaxBufs];
   __shared__ unsigned long long red[RS_THREADS / 32];
   __shared__ int32_t key_s;
   __shared__ int abort_s;
@@ -675,23 +677,24 @@ __global__ void __launch_bounds__(RS_THREADS, 1) rowstream_kernel(const __grid_c
   const int64_t buf_elems = (a.K + 15) / 16 * 16;   // 128-byte aligned buffers
   double* bufs = (double*)rs_smem;
   const int64_t rows = (int64_t)a.n_q * a.R;
+  const int nbuf = a.nbuf;
   if (tid == 0) {
-    for (int i = 0; i < kRsBufs; ++i)
+    for (int i = 0; i < nbuf; ++i)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[i])) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     abort_s = 0;
   }
   __syncthreads();
   if (warp == 0)
-    for (int s = 0; s < kRsBufs; ++s) {
+    for (int s = 0; s < nbuf; ++s) {
       const int64_t g = blockIdx.x + (int64_t)s * gridDim.x;
       if (g < rows) rs_issue(a, g, bufs + s * buf_elems, &bars[s], lane);
     }
   int it = 0;
   int64_t g = blockIdx.x;
   for (; g < rows; g += gridDim.x, ++it) {
-    const int slot = it % kRsBufs;
-    const uint32_t parity = (uint32_t)(it / kRsBufs) & 1u;
+    const int slot = it % nbuf;
+    const uint32_t parity = (uint32_t)(it / nbuf) & 1u;
     // every thread observes the copies' completion on the barrier
     const bool ok = rs_wait(&bars[slot], parity);
     if (!ok && lane == 0) atomicOr(a.err, (unsigned)DEVERR_TIMEOUT);
@@ -733,17 +736,17 @@ __global__ void __launch_bounds__(RS_THREADS, 1) rowstream_kernel(const __grid_c
       put_slices_pair<S>(x0, x1, k0, d + c2, a.slice_stride / 2);
     }
     __syncthreads();   // every thread is done with this buffer
-    const int64_t gn = g + (int64_t)kRsBufs * gridDim.x;
+    const int64_t gn = g + (int64_t)nbuf * gridDim.x;
     if (warp == 0 && gn < rows) rs_issue(a, gn, bufs + slot * buf_elems, &bars[slot], lane);
   }
   // the GEMM behind this kernel may start its launch
   asm volatile("griddepcontrol.launch_dependents;");
   if (abort_s && tid == 0) {
     // let the copies still in flight land before the CTA exits (bounded)
-    for (int k = it; k < it + kRsBufs; ++k) {
+    for (int k = it; k < it + nbuf; ++k) {
       const int64_t gk = blockIdx.x + (int64_t)k * gridDim.x;
       if (gk >= rows) break;
-      rs_wait(&bars[k % kRsBufs], (uint32_t)(k / kRsBufs) & 1u);
+      rs_wait(&bars[k % nbuf], (uint32_t)(k / nbuf) & 1u);
     }
   }
 }
@@ -804,7 +807,11 @@ cudaError_t launch_rowstream(const Problem& p, const Tables& t, int op, int n_sl
     case 5: kern = rowstream_kernel<5>; break;
     default: kern = rowstream_kernel<6>; break;
   }
-  const size_t smem = (size_t)kRsBufs * ((K + 15) / 16 * 16) * sizeof(double);
+  const size_t row_bytes = (size_t)((K + 15) / 16 * 16) * sizeof(double);
+  int nbuf = (int)(kRsSmem / row_bytes);
+  if (nbuf > kRsMaxBufs) nbuf = kRsMaxBufs;
+  if (nbuf < 2) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)nbuf * row_bytes;
   // the attribute is set once per instance and device (kept per host thread)
   thread_local size_t set_for[kMaxSlices + 1][16] = {};
   int dev = 0;
@@ -832,6 +839,7 @@ cudaError_t launch_rowstream(const Problem& p, const Tables& t, int op, int n_sl
   a.slice_stride = (int64_t)p.n_q * R * kpad;
   a.exps = exps;
   a.err = err;
+  a.nbuf = nbuf;
   const int64_t rows = (int64_t)p.n_q * R;
   const int grid = (int)(rows < sms ? (rows > 0 ? rows : 1) : sms);
   kern<<<grid, RS_THREADS, smem, st>>>(a);
