@@ -30,9 +30,9 @@
 // running sums of their 64 columns.  Optional split-K: each K range adds its
 // exact int64 partial sums into a workspace with integer atomics (order-free,
 // so the result is deterministic) and a finalize kernel rounds them.  Tiles
-// 128 x 128 (split) or 128 x 256 (TF32), 64-byte K rows (32 BF16 or 16 FP32),
-// SWIZZLE_64B, all 512 TMEM columns allocated (4 x 128 FP32 accumulators in
-// the split form).
+// 128 x 128 (split: 64-byte K rows of 32 BF16, SWIZZLE_64B, two stages) or
+// 128 x 256 (TF32: 128-byte K rows of 32 FP32, SWIZZLE_128B, four stages), all
+// 512 TMEM columns allocated (4 x 128 FP32 accumulators in the split form).
 // Every wait is bounded: on expiry the kernel records DEVERR_TIMEOUT in the
 // workspace error word, drains its own copies and MMAs, frees TMEM, returns.
 #include <cuda.h>
@@ -48,8 +48,6 @@ namespace symctr {
 namespace {
 
 constexpr int TM = 128;
-constexpr int ROW_BYTES = 64;                  // K bytes per tile row per stage
-constexpr int TILE_BYTES = TM * ROW_BYTES;     // 8 KB per 128-row slice tile per stage
 constexpr int NTHREADS = 384;
 constexpr int EPI_WARP0 = 4;
 constexpr int kExpBias = 4096;     // row exponents are stored biased (0 = all-zero row)
@@ -73,9 +71,15 @@ enum Mode { MODE_SPLIT = 0, MODE_TF32 = 1 };
 // Tile shapes per form: the split form 128 x 128 (four accumulators fill
 // TMEM), the TF32 form 128 x 256 (one accumulator; the wider B tile doubles
 // the MMA work per byte staged, which bounds TF32 at 128 x 128).
+// K bytes per tile row and stage: 64 (32 BF16, SWIZZLE_64B) in the split form,
+// whose 5 + 5 slice tiles make 80 KB a stage; 128 (32 FP32, SWIZZLE_128B) in
+// the TF32 form, so that a stage carries four K8 MMAs and the issuing thread's
+// per-stage waits and commits are amortised over more tensor work.
 template <int KIND>
 struct TileCfg {
   static constexpr int N = KIND == MODE_TF32 ? 256 : 128;    // output columns per CTA
+  static constexpr int ROW_BYTES = KIND == MODE_TF32 ? 128 : 64;
+  static constexpr int KSTEPS = ROW_BYTES / 32;              // MMA K steps per stage
   static constexpr int A_BYTES = TM * ROW_BYTES;             // per slice, per stage
   static constexpr int B_BYTES = N * ROW_BYTES;
   static constexpr int LD = N + 1;                           // staging row stride (elements)
@@ -209,14 +213,18 @@ __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// Shared-memory matrix descriptor: K-major, SWIZZLE_64B, 8-row groups 512 B apart.
+// Shared-memory matrix descriptor: K-major, rows of ROW_BYTES swizzled over
+// their width (SWIZZLE_64B for 64-byte rows, SWIZZLE_128B for 128-byte rows),
+// 8-row groups 8 * ROW_BYTES apart.
+template <int KIND>
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  constexpr int RB = TileCfg<KIND>::ROW_BYTES;
   uint64_t d = 0;
   d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
   d |= (uint64_t)1 << 16;             // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(512 >> 4) << 32;    // stride byte offset
+  d |= (uint64_t)((8 * RB) >> 4) << 32;   // stride byte offset
   d |= (uint64_t)1 << 46;             // descriptor version (tcgen05)
-  d |= (uint64_t)4 << 61;             // SWIZZLE_64B
+  d |= (uint64_t)(RB == 128 ? 2 : 4) << 61;   // SWIZZLE_128B / SWIZZLE_64B
   return d;
 }
 
@@ -385,8 +393,9 @@ __device__ __forceinline__ void store_batch(const Problem& p, double* w, const i
 }
 
 // Descriptor offset of slice tile `i`, K step `kk` (16-byte units).
+template <int KIND>
 __host__ __device__ constexpr uint64_t dofs(int i, int kk) {
-  return (uint64_t)((i * TILE_BYTES + kk * 32) >> 4);
+  return (uint64_t)((i * TM * TileCfg<KIND>::ROW_BYTES + kk * 32) >> 4);
 }
 
 // Compile-time loop: f(std::integral_constant<int, 0>) ... f(..<N-1>).
@@ -404,7 +413,7 @@ __device__ __forceinline__ void static_for(F&& f) {
 template <int KIND, int I, int J, int KK>
 __device__ __forceinline__ void mma_ij(uint32_t tacc, uint64_t da, uint64_t db, uint32_t id,
                                        uint32_t acc) {
-  constexpr unsigned long long oa = dofs(I, KK), ob = dofs(J, KK);
+  constexpr unsigned long long oa = dofs<KIND>(I, KK), ob = dofs<KIND>(J, KK);
   if (KIND == MODE_SPLIT) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t.reg .b64 a, b;\n\t"
@@ -433,7 +442,7 @@ __device__ __forceinline__ void issue_top(uint32_t tmem, uint64_t da, uint64_t d
   static_for<3>([&](auto D) {
     if constexpr (D.value <= S - 1) {
       static_for<D.value + 1>([&](auto I) {
-        static_for<2>([&](auto KK) {
+        static_for<TileCfg<KIND>::KSTEPS>([&](auto KK) {
           constexpr bool first = I.value == 0 && KK.value == 0;
           mma_ij<KIND, I.value, D.value - I.value, KK.value>(
               tmem + 128u * D.value, da, db, id, (first && ((fresh >> D.value) & 1u)) ? 0u : 1u);
@@ -451,7 +460,7 @@ __device__ __forceinline__ void issue_low(uint32_t tmem, uint64_t da, uint64_t d
     constexpr int D = D3.value + 3;
     static_for<D + 1>([&](auto I) {
       if constexpr (I.value < S && D - I.value < S) {
-        static_for<2>([&](auto KK) {
+        static_for<TileCfg<KIND>::KSTEPS>([&](auto KK) {
           constexpr bool first = D == 3 && I.value == 0 && KK.value == 0;
           mma_ij<KIND, I.value, D - I.value, KK.value>(tmem + 384u, da, db, id,
                                                        (fresh && first) ? 0u : 1u);
@@ -586,7 +595,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         mbar_expect_tx(&full[st], stage_bytes);
         uint8_t* sa = tiles + (size_t)st * stage_bytes;
         uint8_t* sb = sa + S * Cfg::A_BYTES;
-        int kc = (kb0 + kb) * (ROW_BYTES / args.ebytes);
+        int kc = (kb0 + kb) * (Cfg::ROW_BYTES / args.ebytes);
         for (int i = 0; i < S; ++i) {
           tma_load_3d(&tma_a, &full[st], sa + i * Cfg::A_BYTES, kc, (int)m0, i * p.n_q + b);
           tma_load_3d(&tma_b, &full[st], sb + i * Cfg::B_BYTES, kc, (int)n0, i * p.n_q + b);
@@ -610,8 +619,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         uint32_t ph = (kb / STAGES) & 1;
         if (!wait_phase(&full[st], ph, ctl)) break;
         tc_fence_after();
-        const uint64_t da = sdesc(ab + st * stage_bytes);
-        const uint64_t db = sdesc(ab + st * stage_bytes + S * Cfg::A_BYTES);
+        const uint64_t da = sdesc<KIND>(ab + st * stage_bytes);
+        const uint64_t db = sdesc<KIND>(ab + st * stage_bytes + S * Cfg::A_BYTES);
         const bool cfirst = KIND == MODE_TF32 ? (kb == 0) : (kb % 2 == 0);
         const int chunk = KIND == MODE_TF32 ? 0 : kb / 2;
         const bool final_chunk = chunk == n_chunks - 1;
@@ -982,11 +991,14 @@ bool encode_map(CUtensorMap* map, const void* base, bool is_f32, int64_t kpad, i
   int eb = is_f32 ? 4 : 2;
   cuuint64_t dims[3] = {(cuuint64_t)kpad, (cuuint64_t)rows, (cuuint64_t)planes};
   cuuint64_t strides[2] = {(cuuint64_t)(kpad * eb), (cuuint64_t)(kpad * eb * rows)};
-  cuuint32_t box[3] = {(cuuint32_t)(ROW_BYTES / eb), (cuuint32_t)box_rows, 1};
+  // 128-byte rows with SWIZZLE_128B (TF32), 64-byte rows with SWIZZLE_64B (split)
+  const int rb = is_f32 ? TileCfg<MODE_TF32>::ROW_BYTES : TileCfg<MODE_SPLIT>::ROW_BYTES;
+  cuuint32_t box[3] = {(cuuint32_t)(rb / eb), (cuuint32_t)box_rows, 1};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = fn(map, is_f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3,
                   const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                  CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  rb == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
@@ -1004,7 +1016,7 @@ cudaError_t launch_tc_mode(const Problem& p, const Tables& tab, const void* a, c
   args.p = p;
   args.S = S;
   args.ebytes = f32 ? 4 : 2;
-  args.n_kb = (int)(kpad * args.ebytes / ROW_BYTES);
+  args.n_kb = (int)(kpad * args.ebytes / TileCfg<KIND>::ROW_BYTES);
   args.eu = eu;
   args.ev = ev;
   args.w = w;
@@ -1089,7 +1101,7 @@ cudaError_t launch_gemm_split(const Problem& p, const Tables& tab, int n_slices,
 
 cudaError_t launch_gemm_tf32(const Problem& p, const Tables& tab, const float* u, const float* v,
                              int64_t kpad, double* w, unsigned* err, cudaStream_t st) {
-  return launch_tc<MODE_TF32, 1, 8>(p, tab, u, v, nullptr, nullptr, kpad, w, err, 1, nullptr, st);
+  return launch_tc<MODE_TF32, 1, 4>(p, tab, u, v, nullptr, nullptr, kpad, w, err, 1, nullptr, st);
 }
 
 cudaError_t launch_bounded_wait_selftest(unsigned* err, long long limit_cycles, cudaStream_t st) {
