@@ -294,11 +294,17 @@ def run_ours(args, rank, world):
     ctr = None
     if args.workload == "mps":
         name, Eh, Ah = mps_workload()
+        if args.chain:
+            name += ", X kept aligned between the steps"
         E, A = torch.from_numpy(Eh).to(dev), torch.from_numpy(Ah).to(dev)
 
         def make(prec):
             p1 = sc.Plan(WL.MPS_STEP1, (WL.MPS_G,), spec(WL.MPS_E), spec(WL.MPS_A), prec)
             p2 = sc.Plan(WL.MPS_STEP2, (WL.MPS_G,), p1.sym_w, spec(WL.MPS_A), prec)
+            if args.chain:
+                # X stays in X = E.A's aligned layout and is read from there by E' = X.A
+                p1.chain(w_aligned=True)
+                p2.chain(u_from=p1)
             X = torch.empty(p1.shape_w, dtype=torch.float64, device=dev)
             out = torch.empty(p2.shape_w, dtype=torch.float64, device=dev)
 
@@ -782,6 +788,8 @@ def main():
                     help="VIRT,OCC of the sweep workload: 512,128 (config 5) or 256,64 (the "
                          "secondary sweep at the CC ladder's dimensions)")
     ap.add_argument("--backward", action="store_true", help="sweep: time the backward pair too")
+    ap.add_argument("--chain", action="store_true",
+                    help="mps: keep X aligned between the two contractions (symctr_plan_chain)")
     ap.add_argument("--complex", action="store_true",
                     help="mps: complex tensors, E' = sum E A conj(A) (four real products per contraction)")
     ap.add_argument("--precision", choices=["split_bf16", "fp64", "tf32"], default="split_bf16")

@@ -136,6 +136,8 @@ typedef struct {
   int32_t single_read_prep;     /* split form: bit 0 (U) / bit 1 (V) set when that operand's
                                    aligned rows are long contiguous runs and its slices are
                                    prepared by the single-read kernel (one HBM read) */
+  int32_t chained;              /* 1 after symctr_plan_chain re-laid the plan out (numel_u,
+                                   numel_v, numel_w then count the chained layouts) */
 } symctr_plan_info;
 
 /* One operand in the general form of Eq. symtsr, for symctr_plan_create_general.
@@ -202,6 +204,31 @@ SYMCTR_API symctr_status symctr_plan_create_general(const char* einsum, int n_mo
                                                    const int32_t* charge_w_or_null,
                                                    symctr_precision prec, int n_slices,
                                                    symctr_plan** out);
+
+/* Contraction chains that stay aligned (Sec. 2.1: the aligned result W_hat,
+ * with its extra symmetry mode Q, is itself a reduced form of W and can be
+ * remapped to any other; Alg. 2's output step is then skipped).  Re-lays a
+ * plan out so that:
+ *  - w_aligned != 0: the result is written as W_hat[b][m][n], float64, C order,
+ *    n_q x M x N (batch b is irrep q_first + b q_step; m and n as in the aligned
+ *    layouts above), with no map back to W's standard reduced form;
+ *  - u_from (v_from) != NULL: U (V) is passed as that plan's aligned result
+ *    W_hat (written by it with w_aligned) instead of a standard reduced form.
+ *    That plan's output modes must be this operand's modes in the same order,
+ *    with the same group, law (or its global negation), sector counts and
+ *    sizes; its free-U modes (which fix its irrep) must all be free modes or
+ *    all contracted modes of this contraction (else SYMCTR_ERR_UNSUPPORTED).
+ * Every form then reads its index maps from the offset tables (the kernels are
+ * the same); numel_u / numel_v / numel_w and the workspace sizes of
+ * symctr_plan_query follow the new layouts.  Call once, before the plan's
+ * first contraction or table attachment (SYMCTR_ERR_ARGUMENT otherwise); the
+ * source plans only lend their layouts and may be destroyed afterwards.  A
+ * chained plan has no backward (symctr_contract_backward returns
+ * SYMCTR_ERR_UNSUPPORTED).  Returns SYMCTR_OK, SYMCTR_ERR_NULLPTR,
+ * SYMCTR_ERR_SHAPE (a source that is not the operand), SYMCTR_ERR_UNSUPPORTED,
+ * SYMCTR_ERR_ARGUMENT or SYMCTR_ERR_OVERFLOW.  Host only. */
+SYMCTR_API symctr_status symctr_plan_chain(symctr_plan* plan, const symctr_plan* u_from,
+                                          const symctr_plan* v_from, int w_aligned);
 
 /* Fill *out with the plan's derived quantities.  Host only. */
 SYMCTR_API symctr_status symctr_plan_query(const symctr_plan* plan, symctr_plan_info* out);

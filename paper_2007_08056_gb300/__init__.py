@@ -65,6 +65,7 @@ class PlanInfo(ctypes.Structure):
         ("tensor_core", ctypes.c_int32), ("general", ctypes.c_int32),
         ("q_first", ctypes.c_int32), ("q_step", ctypes.c_int32),
         ("sectors_w", ctypes.c_int32 * MAX_ORDER), ("single_read_prep", ctypes.c_int32),
+        ("chained", ctypes.c_int32),
     ]
 
 
@@ -122,6 +123,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.symctr_contract_complex.argtypes = [P, ctypes.c_int, ctypes.c_int, P, P, P, P,
                                             ctypes.c_size_t, P]
     lib.symctr_plan_attach_tables.argtypes = [P, P, ctypes.c_size_t, P]
+    lib.symctr_plan_chain.argtypes = [P, P, P, ctypes.c_int]
     lib.symctr_plan_destroy.argtypes = [P]
     lib.symctr_plan_destroy.restype = None
     for f in ("symctr_plan_create", "symctr_plan_create_general", "symctr_plan_query",
@@ -129,7 +131,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
               "symctr_contract_backward", "symctr_check_device_error", "symctr_profile_enable",
               "symctr_profile_read", "symctr_contract_static_scratch",
               "symctr_selftest_bounded_wait", "symctr_contract_complex",
-              "symctr_plan_attach_tables"):
+              "symctr_plan_attach_tables", "symctr_plan_chain"):
         getattr(lib, f).restype = ctypes.c_int
     _LIB = lib
     return lib
@@ -208,6 +210,19 @@ class Plan:
         self.precision = precision
         su, sv = self.sym_u, self.sym_v
         sw = _spec(sym_w) if sym_w is not None else None
+        # the C ABI reads one entry per mode: check every spec against its operand
+        lhs, lw_ = einsum.replace(" ", "").split("->") if "->" in einsum else (einsum, "")
+        labels = lhs.split(",") + [lw_]
+        for lab, sp, name in ((labels[0], su, "sym_u"), (labels[1] if len(labels) > 2 else "", sv, "sym_v"),
+                              (labels[-1], sw, "sym_w")):
+            if sp is None:
+                continue
+            if not (len(sp.signs) == len(sp.dims) == len(lab)) or len(sp.charge) != len(self.moduli):
+                raise ValueError(f"{name}: {len(lab)} modes and {len(self.moduli)} moduli expected")
+            if sp.sectors is not None and len(sp.sectors) != len(lab):
+                raise ValueError(f"{name}: one sector count per mode expected")
+            if sp.sector_dims is not None and len(sp.sector_dims) != len(lab):
+                raise ValueError(f"{name}: one list of sector sizes per mode expected")
         handle = ctypes.c_void_p()
         if su.general or sv.general:
             keep = []
@@ -294,6 +309,31 @@ class Plan:
             if t is not None and t.get_device() != dev:
                 raise ValueError(f"tensor on cuda:{t.get_device()} but the current device is "
                                  f"cuda:{dev}; use torch.cuda.device(...) around the call")
+
+    # -- contraction chains ------------------------------------------------
+    def chain(self, u_from: "Optional[Plan]" = None, v_from: "Optional[Plan]" = None,
+              w_aligned: bool = False) -> "Plan":
+        """Keep intermediates aligned (symctr_plan_chain): with w_aligned the
+        result is W_hat of shape (n_q, M, N), with no map back; u_from / v_from
+        make U / V that plan's aligned result.  Call before the first
+        contraction.  A chained plan has no backward."""
+        _check(load().symctr_plan_chain(self._h, None if u_from is None else u_from._h,
+                                        None if v_from is None else v_from._h, int(bool(w_aligned))))
+        info = PlanInfo()
+        _check(load().symctr_plan_query(self._h, ctypes.byref(info)))
+        self.info = info
+        aligned = lambda p: (int(p.info.n_q), int(p.info.M), int(p.info.N))
+        if u_from is not None:
+            self.shape_u = aligned(u_from)
+        if v_from is not None:
+            self.shape_v = aligned(v_from)
+        if w_aligned:
+            self.shape_w = aligned(self)
+        self._size_u, self._size_v, self._size_w = (torch.Size(self.shape_u), torch.Size(self.shape_v),
+                                                     torch.Size(self.shape_w))
+        self._tables_ready = info.table_bytes == 0
+        self._ws = None
+        return self
 
     # -- device tables -------------------------------------------------------
     def attach_tables(self, device=None):

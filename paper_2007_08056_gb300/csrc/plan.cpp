@@ -147,16 +147,15 @@ struct GenAxis {
   int64_t size = 1;
 };
 
-// Reduced-form offset of aligned index r at irrep Q, or -1 when the entry is
-// absent: the last mode's sector equation sum_i c_i q_i == qa Q + z (mod G),
-// c_i = sign_i G / H_i, has no solution (it needs a multiple of G / H_last),
-// or a block index lies beyond its sector's true size (padding).  Product
-// groups have H = G on every mode and solve componentwise.
-int64_t gen_offset(const GenAxis& a, const GroupDesc& g, int Q, int64_t r) {
+// Sectors q and block indices b of aligned index r at irrep Q over the modes
+// of one side, the last mode's sector solving sum_i c_i q_i == qa Q + z
+// (mod G), c_i = sign_i G / H_i.  False when the entry is absent: that
+// equation has no solution (it needs a multiple of G / H_last) or a block
+// index lies beyond its sector's true size (padding).  Product groups have
+// H = G on every mode and solve componentwise.
+bool gen_decode(const GenAxis& a, const GroupDesc& g, int Q, int64_t r, int* q, int64_t* b) {
   const int target = g_add(g, g_signed(g, a.qa, Q), a.z);
-  if (a.n == 0) return target == 0 ? 0 : -1;
-  int64_t b[SYMCTR_MAX_ORDER];
-  int q[SYMCTR_MAX_ORDER];
+  if (a.n == 0) return target == 0;
   for (int i = a.n - 1; i >= 0; --i) {
     b[i] = r % a.D[i];
     r /= a.D[i];
@@ -173,17 +172,68 @@ int64_t gen_offset(const GenAxis& a, const GroupDesc& g, int Q, int64_t r) {
     const int rhs = ((target - partial) % G + G) % G;
     const int x = ((a.sign[last] * rhs) % G + G) % G;
     const int step = G / a.H[last];
-    if (x % step != 0) return -1;
+    if (x % step != 0) return false;
     q[last] = x / step;
   } else {
     int partial = 0;
     for (int i = 0; i < last; ++i) partial = g_add(g, partial, g_signed(g, a.sign[i], q[i]));
     q[last] = g_signed(g, a.sign[last], g_add(g, target, g_neg(g, partial)));
   }
+  for (int i = 0; i < a.n; ++i)
+    if (a.sd[i] && b[i] >= (*a.sd[i])[q[i]]) return false;
+  return true;
+}
+
+// Reduced-form offset of aligned index r at irrep Q, or -1 when the entry is
+// absent (gen_decode).
+int64_t gen_offset(const GenAxis& a, const GroupDesc& g, int Q, int64_t r) {
+  int q[SYMCTR_MAX_ORDER];
+  int64_t b[SYMCTR_MAX_ORDER];
+  if (!gen_decode(a, g, Q, r, q, b)) return -1;
   int64_t off = 0;
-  for (int i = 0; i < a.n; ++i) {
-    if (a.sd[i] && b[i] >= (*a.sd[i])[q[i]]) return -1;
-    off += (int64_t)q[i] * a.sstride[i] + b[i] * a.bstride[i];
+  for (int i = 0; i < a.n; ++i) off += (int64_t)q[i] * a.sstride[i] + b[i] * a.bstride[i];
+  return off;
+}
+
+// One side of an operand read from another plan's aligned result W_hat[b][m][n]
+// (contraction chains, symctr_plan_chain): for each of the side's modes, the
+// strides of its sector and block digits in that layout (0 for a sector the
+// layout leaves implicit), and, when the source's free-U modes all fall on
+// this side, the batch term: the source irrep Q_src = z - sum coef_i q_i
+// selects batch b = (Q_src - q0) / step, weighted by M_src * N_src.
+struct ChainSide {
+  int64_t sstride[SYMCTR_MAX_ORDER], bstride[SYMCTR_MAX_ORDER];
+  bool batch = false;
+  int coef[SYMCTR_MAX_ORDER];   // source coefficients on this side's modes (0: not free-U there)
+  int z = 0;
+  int q_single = -1, q0 = 0, q_step = 1, n_q = 0;
+  int64_t batch_stride = 0;
+};
+
+int64_t chain_offset(const GenAxis& a, const ChainSide& c, const GroupDesc& g, int Q, int64_t r) {
+  int q[SYMCTR_MAX_ORDER];
+  int64_t b[SYMCTR_MAX_ORDER];
+  if (!gen_decode(a, g, Q, r, q, b)) return -1;
+  int64_t off = 0;
+  for (int i = 0; i < a.n; ++i) off += (int64_t)q[i] * c.sstride[i] + b[i] * c.bstride[i];
+  if (c.batch) {
+    int qs = c.z;
+    for (int i = 0; i < a.n; ++i) {
+      if (c.coef[i] == 0) continue;
+      if (g.n == 1)
+        qs = ((qs - c.coef[i] * q[i]) % g.order + g.order) % g.order;
+      else
+        qs = g_add(g, qs, g_signed(g, -c.coef[i], q[i]));
+    }
+    int bi;
+    if (c.q_single >= 0) {
+      bi = qs == c.q_single ? 0 : -1;
+    } else {
+      const int d = ((qs - c.q0) % g.order + g.order) % g.order;
+      bi = (d % c.q_step == 0 && d / c.q_step < c.n_q) ? d / c.q_step : -1;
+    }
+    if (bi < 0) return -1;
+    off += (int64_t)bi * c.batch_stride;
   }
   return off;
 }
@@ -209,6 +259,13 @@ struct symctr_plan {
   // split form: run length of the single-read preparation of U and V (0: the
   // operand takes the two-phase preparation)
   int64_t row_run[2] = {0, 0};
+  // contraction chains (symctr_plan_chain): U and/or V read from another
+  // plan's aligned result, and/or W written as W_hat; no backward.  A chained
+  // plan is table-driven (general) without having absent entries of its own.
+  bool chained = false;
+  // W holds entries no aligned element covers (padding, sector tuples without
+  // a solution): zeroed as a whole before each contraction
+  bool fill_all = false;
   symctr_plan* bwd_u = nullptr;
   symctr_plan* bwd_v = nullptr;
   bool prof = false;
@@ -527,6 +584,7 @@ symctr_status build(const char* einsum, int n_moduli, const int32_t* moduli, con
     if (!matches(sw, zw)) return bail(SYMCTR_ERR_CHARGE, "given output law contradicts the derived law");
   }
   P->general = P->u.general((int)G) || P->v.general((int)G) || P->w.general((int)G);
+  P->fill_all = P->general;
 
   // ---- sizes ----
   P->numel_u = reduced_numel(P->u);
@@ -835,7 +893,7 @@ symctr_status run_contract_body(const symctr_plan* P, const double* u, const dou
   // general plan, its padding and the entries whose implicit sector has no
   // solution: those plans zero W as a whole first.
   const int64_t fill_n = mode.fill_n < 0 ? P->numel_w : mode.fill_n;
-  if ((P->general || (int64_t)pr.n_q * pr.M * pr.N < P->numel_w) && fill_n > 0) {
+  if ((P->fill_all || (int64_t)pr.n_q * pr.M * pr.N < P->numel_w) && fill_n > 0) {
     e = launch_fill_zero(w, fill_n, st);
     if (e != cudaSuccess) return cuda_status(e, "zero fill");
   }
@@ -967,6 +1025,98 @@ static symctr_status attach_tables(symctr_plan* P, uint8_t* buf, int dev, cudaSt
   return attach_tables(P->bwd_v, next ? next + all_table_bytes(P->bwd_u) : nullptr, dev, st);
 }
 
+// The six standard index maps of a plan in the general form (host).
+static void plan_axes(const symctr_plan* P, GenAxis* gax) {
+  const std::string &lu = P->u.labels, &lv = P->v.labels, &lw = P->w.labels;
+  std::vector<int> FV_in_V = P->FV, C_in_V, FU_in_W, FV_in_W;
+  int sgn_fu[SYMCTR_MAX_ORDER], sgn_cu[SYMCTR_MAX_ORDER], sgn_cv[SYMCTR_MAX_ORDER],
+      sgn_fv[SYMCTR_MAX_ORDER];
+  for (size_t i = 0; i < P->FU.size(); ++i) {
+    sgn_fu[i] = P->u.sign[P->FU[i]];
+    FU_in_W.push_back((int)lw.find(lu[P->FU[i]]));
+  }
+  for (size_t i = 0; i < P->C.size(); ++i) {
+    sgn_cu[i] = P->u.sign[P->C[i]];
+    int j = (int)lv.find(lu[P->C[i]]);
+    C_in_V.push_back(j);
+    sgn_cv[i] = P->v.sign[j];
+  }
+  for (size_t i = 0; i < P->FV.size(); ++i) {
+    sgn_fv[i] = P->v.sign[P->FV[i]];
+    FV_in_W.push_back((int)lw.find(lv[P->FV[i]]));
+  }
+  gax[0] = make_gen_axis(P->u, P->FU, sgn_fu, -1, P->u.z);
+  gax[1] = make_gen_axis(P->u, P->C, sgn_cu, +1, 0);
+  gax[2] = make_gen_axis(P->v, FV_in_V, sgn_fv, -P->sigma, P->v.z);
+  gax[3] = make_gen_axis(P->v, C_in_V, sgn_cv, P->sigma, 0);
+  gax[4] = make_gen_axis(P->w, FU_in_W, sgn_fu, -1, P->u.z);
+  gax[5] = make_gen_axis(P->w, FV_in_W, sgn_fv, -P->sigma, P->v.z);
+}
+
+// The two sides of an operand (its modes `rows`, `cols`, positions in the
+// operand) read from `src`'s aligned result, whose output modes are the
+// operand's modes in order.  Returns false when the source's free-U modes
+// (which fix its irrep) are split between the two sides.
+static bool chain_sides(const symctr_plan* src, const std::vector<int>& rows,
+                        const std::vector<int>& cols, ChainSide* cr, ChainSide* cc) {
+  const int G = src->g.order;
+  const std::string &lw = src->w.labels, &lu = src->u.labels, &lv = src->v.labels;
+  const int s = (int)src->FU.size(), t = (int)src->FV.size();
+  // W positions of the source's free-U and free-V modes, in its aligned order
+  std::vector<int> fu_w, fv_w;
+  for (int i : src->FU) fu_w.push_back((int)lw.find(lu[i]));
+  for (int j : src->FV) fv_w.push_back((int)lw.find(lv[j]));
+  // mixed-radix strides of m = (sectors of free-U but the last, their blocks), n likewise
+  auto strides = [&](const std::vector<int>& modes) {
+    std::vector<int64_t> rad;
+    for (size_t i = 0; i + 1 < modes.size(); ++i) rad.push_back(src->w.H[modes[i]]);
+    for (int p : modes) rad.push_back(src->w.dim[p]);
+    std::vector<int64_t> st(rad.size());
+    int64_t acc = 1;
+    for (int k = (int)rad.size() - 1; k >= 0; --k) {
+      st[k] = acc;
+      acc *= rad[k];
+    }
+    return st;
+  };
+  const std::vector<int64_t> ms = strides(fu_w), ns = strides(fv_w);
+  const int64_t Nsrc = src->prob.N;
+  auto fill = [&](const std::vector<int>& modes, ChainSide* c) {
+    for (size_t k = 0; k < modes.size(); ++k) {
+      const int p = modes[k];   // W position of the source = operand position
+      c->coef[k] = 0;
+      for (int i = 0; i < s; ++i)
+        if (fu_w[i] == p) {
+          c->sstride[k] = i < s - 1 ? ms[i] * Nsrc : 0;
+          c->bstride[k] = ms[(s - 1) + i] * Nsrc;
+          c->coef[k] = src->u.sign[src->FU[i]] * (G / src->u.H[src->FU[i]]);
+        }
+      for (int j = 0; j < t; ++j)
+        if (fv_w[j] == p) {
+          c->sstride[k] = j < t - 1 ? ns[j] : 0;
+          c->bstride[k] = ns[(t - 1) + j];
+        }
+    }
+    c->batch = false;
+    c->z = src->u.z;
+    c->q_single = src->prob.q_single;
+    c->q0 = src->prob.q0;
+    c->q_step = src->prob.q_step;
+    c->n_q = src->prob.n_q;
+    c->batch_stride = src->prob.M * src->prob.N;
+  };
+  fill(rows, cr);
+  fill(cols, cc);
+  int in_rows = 0, in_cols = 0;
+  for (int p : fu_w) {
+    for (int r : rows) in_rows += r == p;
+    for (int c : cols) in_cols += c == p;
+  }
+  if (in_rows && in_cols) return false;
+  (in_cols ? cc : cr)->batch = true;
+  return true;
+}
+
 extern "C" {
 
 symctr_status symctr_plan_create(const char* einsum, int n_moduli, const int32_t* moduli,
@@ -1051,11 +1201,12 @@ symctr_status symctr_plan_query(const symctr_plan* P, symctr_plan_info* o) {
   o->workspace_bytes_backward = wb;
   o->table_bytes = all_table_bytes(P);
   o->tensor_core = P->tensor_core ? 1 : 0;
-  o->general = P->general ? 1 : 0;
+  o->general = P->fill_all ? 1 : 0;
   o->q_first = pr.q_single >= 0 ? pr.q_single : pr.q0;
   o->q_step = pr.q_single >= 0 ? 0 : pr.q_step;
   for (int i = 0; i < P->w.order(); ++i) o->sectors_w[i] = P->w.H[i];
   o->single_read_prep = (P->row_run[0] > 0 ? 1 : 0) | (P->row_run[1] > 0 ? 2 : 0);
+  o->chained = P->chained ? 1 : 0;
   return SYMCTR_OK;
 }
 
@@ -1090,7 +1241,7 @@ symctr_status symctr_align(const symctr_plan* P, int operand, int direction, con
   if ((!src && (direction > 0 ? total : covered) > 0) || (!dst && (direction > 0 ? covered : total) > 0))
     return fail(SYMCTR_ERR_NULLPTR, "NULL argument");
   if (direction == -1) {
-    if (P->general || covered < total) {
+    if (P->fill_all || covered < total) {
       cudaError_t e = launch_fill_zero(dst, total, st);
       if (e != cudaSuccess) return cuda_status(e, "zero fill");
     }
@@ -1126,6 +1277,7 @@ symctr_status symctr_contract_backward(const symctr_plan* P, const double* gw, c
                                        const double* v, double* gu, double* gv, void* ws,
                                        size_t ws_bytes, void* stream) {
   if (!P || !gw) return fail(SYMCTR_ERR_NULLPTR, "NULL argument");
+  if (P->chained) return fail(SYMCTR_ERR_UNSUPPORTED, "a chained plan has no backward");
   if (!P->bwd_u || !P->bwd_v) return fail(SYMCTR_ERR_ARGUMENT, "plan has no backward");
   cudaStream_t st = (cudaStream_t)stream;
   if (gu) {
@@ -1246,6 +1398,88 @@ symctr_status symctr_profile_read(const symctr_plan* P, float* prep_ms, float* g
   if (e == cudaSuccess) e = cudaEventElapsedTime(prep_ms, P->ev[0], P->ev[1]);
   if (e == cudaSuccess) e = cudaEventElapsedTime(gemm_ms, P->ev[1], P->ev[2]);
   return cuda_status(e, "profile read");
+}
+
+symctr_status symctr_plan_chain(symctr_plan* P, const symctr_plan* u_from, const symctr_plan* v_from,
+                                int w_aligned) {
+  if (!P) return fail(SYMCTR_ERR_NULLPTR, "NULL plan");
+  if (!u_from && !v_from && !w_aligned) return SYMCTR_OK;
+  if (P->chained || P->pinned || P->dev_tab)
+    return fail(SYMCTR_ERR_ARGUMENT, "chain a plan once, before its first contraction or table attachment");
+  const GroupDesc& g = P->g;
+  auto same_tensor = [&](const symctr_plan* src, const Tensor& t) -> bool {
+    if (src->g.n != g.n || src->g.order != g.order) return false;
+    for (int i = 0; i < g.n; ++i)
+      if (src->g.mod[i] != g.mod[i]) return false;
+    const Tensor& w = src->w;
+    if (w.order() != t.order()) return false;
+    bool same = w.z == t.z, neg = w.z == g_neg(g, t.z);
+    for (int i = 0; i < t.order(); ++i) {
+      if (w.dim[i] != t.dim[i] || w.H[i] != t.H[i] || w.sd[i] != t.sd[i]) return false;
+      same = same && w.sign[i] == t.sign[i];
+      neg = neg && w.sign[i] == -t.sign[i];
+    }
+    return same || neg;
+  };
+  if (u_from && !same_tensor(u_from, P->u))
+    return fail(SYMCTR_ERR_SHAPE, "u_from's result is not this plan's U (modes, sectors, sizes or law differ)");
+  if (v_from && !same_tensor(v_from, P->v))
+    return fail(SYMCTR_ERR_SHAPE, "v_from's result is not this plan's V (modes, sectors, sizes or law differ)");
+  ChainSide cs[4];
+  std::vector<int> C_in_V;
+  for (int i : P->C) C_in_V.push_back((int)P->v.labels.find(P->u.labels[i]));
+  if (u_from && !chain_sides(u_from, P->FU, P->C, &cs[0], &cs[1]))
+    return fail(SYMCTR_ERR_UNSUPPORTED, "u_from's free-U modes are split between U's free and contracted modes");
+  if (v_from && !chain_sides(v_from, P->FV, C_in_V, &cs[2], &cs[3]))
+    return fail(SYMCTR_ERR_UNSUPPORTED, "v_from's free-U modes are split between V's free and contracted modes");
+  Problem& pr = P->prob;
+  GenAxis gax[6];
+  plan_axes(P, gax);
+  if (pr.n_q > 0) {
+    const int64_t total = tables_entries(pr);
+    if (total > (int64_t)1 << 28) return fail(SYMCTR_ERR_OVERFLOW, "offset tables too large");
+    std::vector<int64_t> tab;
+    try {
+      tab.resize((size_t)total);
+    } catch (const std::bad_alloc&) {
+      return fail(SYMCTR_ERR_OVERFLOW, "offset tables: host allocation failed");
+    }
+    int64_t* t = tab.data();
+    const int64_t ext[6] = {pr.M, pr.K, pr.N, pr.K, pr.M, pr.N};
+    for (int k = 0; k < 6; ++k)
+      for (int b = 0; b < pr.n_q; ++b) {
+        const int Q = batch_irrep(pr, b);
+        for (int64_t r = 0; r < ext[k]; ++r) {
+          int64_t off;
+          if (k < 2 && u_from)
+            off = chain_offset(gax[k], cs[k], g, Q, r);
+          else if (k >= 2 && k < 4 && v_from)
+            off = chain_offset(gax[k], cs[k], g, Q, r);
+          else if (k >= 4 && w_aligned)   // W_hat[b][m][n]: rows (b M + m) N, columns n
+            off = gen_offset(gax[k], g, Q, r) < 0 ? -1 : (k == 4 ? ((int64_t)b * pr.M + r) * pr.N : r);
+          else
+            off = gen_offset(gax[k], g, Q, r);
+          *t++ = off;
+        }
+      }
+    P->htab.swap(tab);
+  }
+  P->chained = true;
+  P->general = true;
+  pr.general = 1;
+  P->row_run[0] = P->row_run[1] = 0;
+  if (u_from) P->numel_u = (int64_t)u_from->prob.n_q * u_from->prob.M * u_from->prob.N;
+  if (v_from) P->numel_v = (int64_t)v_from->prob.n_q * v_from->prob.M * v_from->prob.N;
+  if (w_aligned) P->numel_w = (int64_t)pr.n_q * pr.M * pr.N;
+  Layout full = make_layout(pr, P->tensor_core, true, P->prec, P->n_slices, P->kpad);
+  if (!full.ok) return fail(SYMCTR_ERR_OVERFLOW, "aligned operand too large");
+  P->ws_bytes = P->ws_bytes_min = full.bytes;
+  if (P->tensor_core && pr.q_single < 0 && pr.n_q > 1) {
+    Problem one = pr;
+    one.n_q = 1;
+    P->ws_bytes_min = make_layout(one, true, true, P->prec, P->n_slices, P->kpad).bytes;
+  }
+  return SYMCTR_OK;
 }
 
 void symctr_plan_destroy(symctr_plan* P) {

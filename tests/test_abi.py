@@ -230,9 +230,39 @@ def test_general_plan_errors():
         (((1, -1), (0,), (2, 2), (3, 4)), ok_v, (8,), 3),        # 3 does not divide 8
         (ok_u, ((1, -1), (0,), (2, 2), (2, 2)), (8,), 3),        # contracted b: 4 vs 2 sectors
         (((1, -1), (0,), (2, 2), (4, 4), ((1, 2, 2, 3), (2, 2, 2, 2))), ok_v, (8,), 3),  # 3 > D
-        (((1, -1), (0,), (2, 2), (2, 6)), ((1, -1), (0,), (2, 2), (6, 6)), (2, 3), 5),   # product group
+        (((1, -1), (0, 0), (2, 2), (2, 6)), ((1, -1), (0, 0), (2, 2), (6, 6)), (2, 3), 5),   # product group
     ]
     for su, sv, mod, want in cases:
         with pytest.raises(sc.SymctrError) as ei:
             sc.Plan(spec, mod, su, sv)
         assert ei.value.status == want, (su, sv)
+
+
+def test_chain_layouts_and_errors():
+    """symctr_plan_chain: shapes of the aligned layouts, one chain per plan,
+    sources that are not the operand, split free-U modes."""
+    spec = lambda t: (t.signs, t.charge, t.dims)
+    g = (WL.MPS_G,)
+    p1 = sc.Plan(WL.MPS_STEP1, g, spec(WL.MPS_E), spec(WL.MPS_A), "split_bf16").chain(w_aligned=True)
+    assert p1.shape_w == (8, 128, 2048) and p1.info.numel_w == 8 * 128 * 2048 and p1.info.chained
+    p2 = sc.Plan(WL.MPS_STEP2, g, p1.sym_w, spec(WL.MPS_A), "split_bf16").chain(u_from=p1)
+    assert p2.shape_u == (8, 128, 2048) and p2.info.numel_u == 8 * 128 * 2048
+    with pytest.raises(sc.SymctrError) as ei:
+        p2.chain(w_aligned=True)
+    assert ei.value.status == 12
+    other = sc.Plan(WL.MPS_STEP2, g, spec(WL.MPS_A), spec(WL.MPS_A), "split_bf16")
+    with pytest.raises(sc.SymctrError) as ei:
+        other.chain(u_from=sc.Plan("ab,bc->ac", g, ((1, -1), (0,), (128, 64)), ((1, -1), (0,), (64, 3))))
+    assert ei.value.status == 3
+    r1 = sc.Plan("ab,cd->abcd", (4,), ((1, -1), (0,), (2, 3)), ((1, -1), (0,), (2, 3)))
+    r2 = sc.Plan("abcd,be->acde", (4,), r1.sym_w, ((-1, 1), (0,), (3, 2)))
+    with pytest.raises(sc.SymctrError) as ei:
+        r2.chain(u_from=r1)
+    assert ei.value.status == 5
+
+
+def test_spec_lengths_are_checked():
+    """The binding refuses a symmetry spec whose length differs from its
+    operand's order (the C ABI reads one entry per mode)."""
+    with pytest.raises(ValueError):
+        sc.Plan("ab,abc->c", (4,), ((1, -1), (0,), (2, 3)), ((1, -1), (0,), (2, 3)))
