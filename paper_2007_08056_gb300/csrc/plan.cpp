@@ -908,6 +908,12 @@ symctr_status run_contract_body(const symctr_plan* P, const double* u, const dou
       Tables tab;
       symctr_status s = pass_tables(P, pr, 0, attached, base, L.off_tab, st, &tab);
       if (s != SYMCTR_OK) return s;
+      // the table-driven kernel accumulates split K ranges onto a zeroed W (a
+      // chained plan's W has not been zeroed above)
+      if (!P->fill_all && !mode.accumulate && fill_n > 0) {
+        e = launch_fill_zero(w, fill_n, st);
+        if (e != cudaSuccess) return cuda_status(e, "zero fill");
+      }
       e = launch_gemm_f64(pr, u, v, w, &tab, st);
     } else {
       e = launch_gemm_f64(pr, u, v, w, nullptr, st);

@@ -352,3 +352,39 @@ def test_single_read_prep_nonfinite_is_reported(sc):
     with pytest.raises(sc.SymctrError) as ei:
         p.check_device_error()
     assert ei.value.status == 11
+
+
+@pytest.mark.parametrize("precision", ["split_bf16", "tf32"])
+def test_mps_step_repeatable(sc, precision):
+    """The MPS transfer step (both contractions, the second reading the first's
+    output): against the oracle, and bit-identical over repeated calls."""
+    E = WL.draw(WL.MPS_E, (8,))
+    A = WL.draw(WL.MPS_A, (8,))
+    p1 = sc.Plan(WL.MPS_STEP1, (8,), spec(WL.MPS_E), spec(WL.MPS_A), precision)
+    p2 = sc.Plan(WL.MPS_STEP2, (8,), p1.sym_w, spec(WL.MPS_A), precision)
+    Ed, Ad = dev(E), dev(A)
+    X = p1.contract(Ed, Ad)
+    E2 = p2.contract(X, Ad)
+    again = p2.contract(p1.contract(Ed, Ad), Ad)
+    torch.cuda.synchronize()
+    p1.check_device_error()
+    p2.check_device_error()
+    assert torch.equal(E2, again)
+    o1 = oplan(WL.MPS_STEP1, (8,), spec(WL.MPS_E), spec(WL.MPS_A))
+    o2 = oplan(WL.MPS_STEP2, (8,), (p1.sym_w.signs, p1.sym_w.charge, p1.sym_w.dims), spec(WL.MPS_A))
+    Xr = O.contract_blockloop(o1, E, A)
+    assert rel(host(X), Xr) <= TOL[precision]
+    assert rel(host(E2), O.contract_blockloop(o2, Xr, A)) <= 2 * TOL[precision]
+
+
+def test_mps_nonfinite_is_reported(sc):
+    """An infinity in E (read by the preparation of X = E.A) sets the device
+    error word."""
+    E = WL.draw(WL.MPS_E, (8,)).copy()
+    A = WL.draw(WL.MPS_A, (8,))
+    E[3, 5, 7] = np.inf
+    p1 = sc.Plan(WL.MPS_STEP1, (8,), spec(WL.MPS_E), spec(WL.MPS_A), "split_bf16")
+    p1.contract(dev(E), dev(A))
+    with pytest.raises(sc.SymctrError) as ei:
+        p1.check_device_error()
+    assert ei.value.status == 11
