@@ -197,6 +197,8 @@ def replicas_value(flops_per_step, ms, world):
 # sit beside the kernels; the shared sizing rules are in the internal header)
 KERNEL_SOURCES = {
     "prep_kernel": ("transforms.cu", "symctr_internal.h"),
+    "rowtile_kernel": ("transforms.cu", "symctr_internal.h"),
+    "rowstream_kernel": ("transforms.cu", "symctr_internal.h"),
     "gemm_tc_kernel": ("gemm_tc.cu", "symctr_internal.h"),
     "gemm_f64": ("gemm_f64.cu", "symctr_internal.h"),
 }
@@ -204,7 +206,10 @@ KERNEL_SOURCES = {
 
 def kernel_source_hash(kernel):
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES[kernel]:
+    files = []
+    for k in kernel.split("+"):
+        files += [f for f in KERNEL_SOURCES[k] if f not in files]
+    for f in files:
         with open(os.path.join(ROOT, "paper_2007_08056_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -247,6 +252,28 @@ def prep_bytes(pl):
     return elems * (8 + 4)
 
 
+def prep_kernels(pl):
+    """The operand-preparation kernels a plan launches: per operand, bits 0/1 of
+    info.single_read_prep mean rows streamed by bulk copies (rowstream_kernel),
+    bits 2/3 whole short rows per CTA (rowtile_kernel), neither the two-phase
+    prep_kernel (which also runs alone to zero split-K sums when no short-row
+    kernel runs)."""
+    i = pl.info
+    if i.precision != 1:
+        return ["prep_kernel"]
+    names = []
+    for op in (0, 1):
+        if i.single_read_prep & (1 << op):
+            names.append("rowstream_kernel")
+        elif i.single_read_prep & (4 << op):
+            names.append("rowtile_kernel")
+        else:
+            names.append("prep_kernel")
+    if "rowtile_kernel" not in names:
+        names.append("prep_kernel")
+    return names
+
+
 def rooflines(args, plans, prep, gemm, pk):
     """One roofline per kernel kind of the step: achieved = algorithmic work of
     its launches in one step / their CUDA-event time in that step."""
@@ -276,10 +303,14 @@ def rooflines(args, plans, prep, gemm, pk):
     if args.precision != "fp64" and prep_ms > 0:
         nbytes = sum(prep_bytes(pl) for pl in plans)
         achieved = nbytes / (prep_ms * 1e-3) / 1e9
-        key = f"prep_kernel/{args.precision}/{args.workload}"
-        out.append({"kernel": "prep_kernel", "bound": "hbm", "achieved": round(achieved, 1),
+        names = []
+        for pl in plans:
+            names += [k for k in prep_kernels(pl) if k not in names]
+        label = "+".join(names)
+        key = f"{label}/{args.precision}/{args.workload}"
+        out.append({"kernel": label, "bound": "hbm", "achieved": round(achieved, 1),
                     "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": round(achieved / pk["hbm_gbs"], 4),
-                    "traffic": load_traffic("prep_kernel", key), "peak_src": f"{pk['src']} hbm copy",
+                    "traffic": load_traffic(label, key), "peak_src": f"{pk['src']} hbm copy",
                     "launches_per_step": len(plans), "ms_per_step": round(prep_ms, 4),
                     "work_per_launch": nbytes / len(plans)})
     return out

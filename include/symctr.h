@@ -135,7 +135,12 @@ typedef struct {
   int32_t sectors_w[SYMCTR_MAX_ORDER]; /* sector count of each mode of W */
   int32_t single_read_prep;     /* split form: bit 0 (U) / bit 1 (V) set when that operand's
                                    aligned rows are long contiguous runs and its slices are
-                                   prepared by the single-read kernel (one HBM read) */
+                                   prepared by the single-read kernel (one HBM read); bit 2
+                                   (U) / bit 3 (V) set when that operand's whole rows are
+                                   read once by the short-row kernel instead: K (padded) at
+                                   most 4096, or at most 2048 for rows that are the reduced
+                                   form's unit-stride side or long runs (real data; complex
+                                   data takes the two-phase kernel) */
   int32_t chained;              /* 1 after symctr_plan_chain re-laid the plan out (numel_u,
                                    numel_v, numel_w then count the chained layouts) */
 } symctr_plan_info;

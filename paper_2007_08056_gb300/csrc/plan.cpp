@@ -259,6 +259,9 @@ struct symctr_plan {
   // split form: run length of the single-read preparation of U and V (0: the
   // operand takes the two-phase preparation)
   int64_t row_run[2] = {0, 0};
+  // split form, K <= kRowTileMaxK: operand op's whole aligned rows fit one
+  // CTA's shared memory and it takes the short-row single-read kernel
+  bool row_tile[2] = {false, false};
   // contraction chains (symctr_plan_chain): U and/or V read from another
   // plan's aligned result, and/or W written as W_hat; no backward.  A chained
   // plan is table-driven (general) without having absent entries of its own.
@@ -733,6 +736,24 @@ symctr_status build(const char* einsum, int n_moduli, const int32_t* moduli, con
     }
   }
 
+  // Short rows (split form): operands whose padded K is at most kRowTileMaxK
+  // are read once by the short-row kernel (whole rows per CTA, no grid
+  // barrier), with the exceptions below.
+  if (P->tensor_core && prec == SYMCTR_SPLIT_BF16 && P->kpad <= kRowTileMaxK) {
+    const AxisMap* rows[2] = {&pr.u.rows, &pr.v.rows};
+    for (int op = 0; op < 2; ++op) {
+      // rows that are the reduced form's unit-stride side are gathered across
+      // rows, at least 4 per CTA (32-byte sectors): K <= 2048; rows of
+      // contiguous runs up to K = 2048 also go here (the bulk-copy kernel, one
+      // row per step, pays off on longer rows)
+      const bool rows_contig = rows[op]->n > 0 && rows[op]->bstride[rows[op]->n - 1] == 1;
+      if (rows_contig && P->kpad > kRowTileMaxK / 2) continue;
+      if (P->row_run[op] > 0 && P->kpad > kRowTileMaxK / 2) continue;
+      P->row_tile[op] = true;
+      P->row_run[op] = 0;
+    }
+  }
+
   if (with_backward) {
     // gU = einsum(lw,lv->lu)(gW, V): result carries U's law.
     OwnedDesc dw(P->w, g), du(P->u, g), dv(P->v, g);
@@ -957,9 +978,22 @@ symctr_status run_contract_body(const symctr_plan* P, const double* u, const dou
     int32_t* part = split && L.off_part ? (int32_t*)(base + L.off_part) : nullptr;
     // operands with row runs take the single-read kernel (real data only)
     const bool rs[2] = {split && pr.es == 1 && P->row_run[0] > 0, split && pr.es == 1 && P->row_run[1] > 0};
-    e = launch_prep(pc, tab, split, P->n_slices, u, v, base + L.off_a, base + L.off_b, ea, eb, part,
-                    P->kpad, err, barrier, acc, acc_n, rs, st);
-    if (e != cudaSuccess) return cuda_status(e, "operand preparation");
+    // short rows take the short-row kernel (real data only)
+    const bool rt[2] = {split && pr.es == 1 && P->row_tile[0], split && pr.es == 1 && P->row_tile[1]};
+    const bool skip[2] = {rs[0] || rt[0], rs[1] || rt[1]};
+    // the two-phase kernel runs for an operand left to it, or to zero the
+    // split-K sums when no short-row kernel runs
+    const bool two_phase = !skip[0] || !skip[1] || !(rt[0] || rt[1]);
+    if (two_phase) {
+      e = launch_prep(pc, tab, split, P->n_slices, u, v, base + L.off_a, base + L.off_b, ea, eb, part,
+                      P->kpad, err, barrier, acc, acc_n, skip, st);
+      if (e != cudaSuccess) return cuda_status(e, "operand preparation");
+    }
+    if (rt[0] || rt[1]) {
+      e = launch_rowtile(pc, tab, P->n_slices, rt, u, v, base + L.off_a, base + L.off_b, ea, eb, P->kpad,
+                         err, two_phase ? nullptr : acc, two_phase ? 0 : acc_n, st);
+      if (e != cudaSuccess) return cuda_status(e, "operand preparation (short rows)");
+    }
     for (int op = 0; op < 2; ++op) {
       if (!rs[op]) continue;
       e = launch_rowstream(pc, tab, op, P->n_slices, P->row_run[op], op == 0 ? u : v,
@@ -1211,7 +1245,8 @@ symctr_status symctr_plan_query(const symctr_plan* P, symctr_plan_info* o) {
   o->q_first = pr.q_single >= 0 ? pr.q_single : pr.q0;
   o->q_step = pr.q_single >= 0 ? 0 : pr.q_step;
   for (int i = 0; i < P->w.order(); ++i) o->sectors_w[i] = P->w.H[i];
-  o->single_read_prep = (P->row_run[0] > 0 ? 1 : 0) | (P->row_run[1] > 0 ? 2 : 0);
+  o->single_read_prep = (P->row_run[0] > 0 ? 1 : 0) | (P->row_run[1] > 0 ? 2 : 0) |
+                        (P->row_tile[0] ? 4 : 0) | (P->row_tile[1] ? 8 : 0);
   o->chained = P->chained ? 1 : 0;
   return SYMCTR_OK;
 }

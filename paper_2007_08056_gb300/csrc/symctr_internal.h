@@ -206,7 +206,8 @@ cudaError_t launch_align_f64(const Problem& p, int operand, int direction, const
 cudaError_t launch_gemm_f64(const Problem& p, const double* u, const double* v, double* w,
                             const Tables* tables, cudaStream_t st);
 cudaError_t launch_fill_zero(double* w, int64_t n, cudaStream_t st);
-// skip[op]: operand op is prepared by launch_rowstream instead (NULL: neither)
+// skip[op]: operand op is prepared by launch_rowstream or launch_rowtile
+// instead (NULL: neither)
 cudaError_t launch_prep(const Problem& p, const Tables& t, bool split, int n_slices,
                         const double* u, const double* v, void* ua, void* va, int32_t* eu,
                         int32_t* ev, int32_t* partials, int64_t kpad, unsigned* err, unsigned* barrier,
@@ -219,6 +220,18 @@ constexpr int64_t kRowStreamMaxK = 8192;
 cudaError_t launch_rowstream(const Problem& p, const Tables& t, int op, int n_slices, int64_t run,
                              const double* src, void* slices, int32_t* exps, int64_t kpad,
                              unsigned* err, cudaStream_t st);
+// Single-read split-form preparation of short rows: the operands with on[op]
+// set, K <= kRowTileMaxK (padded), 2^rowtile_rows_log2(kpad) whole rows per
+// CTA in rowtile_smem_bytes of shared memory; also zeroes zero64 (the split-K
+// sums) when no other preparation kernel runs.
+constexpr int64_t kRowTileMaxK = 4096;
+constexpr int64_t kRowTileElems = 8192;   // aligned entries held per CTA (at most; at least 2 rows)
+int rowtile_rows_log2(int64_t kpad);
+size_t rowtile_smem_bytes(int64_t K, int64_t kpad);
+cudaError_t launch_rowtile(const Problem& p, const Tables& t, int n_slices, const bool* on,
+                           const double* u, const double* v, void* ua, void* va, int32_t* eu,
+                           int32_t* ev, int64_t kpad, unsigned* err, unsigned long long* zero64,
+                           int64_t zero64_n, cudaStream_t st);
 cudaError_t launch_bounded_wait_selftest(unsigned* err, long long limit_cycles, cudaStream_t st);
 cudaError_t launch_gemm_split(const Problem& p, const Tables& t, int n_slices, const uint16_t* us,
                               const uint16_t* vs, const int32_t* eu, const int32_t* ev,

@@ -381,6 +381,27 @@ __device__ __forceinline__ void put_slices_pair(double x0, double x1, int k0, ui
   put_digits<S>(y0, y1, dst, stride);
 }
 
+// Four adjacent columns of one row: per slice, four BF16 digits in one 8-byte
+// store (dst and stride in units of uint2).
+template <int S, int I = 0>
+__device__ __forceinline__ void put_digits_quad(const uint64_t (&y)[4], uint2* dst, int64_t stride) {
+  if constexpr (I < S) {
+    const __nv_bfloat162 lo = __floats2bfloat162_rn(digit_value<S, I>(y[0]), digit_value<S, I>(y[1]));
+    const __nv_bfloat162 hi = __floats2bfloat162_rn(digit_value<S, I>(y[2]), digit_value<S, I>(y[3]));
+    dst[(int64_t)I * stride] =
+        make_uint2(*reinterpret_cast<const uint32_t*>(&lo), *reinterpret_cast<const uint32_t*>(&hi));
+    put_digits_quad<S, I + 1>(y, dst, stride);
+  }
+}
+
+template <int S>
+__device__ __forceinline__ void put_slices_quad(const double (&x)[4], int k0, uint2* dst, int64_t stride) {
+  uint64_t y[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) y[j] = (uint64_t)(fixed_point(x[j], k0) + (int64_t)digit_bias(S));
+  put_digits_quad<S>(y, dst, stride);
+}
+
 __device__ __forceinline__ float tf32_round(double x) {
   uint32_t u = __float_as_uint(__double2float_rn(x));
   if ((u & 0x7F800000u) != 0x7F800000u) u = (u + 0xFFFu + ((u >> 13) & 1u)) & ~0x1FFFu;
@@ -721,19 +742,20 @@ __global__ void __launch_bounds__(RS_THREADS, 1) rowstream_kernel(const __grid_c
     }
     __syncthreads();
     const int k0 = row_k0(key_s, S);
-    // the digits, two adjacent columns per thread and step (zeros beyond K)
-    uint32_t* d = a.dst + g * (a.kpad / 2);
-    for (int64_t c2 = tid; c2 < a.kpad / 2; c2 += RS_THREADS) {
-      const int64_t c = 2 * c2;
-      double x0 = 0.0, x1 = 0.0;
-      if (c + 1 < a.K) {
-        const double2 v2 = *reinterpret_cast<const double2*>(row + c);
-        x0 = v2.x;
-        x1 = v2.y;
-      } else if (c < a.K) {
-        x0 = row[c];
+    // the digits, four adjacent columns per thread and step (zeros beyond K)
+    uint2* d = reinterpret_cast<uint2*>(a.dst) + g * (a.kpad / 4);
+    for (int64_t q = tid; q < a.kpad / 4; q += RS_THREADS) {
+      const int64_t c = 4 * q;
+      double x[4];
+      if (c + 4 <= a.K) {
+        const double2 v0 = *reinterpret_cast<const double2*>(row + c);
+        const double2 v1 = *reinterpret_cast<const double2*>(row + c + 2);
+        x[0] = v0.x, x[1] = v0.y, x[2] = v1.x, x[3] = v1.y;
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) x[e] = c + e < a.K ? row[c + e] : 0.0;
       }
-      put_slices_pair<S>(x0, x1, k0, d + c2, a.slice_stride / 2);
+      put_slices_quad<S>(x, k0, d + q, a.slice_stride / 4);
     }
     __syncthreads();   // every thread is done with this buffer
     const int64_t gn = g + (int64_t)nbuf * gridDim.x;
@@ -768,7 +790,235 @@ void operand_extent(const Problem& p, int operand, int64_t* R, int64_t* Cn) {
   else { *R = p.M; *Cn = p.N; }
 }
 
+// ---------------------------------------------------------------------------
+// Single-read preparation of short rows (split form, K <= kRowTileMaxK).  One
+// CTA holds 2^rlog whole aligned rows in shared memory: it gathers them once
+// (consecutive threads on consecutive rows when the rows are the reduced form's
+// unit-stride side, else on consecutive columns), takes each row's maximum
+// there and writes the row's digits from there.  No grid barrier: the
+// operands' preparation is one plain launch.
+// ---------------------------------------------------------------------------
+constexpr int RT_THREADS = 512;
+
+// 8-byte asynchronous copy global -> shared; src_bytes 0 fills zeros (reads nothing)
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+               : "memory");
+}
+
+struct RowTileArgs {
+  Problem p;
+  Tables t;
+  int64_t kpad;
+  int rlog;                  // rows per CTA = 2^rlog
+  uint32_t units[2];         // (irrep, row block) units of U and of V (0: not prepared here)
+  const double* src[2];
+  uint32_t* dst[2];          // BF16 digit pairs: [S][n_q][R][kpad / 2]
+  int32_t* exps[2];          // [n_q][R] biased row exponents
+  bool fast_rows[2];
+  size_t buf_off;            // byte offset of the row buffer in shared memory
+  unsigned* err;
+  unsigned long long* zero64;  // split-K partial sums, zeroed here
+  int64_t zero64_n;
+};
+
+template <int S>
+__global__ void __launch_bounds__(RT_THREADS) rowtile_kernel(const __grid_constant__ RowTileArgs a) {
+  extern __shared__ __align__(16) uint8_t rt_smem[];
+  const Problem& p = a.p;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int R = 1 << a.rlog;
+  const int Kc = (int)p.K;
+  const int kpad = (int)a.kpad;
+  // row pitch kpad + 2 doubles: 16-byte aligned pairs for the digit pass, and
+  // row-strided stores of the gather spread over the banks
+  const int LD = kpad + 2;
+  int64_t* coff = (int64_t*)rt_smem;
+  int64_t* roff = coff + Kc;
+  unsigned long long* rmx = (unsigned long long*)(roff + R);
+  int32_t* rk0 = (int32_t*)(rmx + R);
+  // index splits i = r * n + c by a float reciprocal: exact while i / n <= 64
+  // and n <= 4096 (the error, below 2^-17, stays under the 0.5 / n margin)
+  const float inv_k = 1.0f / (float)Kc;
+  const float inv_q = 1.0f / (float)(kpad >> 2);
+  double* buf = (double*)(rt_smem + a.buf_off);
+  const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + tid; i < a.zero64_n; i += gthreads) a.zero64[i] = 0ull;
+  // every CTA of this grid is resident once all have passed here: the GEMM
+  // behind it may start its setup
+  asm volatile("griddepcontrol.launch_dependents;");
+  const uint32_t total = a.units[0] + a.units[1];
+  for (uint32_t unit = blockIdx.x; unit < total; unit += gridDim.x) {
+    const int op = unit < a.units[0] ? 0 : 1;
+    const uint32_t un = op == 0 ? unit : unit - a.units[0];
+    const int64_t Rtot = op == 0 ? p.M : p.N;
+    const uint32_t rblocks = (uint32_t)((Rtot + R - 1) >> a.rlog);
+    const uint32_t b = un / rblocks;
+    const int64_t r0 = (int64_t)(un - b * rblocks) << a.rlog;
+    const int64_t* rtab = (op == 0 ? a.t.urow : a.t.vrow) + (int64_t)b * Rtot;
+    const int64_t* ctab = (op == 0 ? a.t.ucol : a.t.vcol) + (int64_t)b * Kc;
+    const double* src = a.src[op];
+    __syncthreads();   // the previous unit is done with shared memory
+    // offsets, then the rows: asynchronous 8-byte copies into shared memory,
+    // every copy of a thread in flight at once (an absent row or column,
+    // offset -1 in general plans, and rows past the end are zero-filled)
+    for (int k = tid; k < Kc; k += RT_THREADS) cp_async8(coff + k, ctab + k, 8u);
+    for (int r = tid; r < R; r += RT_THREADS) {
+      if (r0 + r < Rtot) cp_async8(roff + r, rtab + r0 + r, 8u);
+      else roff[r] = -1;
+      rmx[r] = 0ull;
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+    const int n = R * Kc;
+    const bool fr = a.fast_rows[op];
+    for (int i = tid; i < n; i += RT_THREADS) {
+      int r, k;
+      if (fr) {
+        r = i & (R - 1);
+        k = i >> a.rlog;
+      } else {
+        r = __float2int_rz(((float)i + 0.5f) * inv_k);
+        k = i - r * Kc;
+      }
+      const int64_t ro = roff[r], co = coff[k];
+      const bool ok = ro >= 0 && co >= 0;
+      cp_async8(buf + r * LD + k, ok ? src + ro + co : src, ok ? 8u : 0u);
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+    // row maxima: 8 / R warps per row when R < 8, else a warp per row
+    {
+      constexpr int NW = RT_THREADS / 32;
+      const int wpr = R < NW ? NW / R : 1;
+      const int sub = warp % wpr;
+      for (int r = warp / wpr; r < R; r += NW / wpr) {
+        uint64_t m = 0;
+        for (int k = sub * 32 + lane; k < Kc; k += 32 * wpr) m = max(m, abs_bits(buf[r * LD + k]));
+        for (int o = 16; o > 0; o >>= 1)
+          m = max(m, (uint64_t)__shfl_xor_sync(0xffffffffu, (unsigned long long)m, o));
+        if (lane == 0) atomicMax(&rmx[r], (unsigned long long)m);
+      }
+    }
+    __syncthreads();
+    for (int r = tid; r < R; r += RT_THREADS) {
+      unsigned bad = 0;
+      const int32_t key = row_key<S>(rmx[r], bad);
+      if (bad) atomicOr(a.err, (unsigned)DEVERR_NONFINITE);
+      if (r0 + r < Rtot) a.exps[op][(int64_t)b * Rtot + r0 + r] = key;
+      rk0[r] = row_k0(key, S);
+    }
+    __syncthreads();
+    // digits: consecutive threads on consecutive groups of four columns of a
+    // row (the padding columns K..kpad-1 get zero digits)
+    const int Q4 = kpad >> 2;
+    const int64_t sstride = (int64_t)p.n_q * Rtot * Q4;   // uint2 quads per slice
+    uint2* dst = reinterpret_cast<uint2*>(a.dst[op]) + ((int64_t)b * Rtot + r0) * Q4;
+    const int rows_here = (int)min((int64_t)R, Rtot - r0);
+    for (int j = tid; j < rows_here * Q4; j += RT_THREADS) {
+      const int r = __float2int_rz(((float)j + 0.5f) * inv_q);
+      const int c = 4 * (j - r * Q4);
+      const double2* at = reinterpret_cast<const double2*>(buf + r * LD + c);
+      double x[4];
+      if (c + 4 <= Kc) {
+        const double2 v0 = at[0], v1 = at[1];
+        x[0] = v0.x, x[1] = v0.y, x[2] = v1.x, x[3] = v1.y;
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) x[e] = c + e < Kc ? buf[r * LD + c + e] : 0.0;
+      }
+      put_slices_quad<S>(x, rk0[r], dst + j, sstride);
+    }
+  }
+}
+
 }  // namespace
+
+int rowtile_rows_log2(int64_t kpad) {
+  int rl = 0;
+  while (rl < 6 && ((kpad << (rl + 1)) <= kRowTileElems)) ++rl;   // K = 4096: 2 rows
+  return rl;
+}
+
+// column offsets, row offsets, row maxima, row scale keys, then the rows
+static size_t rowtile_head_bytes(int64_t K, int64_t R) {
+  return ((size_t)(K + 2 * R) * 8 + (size_t)R * 4 + 15) / 16 * 16;
+}
+
+size_t rowtile_smem_bytes(int64_t K, int64_t kpad) {
+  const int64_t R = (int64_t)1 << rowtile_rows_log2(kpad);
+  return rowtile_head_bytes(K, R) + (size_t)R * (kpad + 2) * 8;
+}
+
+cudaError_t launch_rowtile(const Problem& p, const Tables& t, int n_slices, const bool* on,
+                           const double* u, const double* v, void* ua, void* va, int32_t* eu,
+                           int32_t* ev, int64_t kpad, unsigned* err, unsigned long long* zero64,
+                           int64_t zero64_n, cudaStream_t st) {
+  if (n_slices < 1 || n_slices > kMaxSlices || p.es != 1 || p.K < 1 || kpad > kRowTileMaxK ||
+      kpad % 32 != 0 || kpad < p.K)
+    return cudaErrorInvalidValue;
+  void (*kern)(RowTileArgs) = nullptr;
+  switch (n_slices) {
+    case 1: kern = rowtile_kernel<1>; break;
+    case 2: kern = rowtile_kernel<2>; break;
+    case 3: kern = rowtile_kernel<3>; break;
+    case 4: kern = rowtile_kernel<4>; break;
+    case 5: kern = rowtile_kernel<5>; break;
+    default: kern = rowtile_kernel<6>; break;
+  }
+  RowTileArgs a;
+  a.p = p;
+  a.t = t;
+  a.kpad = kpad;
+  a.rlog = rowtile_rows_log2(kpad);
+  const int64_t R = (int64_t)1 << a.rlog;
+  const int64_t units[2] = {on[0] ? (int64_t)p.n_q * ((p.M + R - 1) / R) : 0,
+                            on[1] ? (int64_t)p.n_q * ((p.N + R - 1) / R) : 0};
+  if (units[0] + units[1] > 0x7FFFFFFFll) return cudaErrorInvalidValue;
+  a.units[0] = (uint32_t)units[0];
+  a.units[1] = (uint32_t)units[1];
+  a.src[0] = u;
+  a.src[1] = v;
+  a.dst[0] = (uint32_t*)ua;
+  a.dst[1] = (uint32_t*)va;
+  a.exps[0] = eu;
+  a.exps[1] = ev;
+  a.fast_rows[0] = rows_fast(p.u);
+  a.fast_rows[1] = rows_fast(p.v);
+  a.buf_off = rowtile_head_bytes(p.K, R);
+  a.err = err;
+  a.zero64 = zero64;
+  a.zero64_n = zero64_n;
+  const size_t smem = rowtile_smem_bytes(p.K, kpad);
+  // the attribute and the occupancy are taken once per instance and device
+  // (kept per host thread)
+  thread_local size_t set_for[kMaxSlices + 1][16] = {};
+  thread_local int resident[kMaxSlices + 1][16] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 16) return cudaErrorInvalidDevice;
+  if (set_for[n_slices][dev] < smem) {
+    e = cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    set_for[n_slices][dev] = smem;
+    resident[n_slices][dev] = 0;
+  }
+  if (resident[n_slices][dev] == 0) {
+    int sms = 0, per = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, RT_THREADS, smem);
+    if (e != cudaSuccess) return e;
+    resident[n_slices][dev] = sms * (per > 0 ? per : 1);
+  }
+  const int64_t work = units[0] + units[1];
+  const int64_t zero_ctas = (zero64_n + RT_THREADS - 1) / RT_THREADS;
+  int64_t grid = work > 0 ? work : (zero_ctas > 0 ? zero_ctas : 1);
+  if (grid > resident[n_slices][dev]) grid = resident[n_slices][dev];
+  kern<<<(unsigned)grid, RT_THREADS, smem, st>>>(a);
+  ++g_kernel_launches;
+  return cudaGetLastError();
+}
 
 cudaError_t launch_fill_zero(double* w, int64_t n, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;

@@ -166,6 +166,40 @@ def test_engine_of_each_form_is_reported():
     assert peps.info.M == 2 and peps.info.tensor_core == 0
 
 
+def test_preparation_kernel_of_each_operand_is_reported():
+    """plan.info.single_read_prep: bits 0/1 (U/V) for rows of long contiguous
+    runs (streamed by bulk copies), bits 2/3 for short rows (padded K <= 4096,
+    whole rows per CTA); neither: the two-phase kernel (scan, grid barrier,
+    slicing).  TF32 and float64 plans prepare no slices."""
+    spec = lambda t: (t.signs, t.charge, t.dims)
+    c = WL.CC_LADDER
+    cc = sc.Plan(c.einsum, c.moduli, spec(c.u), spec(c.v), "split_bf16").info
+    assert cc.K > 4096 and cc.single_read_prep == 1
+    for prec, want in (("split_bf16", 12), ("tf32", 0), ("fp64", 0)):
+        p1 = sc.Plan(WL.MPS_STEP1, (WL.MPS_G,), spec(WL.MPS_E), spec(WL.MPS_A), prec)
+        p2 = sc.Plan(WL.MPS_STEP2, (WL.MPS_G,), p1.sym_w, spec(WL.MPS_A), prec)
+        assert p1.info.single_read_prep == want and p2.info.single_read_prep == want
+    # ij,jk: U's rows run along K, V's rows are the unit-stride side (at most
+    # K = 2048 on the short-row kernel)
+    for K, want in ((2048, 12), (2049, 4), (4096, 4), (4097, 0), (8192, 0)):
+        p = sc.Plan("ij,jk->ik", (2,), ((1, -1), (0,), (64, K)), ((1, -1), (0,), (K, 64)),
+                    "split_bf16")
+        assert p.info.K == K and p.info.single_read_prep == want
+    # U's rows are runs of 4096 contiguous entries (bulk copies); V's rows run
+    # along K too and take the short-row kernel, or are the unit-stride side
+    # and take the two-phase kernel
+    p = sc.Plan("ij,kj->ik", (2,), ((1, -1), (0,), (1024, 4096)), ((1, -1), (0,), (64, 4096)),
+                "split_bf16")
+    assert p.info.single_read_prep == 1 | 8
+    p = sc.Plan("ij,jk->ik", (2,), ((1, -1), (0,), (1024, 4096)), ((1, -1), (0,), (4096, 64)),
+                "split_bf16")
+    assert p.info.single_read_prep == 1
+    # short rows with runs: the short-row kernel
+    p = sc.Plan("ij,kj->ik", (2,), ((1, -1), (0,), (4096, 1024)), ((1, -1), (0,), (64, 1024)),
+                "split_bf16")
+    assert p.info.single_read_prep == 4 | 8
+
+
 class _FakeTensor:
     def __init__(self, dev):
         self.dev = dev

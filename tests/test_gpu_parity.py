@@ -315,25 +315,31 @@ def test_split_bit_exact_on_integer_inputs(sc, k_sectors, D):
     assert np.array_equal(got, want.astype(np.float64))
 
 
-def test_single_read_prep_bit_exact_on_integer_inputs(sc):
-    """The single-read preparation (rows streamed into shared memory by bulk
-    copies of contiguous runs) on a shape that takes it: integer inputs of two
-    BF16 digits must give the exact integer product rounded once, bit for bit,
-    as in the two-phase preparation."""
-    G, D_i, D_j, D_k = 2, 1024, 4096, 64
+@pytest.mark.parametrize("einsum,D_i,D_j,prep", [("ij,jk->ik", 1024, 4096, 1), ("ij,kj->ik", 1024, 4096, 1 | 8),
+                                                  ("ij,kj->ik", 1024, 1000, 4 | 8),
+                                                  ("ij,jk->ik", 1024, 2000, 4 | 8),
+                                                  ("ij,jk->ik", 1024, 3000, 1), ("ij,jk->ik", 500, 3000, 4)])
+def test_single_read_prep_bit_exact_on_integer_inputs(sc, einsum, D_i, D_j, prep):
+    """The single-read preparations on shapes that take them (plan bits 0/1:
+    rows streamed by bulk copies of contiguous runs; 2/3: whole short rows per
+    CTA, gathered along the rows or across them; neither: the two-phase
+    kernel), alone and side by side: integer inputs of two BF16 digits must give
+    the exact integer product rounded once, bit for bit."""
+    G, D_k = 2, 72
     su = ((1, -1), (0,), (D_i, D_j))
-    sv = ((1, -1), (0,), (D_j, D_k))
-    rng = np.random.default_rng(611)
+    sv = ((1, -1), (0,), (D_j, D_k) if einsum == "ij,jk->ik" else (D_k, D_j))
+    rng = np.random.default_rng(611 + D_j)
     u = rng.integers(-4096, 4097, size=(G, D_i, D_j)).astype(np.float64)
-    v = rng.integers(-4096, 4097, size=(G, D_j, D_k)).astype(np.float64)
+    v = rng.integers(-4096, 4097, size=(G,) + sv[2]).astype(np.float64)
     u[:, :4, :] = 4096.0
     u[:, 4:6, :] = -4096.0
     u[:, 6, :] = 0.0              # an all-zero row
-    p = sc.Plan("ij,jk->ik", (G,), su, sv, "split_bf16")
-    assert p.info.single_read_prep & 1
+    p = sc.Plan(einsum, (G,), su, sv, "split_bf16")
+    assert p.info.single_read_prep == prep
     got = host(p.contract(dev(u), dev(v)))
     p.check_device_error()
-    want = np.stack([np.matmul(u[q].astype(np.int64), v[q].astype(np.int64)) for q in range(G)])
+    vm = v if einsum == "ij,jk->ik" else np.swapaxes(v, 1, 2)
+    want = np.stack([np.matmul(u[q].astype(np.int64), vm[q].astype(np.int64)) for q in range(G)])
     assert np.array_equal(got, want.astype(np.float64))
 
 
