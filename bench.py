@@ -305,7 +305,9 @@ def rooflines(args, plans, prep, gemm, pk):
         achieved = nbytes / (prep_ms * 1e-3) / 1e9
         names = []
         for pl in plans:
-            names += [k for k in prep_kernels(pl) if k not in names]
+            for k in prep_kernels(pl):
+                if k not in names:
+                    names.append(k)
         label = "+".join(names)
         key = f"{label}/{args.precision}/{args.workload}"
         out.append({"kernel": label, "bound": "hbm", "achieved": round(achieved, 1),
