@@ -481,8 +481,8 @@ def run_ours(args, rank, world):
         _, t_or, reps = time_oracle(args.workload, *inputs_host, budget_s=args.cpu_budget, c=ctr)
         line["cpu_baseline"] = {"value": round(flops / t_or / 1e12, 6), "unit": "TFLOP/s",
                                 "cores": _CORES, "kind": "oracle",
-                                "sample": f"whole step (both contractions), block-loop route, "
-                                          f"median of {reps} runs, {t_or * 1e3:.1f} ms each"}
+                                "sample": f"whole step ({'both contractions' if args.workload == 'mps' else 'the contraction'}), "
+                                          f"block-loop route, median of {reps} runs, {t_or * 1e3:.1f} ms each"}
     return line
 
 
