@@ -693,6 +693,7 @@ __global__ void __launch_bounds__(RS_THREADS, 1) rowstream_kernel(const __grid_c
   __shared__ __align__(8) uint64_t bars[kRsMaxBufs];
   __shared__ unsigned long long red[RS_THREADS / 32];
   __shared__ int32_t key_s;
+  __shared__ int exact_s;
   __shared__ int abort_s;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t buf_elems = (a.K + 15) / 16 * 16;   // 128-byte aligned buffers
@@ -725,22 +726,50 @@ __global__ void __launch_bounds__(RS_THREADS, 1) rowstream_kernel(const __grid_c
       break;
     }
     const double* row = bufs + slot * buf_elems;
-    // the row maximum (integer max of the IEEE bit patterns)
-    uint64_t mx = 0;
-    for (int64_t c = tid; c < a.K; c += RS_THREADS) mx = max(mx, abs_bits(row[c]));
-    for (int o = 16; o > 0; o >>= 1) mx = max(mx, (uint64_t)__shfl_xor_sync(0xffffffffu, (unsigned long long)mx, o));
-    if (lane == 0) red[warp] = mx;
+    // the row maximum (integer max of the IEEE bit patterns) over the high
+    // words: sign dropped, the exponent and the top 20 mantissa bits decide
+    // the row's scale whenever they are not all zero
+    {
+      const uint32_t* hw = reinterpret_cast<const uint32_t*>(row) + 1;
+      uint32_t mh = 0;
+#pragma unroll 4
+      for (int64_t c = tid; c < a.K; c += RS_THREADS) mh = max(mh, hw[2 * c] & 0x7FFFFFFFu);
+      for (int o = 16; o > 0; o >>= 1) mh = max(mh, __shfl_xor_sync(0xffffffffu, mh, o));
+      if (lane == 0) red[warp] = (unsigned long long)mh << 32;
+    }
     __syncthreads();
     if (tid == 0) {
       uint64_t m = 0;
       for (int w = 0; w < RS_THREADS / 32; ++w) m = max(m, (uint64_t)red[w]);
-      unsigned bad = 0;
-      const int32_t key = row_key<S>(m, bad);
-      if (bad) atomicOr(a.err, (unsigned)DEVERR_NONFINITE);
-      a.exps[g] = key;
-      key_s = key;
+      exact_s = m == 0;
+      if (m != 0) {
+        unsigned bad = 0;
+        const int32_t key = row_key<S>(m, bad);
+        if (bad) atomicOr(a.err, (unsigned)DEVERR_NONFINITE);
+        a.exps[g] = key;
+        key_s = key;
+      }
     }
     __syncthreads();
+    if (exact_s) {
+      // all high words zero (a zero row, or entries below 2^-1042 only): the
+      // exact maximum of the whole bit patterns
+      uint64_t mx = 0;
+      for (int64_t c = tid; c < a.K; c += RS_THREADS) mx = max(mx, abs_bits(row[c]));
+      for (int o = 16; o > 0; o >>= 1) mx = max(mx, (uint64_t)__shfl_xor_sync(0xffffffffu, (unsigned long long)mx, o));
+      if (lane == 0) red[warp] = mx;
+      __syncthreads();
+      if (tid == 0) {
+        uint64_t m = 0;
+        for (int w = 0; w < RS_THREADS / 32; ++w) m = max(m, (uint64_t)red[w]);
+        unsigned bad = 0;
+        const int32_t key = row_key<S>(m, bad);
+        if (bad) atomicOr(a.err, (unsigned)DEVERR_NONFINITE);
+        a.exps[g] = key;
+        key_s = key;
+      }
+      __syncthreads();
+    }
     const int k0 = row_k0(key_s, S);
     // the digits, four adjacent columns per thread and step (zeros beyond K)
     uint2* d = reinterpret_cast<uint2*>(a.dst) + g * (a.kpad / 4);
@@ -837,10 +866,13 @@ __global__ void __launch_bounds__(RT_THREADS) rowtile_kernel(const __grid_consta
   int64_t* roff = coff + Kc;
   unsigned long long* rmx = (unsigned long long*)(roff + R);
   int32_t* rk0 = (int32_t*)(rmx + R);
-  // index splits i = r * n + c by a float reciprocal: exact while i / n <= 64
+  // index split j = r * n + c by a float reciprocal: exact while j / n <= 64
   // and n <= 4096 (the error, below 2^-17, stays under the 0.5 / n margin)
-  const float inv_k = 1.0f / (float)Kc;
   const float inv_q = 1.0f / (float)(kpad >> 2);
+  // row walks over columns: wpr warps per row when R < 16, else a warp per row
+  constexpr int NW = RT_THREADS / 32;
+  const int wpr = R < NW ? NW / R : 1;
+  const int sub = warp % wpr;
   double* buf = (double*)(rt_smem + a.buf_off);
   const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + tid; i < a.zero64_n; i += gthreads) a.zero64[i] = 0ull;
@@ -870,35 +902,55 @@ __global__ void __launch_bounds__(RT_THREADS) rowtile_kernel(const __grid_consta
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
-    const int n = R * Kc;
-    const bool fr = a.fast_rows[op];
-    for (int i = tid; i < n; i += RT_THREADS) {
-      int r, k;
-      if (fr) {
-        r = i & (R - 1);
-        k = i >> a.rlog;
-      } else {
-        r = __float2int_rz(((float)i + 0.5f) * inv_k);
-        k = i - r * Kc;
+    if (a.fast_rows[op]) {
+      // consecutive threads on consecutive rows (the unit-stride side); a
+      // thread keeps one row (R divides the block) and walks its columns
+      const int r = tid & (R - 1);
+      const int64_t ro = roff[r];
+      const double* rowp = src + (ro >= 0 ? ro : 0);
+      double* brow = buf + r * LD;
+#pragma unroll 4
+      for (int k = tid >> a.rlog; k < Kc; k += RT_THREADS >> a.rlog) {
+        const int64_t co = coff[k];
+        const bool ok = ro >= 0 && co >= 0;
+        cp_async8(brow + k, ok ? rowp + co : src, ok ? 8u : 0u);
       }
-      const int64_t ro = roff[r], co = coff[k];
-      const bool ok = ro >= 0 && co >= 0;
-      cp_async8(buf + r * LD + k, ok ? src + ro + co : src, ok ? 8u : 0u);
+    } else {
+      // lanes on consecutive columns, wpr warps per row
+      for (int r = warp / wpr; r < R; r += NW / wpr) {
+        const int64_t ro = roff[r];
+        const double* rowp = src + (ro >= 0 ? ro : 0);
+        double* brow = buf + r * LD;
+#pragma unroll 4
+        for (int k = sub * 32 + lane; k < Kc; k += 32 * wpr) {
+          const int64_t co = coff[k];
+          const bool ok = ro >= 0 && co >= 0;
+          cp_async8(brow + k, ok ? rowp + co : src, ok ? 8u : 0u);
+        }
+      }
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
-    // row maxima: 8 / R warps per row when R < 8, else a warp per row
-    {
-      constexpr int NW = RT_THREADS / 32;
-      const int wpr = R < NW ? NW / R : 1;
-      const int sub = warp % wpr;
-      for (int r = warp / wpr; r < R; r += NW / wpr) {
-        uint64_t m = 0;
-        for (int k = sub * 32 + lane; k < Kc; k += 32 * wpr) m = max(m, abs_bits(buf[r * LD + k]));
-        for (int o = 16; o > 0; o >>= 1)
-          m = max(m, (uint64_t)__shfl_xor_sync(0xffffffffu, (unsigned long long)m, o));
-        if (lane == 0) atomicMax(&rmx[r], (unsigned long long)m);
-      }
+    // row maxima over the high words (sign dropped: the exponent and the top
+    // 20 mantissa bits decide the row's scale whenever they are not all zero)
+    for (int r = warp / wpr; r < R; r += NW / wpr) {
+      const uint32_t* hw = reinterpret_cast<const uint32_t*>(buf + r * LD) + 1;
+      uint32_t m = 0;
+#pragma unroll 4
+      for (int k = sub * 32 + lane; k < Kc; k += 32 * wpr) m = max(m, hw[2 * k] & 0x7FFFFFFFu);
+      for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+      if (lane == 0) atomicMax(&rmx[r], (unsigned long long)m << 32);
+    }
+    __syncthreads();
+    // rows whose high words are all zero (zero rows, or entries below 2^-1042
+    // only): the exact maximum of the whole bit patterns
+    for (int r = warp / wpr; r < R; r += NW / wpr) {
+      if (rmx[r] != 0ull) continue;
+      uint64_t m = 0;
+      for (int k = sub * 32 + lane; k < Kc; k += 32 * wpr) m = max(m, abs_bits(buf[r * LD + k]));
+      for (int o = 16; o > 0; o >>= 1)
+        m = max(m, (uint64_t)__shfl_xor_sync(0xffffffffu, (unsigned long long)m, o));
+      if (lane == 0 && m != 0) atomicMax(&rmx[r], (unsigned long long)m);
     }
     __syncthreads();
     for (int r = tid; r < R; r += RT_THREADS) {

@@ -334,13 +334,25 @@ def test_single_read_prep_bit_exact_on_integer_inputs(sc, einsum, D_i, D_j, prep
     u[:, :4, :] = 4096.0
     u[:, 4:6, :] = -4096.0
     u[:, 6, :] = 0.0              # an all-zero row
+    # a row of subnormals k * 2^-1050, |k| <= 127: every high word is zero (the
+    # row scale comes from the exact pass over the whole bit patterns) and the
+    # row scale is the clamped one, 2^(8S - 1076) = 2^-1036 at S = 5, at which
+    # each entry is the single BF16 digit k * 2^-8 below the top: its products
+    # with V's two digits stay in the exact diagonals
+    ks = rng.integers(-127, 128, size=(G, D_j))
+    u[:, 7, :] = np.ldexp(ks.astype(np.float64), -1050)
     p = sc.Plan(einsum, (G,), su, sv, "split_bf16")
     assert p.info.single_read_prep == prep
     got = host(p.contract(dev(u), dev(v)))
     p.check_device_error()
     vm = v if einsum == "ij,jk->ik" else np.swapaxes(v, 1, 2)
-    want = np.stack([np.matmul(u[q].astype(np.int64), vm[q].astype(np.int64)) for q in range(G)])
-    assert np.array_equal(got, want.astype(np.float64))
+    ui = u.copy()
+    ui[:, 7, :] = 0.0
+    want = np.stack([np.matmul(ui[q].astype(np.int64), vm[q].astype(np.int64)) for q in range(G)])
+    want = want.astype(np.float64)
+    for q in range(G):
+        want[q, 7, :] = np.ldexp((ks[q].astype(np.int64) @ vm[q].astype(np.int64)).astype(np.float64), -1050)
+    assert np.array_equal(got, want)
 
 
 def test_single_read_prep_nonfinite_is_reported(sc):
