@@ -201,6 +201,19 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
         "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
 }
+// 8 consecutive 32-bit TMEM columns of this warp's 32 lanes.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* r) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                 "=r"(r[7])
+               : "r"(taddr));
+}
+template <int W>
+__device__ __forceinline__ void tmem_ld_w(uint32_t taddr, uint32_t* r) {
+  if constexpr (W == 16) tmem_ld16(taddr, r);
+  else if constexpr (W == 8) tmem_ld8(taddr, r);
+  else tmem_ld4(taddr, r);
+}
 __device__ __forceinline__ void tmem_st4(uint32_t taddr, const uint32_t* r) {
   asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr),
                "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3])
@@ -677,21 +690,24 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     // after chunk c: the accumulators in drained_after(c) (always diagonal 2's;
     // every 2nd chunk diagonal 1's, every 4th diagonal 0's), as three
     // straight-line variants
+    // W columns per TMEM load and wait: 16 when only diagonal 2 is drained
+    // (the common case), 8 otherwise (registers: the running sums take 192)
     auto drain_top = [&](auto D0c, auto D1c) {
       constexpr bool d0 = decltype(D0c)::value, d1 = live1 && decltype(D1c)::value, d2 = live2;
+      constexpr int W = (!d0 && !d1) ? 16 : 8;
 #pragma unroll
-      for (int pc = 0; pc < 16; ++pc) {
-        uint32_t a0[4], a1[4], a2[4];
+      for (int pc = 0; pc < 64 / W; ++pc) {
+        uint32_t a0[W], a1[W], a2[W];
         (void)a0, (void)a1, (void)a2;   // unused in the variants that skip a diagonal
-        if constexpr (d0) tmem_ld4(lane_base + 0 + pc * 4, a0);
-        if constexpr (d1) tmem_ld4(lane_base + 128 + pc * 4, a1);
-        if constexpr (d2) tmem_ld4(lane_base + 256 + pc * 4, a2);
+        if constexpr (d0) tmem_ld_w<W>(lane_base + 0 + pc * W, a0);
+        if constexpr (d1) tmem_ld_w<W>(lane_base + 128 + pc * W, a1);
+        if constexpr (d2) tmem_ld_w<W>(lane_base + 256 + pc * W, a2);
         tmem_wait_ld();
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          if constexpr (d0) s0[pc * 4 + j] += (int32_t)__float_as_uint(__uint_as_float(a0[j]) + M0) - B0;
-          if constexpr (d1) s1[pc * 4 + j] += (int32_t)__float_as_uint(__uint_as_float(a1[j]) + M1) - B1;
-          if constexpr (d2) s2[pc * 4 + j] += (int32_t)__float_as_uint(__uint_as_float(a2[j]) + M2) - B2;
+        for (int j = 0; j < W; ++j) {
+          if constexpr (d0) s0[pc * W + j] += (int32_t)__float_as_uint(__uint_as_float(a0[j]) + M0) - B0;
+          if constexpr (d1) s1[pc * W + j] += (int32_t)__float_as_uint(__uint_as_float(a1[j]) + M1) - B1;
+          if constexpr (d2) s2[pc * W + j] += (int32_t)__float_as_uint(__uint_as_float(a2[j]) + M2) - B2;
         }
       }
     };
