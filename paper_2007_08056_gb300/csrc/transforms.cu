@@ -687,14 +687,54 @@ __device__ __forceinline__ void rs_issue(const RowStreamArgs& a, int64_t g, doub
   }
 }
 
+// Maximum of the high words of a row (sign dropped: the exponent and the top
+// 20 mantissa bits decide the row's scale whenever they are not all zero)
+// into *m: a shared-memory atomic per warp.
+__device__ __forceinline__ void rs_hi_max(const double* row, int64_t K, uint32_t* m, int tid, int lane) {
+  const uint32_t* hw = reinterpret_cast<const uint32_t*>(row) + 1;
+  uint32_t mh = 0;
+#pragma unroll 4
+  for (int64_t c = tid; c < K; c += RS_THREADS) mh = max(mh, hw[2 * c] & 0x7FFFFFFFu);
+  for (int o = 16; o > 0; o >>= 1) mh = max(mh, __shfl_xor_sync(0xffffffffu, mh, o));
+  if (lane == 0) atomicMax(m, mh);
+}
+
+// The row's scale from its high-word maximum m (read by every thread after a
+// barrier, so the branch is uniform): all high words zero (a zero row, or
+// entries below 2^-1042 only) takes the exact maximum of the whole bit
+// patterns, with one more barrier.  Thread 0 stores the exponent.
+template <int S>
+__device__ __forceinline__ int rs_row_k0(const RowStreamArgs& a, const double* row, int64_t g, uint32_t m,
+                                         unsigned long long* red, int tid, int warp, int lane) {
+  uint64_t ab = (uint64_t)m << 32;
+  if (m == 0) {
+    uint64_t mx = 0;
+    for (int64_t c = tid; c < a.K; c += RS_THREADS) mx = max(mx, abs_bits(row[c]));
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, (uint64_t)__shfl_xor_sync(0xffffffffu, (unsigned long long)mx, o));
+    if (lane == 0) red[warp] = mx;
+    __syncthreads();
+    for (int w = 0; w < RS_THREADS / 32; ++w) ab = max(ab, (uint64_t)red[w]);
+  }
+  unsigned bad = 0;
+  const int32_t key = row_key<S>(ab, bad);
+  if (tid == 0) {
+    if (bad) atomicOr(a.err, (unsigned)DEVERR_NONFINITE);
+    a.exps[g] = key;
+  }
+  return row_k0(key, S);
+}
+
+// Software-pipelined over the CTA's rows: iteration i writes the digits of
+// row i and takes the maximum of row i + 1 (whose copy was queued nbuf - 1
+// rows earlier), then one barrier frees row i's buffer for its refill and
+// publishes row i + 1's maximum.  The maxima rotate over three shared words,
+// each cleared two barriers before its next use.
 template <int S>
 __global__ void __launch_bounds__(RS_THREADS, 1) rowstream_kernel(const __grid_constant__ RowStreamArgs a) {
   extern __shared__ __align__(128) uint8_t rs_smem[];
   __shared__ __align__(8) uint64_t bars[kRsMaxBufs];
   __shared__ unsigned long long red[RS_THREADS / 32];
-  __shared__ int32_t key_s;
-  __shared__ int exact_s;
-  __shared__ int abort_s;
+  __shared__ uint32_t mxs[3];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t buf_elems = (a.K + 15) / 16 * 16;   // 128-byte aligned buffers
   double* bufs = (double*)rs_smem;
@@ -704,74 +744,32 @@ __global__ void __launch_bounds__(RS_THREADS, 1) rowstream_kernel(const __grid_c
     for (int i = 0; i < nbuf; ++i)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[i])) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    abort_s = 0;
   }
+  if (tid < 3) mxs[tid] = 0u;
   __syncthreads();
   if (warp == 0)
     for (int s = 0; s < nbuf; ++s) {
       const int64_t g = blockIdx.x + (int64_t)s * gridDim.x;
       if (g < rows) rs_issue(a, g, bufs + s * buf_elems, &bars[s], lane);
     }
-  int it = 0;
   int64_t g = blockIdx.x;
-  for (; g < rows; g += gridDim.x, ++it) {
-    const int slot = it % nbuf;
-    const uint32_t parity = (uint32_t)(it / nbuf) & 1u;
-    // every thread observes the copies' completion on the barrier
-    const bool ok = rs_wait(&bars[slot], parity);
+  int it = 0;
+  bool abort = false;
+  int first_pending = 0;   // on abort: the first row whose copy may be in flight
+  int k0 = 0;
+  if (g < rows) {
+    // row 0's maximum
+    const bool ok = rs_wait(&bars[0], 0u);
+    if (ok) rs_hi_max(bufs, a.K, &mxs[0], tid, lane);
     if (!ok && lane == 0) atomicOr(a.err, (unsigned)DEVERR_TIMEOUT);
-    if (__syncthreads_or(!ok)) {
-      if (tid == 0) abort_s = 1;
-      __syncthreads();
-      break;
-    }
+    abort = __syncthreads_or(!ok);
+    if (!abort) k0 = rs_row_k0<S>(a, bufs, g, *(volatile uint32_t*)&mxs[0], red, tid, warp, lane);
+  }
+  for (; !abort && g < rows; g += gridDim.x, ++it) {
+    const int slot = it % nbuf;
     const double* row = bufs + slot * buf_elems;
-    // the row maximum (integer max of the IEEE bit patterns) over the high
-    // words: sign dropped, the exponent and the top 20 mantissa bits decide
-    // the row's scale whenever they are not all zero
-    {
-      const uint32_t* hw = reinterpret_cast<const uint32_t*>(row) + 1;
-      uint32_t mh = 0;
-#pragma unroll 4
-      for (int64_t c = tid; c < a.K; c += RS_THREADS) mh = max(mh, hw[2 * c] & 0x7FFFFFFFu);
-      for (int o = 16; o > 0; o >>= 1) mh = max(mh, __shfl_xor_sync(0xffffffffu, mh, o));
-      if (lane == 0) red[warp] = (unsigned long long)mh << 32;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      uint64_t m = 0;
-      for (int w = 0; w < RS_THREADS / 32; ++w) m = max(m, (uint64_t)red[w]);
-      exact_s = m == 0;
-      if (m != 0) {
-        unsigned bad = 0;
-        const int32_t key = row_key<S>(m, bad);
-        if (bad) atomicOr(a.err, (unsigned)DEVERR_NONFINITE);
-        a.exps[g] = key;
-        key_s = key;
-      }
-    }
-    __syncthreads();
-    if (exact_s) {
-      // all high words zero (a zero row, or entries below 2^-1042 only): the
-      // exact maximum of the whole bit patterns
-      uint64_t mx = 0;
-      for (int64_t c = tid; c < a.K; c += RS_THREADS) mx = max(mx, abs_bits(row[c]));
-      for (int o = 16; o > 0; o >>= 1) mx = max(mx, (uint64_t)__shfl_xor_sync(0xffffffffu, (unsigned long long)mx, o));
-      if (lane == 0) red[warp] = mx;
-      __syncthreads();
-      if (tid == 0) {
-        uint64_t m = 0;
-        for (int w = 0; w < RS_THREADS / 32; ++w) m = max(m, (uint64_t)red[w]);
-        unsigned bad = 0;
-        const int32_t key = row_key<S>(m, bad);
-        if (bad) atomicOr(a.err, (unsigned)DEVERR_NONFINITE);
-        a.exps[g] = key;
-        key_s = key;
-      }
-      __syncthreads();
-    }
-    const int k0 = row_k0(key_s, S);
-    // the digits, four adjacent columns per thread and step (zeros beyond K)
+    // the digits of row it, four adjacent columns per thread and step (zeros
+    // beyond K)
     uint2* d = reinterpret_cast<uint2*>(a.dst) + g * (a.kpad / 4);
     for (int64_t q = tid; q < a.kpad / 4; q += RS_THREADS) {
       const int64_t c = 4 * q;
@@ -786,15 +784,33 @@ __global__ void __launch_bounds__(RS_THREADS, 1) rowstream_kernel(const __grid_c
       }
       put_slices_quad<S>(x, k0, d + q, a.slice_stride / 4);
     }
-    __syncthreads();   // every thread is done with this buffer
+    // the maximum of row it + 1
+    const int64_t g1 = g + gridDim.x;
+    const int slot1 = (it + 1) % nbuf;
+    bool ok = true;
+    if (g1 < rows) {
+      ok = rs_wait(&bars[slot1], (uint32_t)((it + 1) / nbuf) & 1u);
+      if (ok) rs_hi_max(bufs + slot1 * buf_elems, a.K, &mxs[(it + 1) % 3], tid, lane);
+      if (!ok && lane == 0) atomicOr(a.err, (unsigned)DEVERR_TIMEOUT);
+    }
+    // row it's buffer is free; row it + 1's maximum is complete
+    abort = __syncthreads_or(!ok);
+    if (abort) {
+      first_pending = it + 1;
+      break;
+    }
+    if (tid == 0) mxs[it % 3] = 0u;   // row it + 3 collects here, after the next barrier
     const int64_t gn = g + (int64_t)nbuf * gridDim.x;
     if (warp == 0 && gn < rows) rs_issue(a, gn, bufs + slot * buf_elems, &bars[slot], lane);
+    if (g1 < rows)
+      k0 = rs_row_k0<S>(a, bufs + slot1 * buf_elems, g1, *(volatile uint32_t*)&mxs[(it + 1) % 3], red, tid,
+                        warp, lane);
   }
   // the GEMM behind this kernel may start its launch
   asm volatile("griddepcontrol.launch_dependents;");
-  if (abort_s && tid == 0) {
+  if (abort && tid == 0) {
     // let the copies still in flight land before the CTA exits (bounded)
-    for (int k = it; k < it + nbuf; ++k) {
+    for (int k = first_pending; k < it + nbuf; ++k) {
       const int64_t gk = blockIdx.x + (int64_t)k * gridDim.x;
       if (gk >= rows) break;
       rs_wait(&bars[k % nbuf], (uint32_t)(k / nbuf) & 1u);
