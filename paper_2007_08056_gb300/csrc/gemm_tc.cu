@@ -214,6 +214,23 @@ __device__ __forceinline__ void tmem_ld_w(uint32_t taddr, uint32_t* r) {
   else if constexpr (W == 8) tmem_ld8(taddr, r);
   else tmem_ld4(taddr, r);
 }
+// Zeros into W consecutive 32-bit TMEM columns of this warp's 32 lanes.
+template <int W>
+__device__ __forceinline__ void tmem_zero_w(uint32_t taddr) {
+  const uint32_t z = 0u;
+  if constexpr (W == 16) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+        "{%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1};" ::"r"(taddr),
+        "r"(z)
+        : "memory");
+  } else {
+    static_assert(W == 8, "8 or 16 columns");
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1};" ::"r"(taddr),
+                 "r"(z)
+                 : "memory");
+  }
+}
 __device__ __forceinline__ void tmem_st4(uint32_t taddr, const uint32_t* r) {
   asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr),
                "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3])
@@ -243,10 +260,10 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
 
 // Instruction descriptor: FP32 accumulate, K-major A and B, M = 128,
 // N = the form's tile width.
-template <int KIND>
+template <int KIND, int N = TileCfg<KIND>::N>
 __host__ __device__ constexpr uint32_t idesc() {
   return (1u << 4) | ((KIND == MODE_SPLIT ? 1u : 2u) << 7) | ((KIND == MODE_SPLIT ? 1u : 2u) << 10) |
-         ((uint32_t)(TileCfg<KIND>::N >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
 }
 
 // RN(R * 2^e) as float64 using integer operations only (ties to even).
@@ -446,9 +463,8 @@ __device__ __forceinline__ void mma_ij(uint32_t tacc, uint64_t da, uint64_t db, 
   }
 }
 
-// Slice pairs of the exact diagonals 0, 1, 2, each into its own accumulator;
-// bit d of `fresh` makes diagonal d's first MMA overwrite its accumulator
-// (it was drained after the previous chunk).
+// TF32 form (one "slice"): the MMAs of a stage into accumulator 0; bit 0 of
+// `fresh` makes the first overwrite it.
 template <int KIND, int S>
 __device__ __forceinline__ void issue_top(uint32_t tmem, uint64_t da, uint64_t db, uint32_t id,
                                           uint32_t fresh) {
@@ -465,20 +481,56 @@ __device__ __forceinline__ void issue_top(uint32_t tmem, uint64_t da, uint64_t d
   });
 }
 
-// Slice pairs of diagonals 3 .. S-1, all into TMEM accumulator 3.
-template <int KIND, int S>
-__device__ __forceinline__ void issue_low(uint32_t tmem, uint64_t da, uint64_t db, uint32_t id,
-                                          bool fresh) {
-  static_for<(S > 3 ? S - 3 : 0)>([&](auto D3) {
-    constexpr int D = D3.value + 3;
-    static_for<D + 1>([&](auto I) {
-      if constexpr (I.value < S && D - I.value < S) {
-        static_for<TileCfg<KIND>::KSTEPS>([&](auto KK) {
-          constexpr bool first = D == 3 && I.value == 0 && KK.value == 0;
-          mma_ij<KIND, I.value, D - I.value, KK.value>(tmem + 384u, da, db, id,
-                                                       (fresh && first) ? 0u : 1u);
-        });
+// Split form, slice pairs (i, j) with i + j <= S - 1, one MMA each or two at
+// once: pairs (i, j) and (i, j + 1) whose targets are consecutive
+// accumulators (diagonals i + j and i + j + 1 <= 3, accumulator 3 holding every
+// diagonal >= 3) share one N = 256 MMA over B slices j and j + 1, which lie
+// one after the other in shared memory: the A slice is read once for both.
+// "top" entries touch an exact accumulator (diagonal <= 2), "low" entries only
+// accumulator 3.  Every MMA accumulates; the epilogue zeroes the accumulators
+// at the start of the tile and after each drain.
+struct PairSched {
+  int n_top = 0, n_low = 0;
+  int ti[21] = {}, tj[21] = {}, tw[21] = {};   // top: A slice, first B slice, 2 = combined
+  int li[21] = {}, lj[21] = {};
+};
+__host__ __device__ constexpr PairSched pair_sched(int S) {
+  PairSched r;
+  for (int i = 0; i < S; ++i) {
+    for (int j = 0; i + j <= S - 1; ++j) {
+      const bool combine = i + j <= 2 && i + j + 1 <= S - 1;
+      if (combine) {
+        r.ti[r.n_top] = i, r.tj[r.n_top] = j, r.tw[r.n_top] = 2, ++r.n_top;
+        ++j;
+      } else if (i + j <= 2) {
+        r.ti[r.n_top] = i, r.tj[r.n_top] = j, r.tw[r.n_top] = 1, ++r.n_top;
+      } else {
+        r.li[r.n_low] = i, r.lj[r.n_low] = j, ++r.n_low;
       }
+    }
+  }
+  return r;
+}
+
+template <int S>
+__device__ __forceinline__ void issue_top_acc(uint32_t tmem, uint64_t da, uint64_t db, uint32_t id128,
+                                              uint32_t id256) {
+  constexpr PairSched P = pair_sched(S);
+  static_for<P.n_top>([&](auto T) {
+    constexpr int I = P.ti[T.value], J = P.tj[T.value], D = I + J;
+    static_for<TileCfg<MODE_SPLIT>::KSTEPS>([&](auto KK) {
+      mma_ij<MODE_SPLIT, I, J, KK.value>(tmem + 128u * D, da, db, P.tw[T.value] == 2 ? id256 : id128, 1u);
+    });
+  });
+}
+
+template <int S>
+__device__ __forceinline__ void issue_low_acc(uint32_t tmem, uint64_t da, uint64_t db, uint32_t id128) {
+  constexpr PairSched P = pair_sched(S);
+  static_for<P.n_low>([&](auto T) {
+    constexpr int I = P.li[T.value], J = P.lj[T.value];
+    static_for<TileCfg<MODE_SPLIT>::KSTEPS>([&](auto KK) {
+      mma_ij<MODE_SPLIT, I, J, KK.value>(tmem + 384u, da, db, id128, 1u);
     });
   });
 }
@@ -531,7 +583,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   uint64_t* drain = acc_full + 1;
   uint64_t* low_full = drain + 1;
   uint64_t* low_empty = low_full + 1;
-  int64_t* coff = (int64_t*)(low_empty + 1);   // [TNk] W column offsets
+  uint64_t* zero_done = low_empty + 1;          // split form: accumulators zeroed
+  int64_t* coff = (int64_t*)(zero_done + 1);   // [TNk] W column offsets
   int32_t* cexp = (int32_t*)(coff + TNk);       // [TNk] column exponents
   int64_t* roffs = (int64_t*)(cexp + TNk);       // [TM] W row offsets
   int32_t* rexps = (int32_t*)(roffs + TM);       // [TM] row exponents
@@ -560,6 +613,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     mbar_init(drain, 1);
     mbar_init(low_full, 1);
     mbar_init(low_empty, 8);
+    mbar_init(zero_done, 8);
     ctl->abort = 0;
     ctl->err = args.err;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -640,21 +694,28 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         bool ok = true;
         // fold of accumulator 3 after chunk c: (c + 1) % kFoldChunks == 0, not the last chunk
         constexpr bool has_low = KIND == MODE_SPLIT && S >= 4;
-        if (cfirst) {
+        if (KIND == MODE_SPLIT && kb == 0) {
+          // the epilogue warps have zeroed the accumulators
+          ok = wait_phase(zero_done, 0, ctl);
+          tc_fence_after();
+        }
+        if (KIND == MODE_TF32) {
+          if (ok) issue_top<KIND, S>(tmem, da, db, id, kb == 0 ? 7u : 0u);
+        } else if (cfirst) {
           if (has_low && chunk > 0 && chunk % kFoldChunks == 0) {
-            ok = wait_phase(low_empty, (uint32_t)(chunk / kFoldChunks - 1) & 1, ctl);
+            ok = ok && wait_phase(low_empty, (uint32_t)(chunk / kFoldChunks - 1) & 1, ctl);
             tc_fence_after();
           }
-          if (ok) issue_low<KIND, S>(tmem, da, db, id, kb == 0);
+          if (ok) issue_low_acc<S>(tmem, da, db, id);
           if (chunk > 0) {
-            ok = wait_phase(top_empty, (chunk - 1) & 1, ctl);
+            ok = ok && wait_phase(top_empty, (chunk - 1) & 1, ctl);
             tc_fence_after();
           }
-          if (ok) issue_top<KIND, S>(tmem, da, db, id, KIND == MODE_TF32 ? 7u : drained_after(chunk - 1));
+          if (ok) issue_top_acc<S>(tmem, da, db, id, idesc<KIND, 256>());
         } else {
-          issue_top<KIND, S>(tmem, da, db, id, 0u);
+          issue_top_acc<S>(tmem, da, db, id, idesc<KIND, 256>());
           if (!final_chunk) tc_commit(top_full);
-          issue_low<KIND, S>(tmem, da, db, id, false);
+          issue_low_acc<S>(tmem, da, db, id);
           if (has_low && !final_chunk && (chunk + 1) % kFoldChunks == 0) tc_commit(low_full);
         }
         tc_commit(&empty[st]);
@@ -709,10 +770,24 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           if constexpr (d1) s1[pc * W + j] += (int32_t)__float_as_uint(__uint_as_float(a1[j]) + M1) - B1;
           if constexpr (d2) s2[pc * W + j] += (int32_t)__float_as_uint(__uint_as_float(a2[j]) + M2) - B2;
         }
+        // the MMAs accumulate: a drained accumulator restarts from zero
+        if constexpr (d0) tmem_zero_w<W>(lane_base + 0 + pc * W);
+        if constexpr (d1) tmem_zero_w<W>(lane_base + 128 + pc * W);
+        if constexpr (d2) tmem_zero_w<W>(lane_base + 256 + pc * W);
       }
+      tmem_wait_st();
     };
     bool ok = true;
     if (KIND == MODE_SPLIT) {
+      // the accumulators start from zero (every MMA accumulates)
+#pragma unroll
+      for (int acc = 0; acc < 4; ++acc)
+#pragma unroll
+        for (int pc = 0; pc < 4; ++pc) tmem_zero_w<16>(lane_base + 128 * acc + pc * 16);
+      tmem_wait_st();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(zero_done);
       for (int c = 0; c + 1 < n_chunks; ++c) {
         if (!wait_phase_sleep(top_full, c & 1, ctl)) {
           ok = false;
@@ -1045,7 +1120,7 @@ cudaError_t launch_tc_mode(const Problem& p, const Tables& tab, const void* a, c
   args.wrow = tab.wrow;
   args.wcol = tab.wcol;
   constexpr int TNk = TileCfg<KIND>::N;
-  size_t smem = 1024 + tile_region_bytes<KIND, S, STAGES>() + 8 * (2 * STAGES + 6) + 8 * TNk + 4 * TNk +
+  size_t smem = 1024 + tile_region_bytes<KIND, S, STAGES>() + 8 * (2 * STAGES + 7) + 8 * TNk + 4 * TNk +
                 8 * TM + 4 * TM + 16 + 64;
   auto kern = gemm_tc_kernel<KIND, S, STAGES, GEN>;
   thread_local bool attr_set[64] = {};
