@@ -710,8 +710,9 @@ symctr_status build(const char* einsum, int n_moduli, const int32_t* moduli, con
   }
 
   // Single-read preparation (split form): an operand whose aligned rows are
-  // column-contiguous runs of at least 128 entries, at most kRowStreamMaxK
-  // long, every run start and row offset even (16-byte bulk copies), and
+  // column-contiguous runs of at least 128 entries, at most kRowClusterMaxK
+  // long (clusters of CTAs beyond kRowStreamMaxK), every run start and row
+  // offset even (16-byte bulk copies), and
   // large enough (>= 32 MB) to be bandwidth-bound.
   if (P->tensor_core && prec == SYMCTR_SPLIT_BF16 && !P->general) {
     const AxisMap* rows[2] = {&pr.u.rows, &pr.v.rows};
@@ -726,7 +727,7 @@ symctr_status build(const char* einsum, int n_moduli, const int32_t* moduli, con
       if (rows_contig || c.n == 0 || c.bstride[c.n - 1] != 1) continue;
       int64_t L = c.D[c.n - 1];
       for (int i = c.n - 2; i >= 0 && c.bstride[i] == L; --i) L *= c.D[i];
-      if (L < 128 || L % 2 != 0 || pr.K % L != 0 || pr.K > kRowStreamMaxK) continue;
+      if (L < 128 || L % 2 != 0 || pr.K % L != 0 || pr.K > kRowClusterMaxK) continue;
       if ((int64_t)pr.n_q * R[op] * pr.K < ((int64_t)4 << 20)) continue;
       bool even = true;
       for (int64_t i = 0; i < (int64_t)pr.n_q * R[op] && even; ++i) even = rtab[op][i] % 2 == 0;

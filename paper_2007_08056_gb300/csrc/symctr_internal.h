@@ -215,8 +215,12 @@ cudaError_t launch_prep(const Problem& p, const Tables& t, bool split, int n_sli
                         cudaStream_t st);
 // Single-read split-form preparation of operand op (0 = U, 1 = V) whose
 // aligned rows are runs of `run` contiguous reduced-form entries and at most
-// kRowStreamMaxK long (plan-time eligibility: row_run in plan.cpp).
+// kRowClusterMaxK long (plan-time eligibility: row_run in plan.cpp); rows
+// longer than kRowStreamMaxK take the cluster form.
 constexpr int64_t kRowStreamMaxK = 8192;
+// Longer rows (up to kRowClusterMaxK) are held by a cluster of up to 8 CTAs,
+// each streaming one segment of every row.
+constexpr int64_t kRowClusterMaxK = 8 * kRowStreamMaxK;
 cudaError_t launch_rowstream(const Problem& p, const Tables& t, int op, int n_slices, int64_t run,
                              const double* src, void* slices, int32_t* exps, int64_t kpad,
                              unsigned* err, cudaStream_t st);

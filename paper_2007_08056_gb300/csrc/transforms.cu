@@ -646,6 +646,7 @@ struct RowStreamArgs {
   int32_t* exps;            // [n_q][R] biased row exponents
   unsigned* err;
   int nbuf;                 // row buffers (<= kRsMaxBufs)
+  int64_t seg;              // cluster form: columns per CTA (rank r holds [r seg, (r+1) seg))
 };
 
 // Bounded wait on a bulk-copy barrier (about 2 s of SM clock); false on expiry.
@@ -816,6 +817,239 @@ __global__ void __launch_bounds__(RS_THREADS, 1) rowstream_kernel(const __grid_c
       rs_wait(&bars[k % nbuf], (uint32_t)(k / nbuf) & 1u);
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// Rows longer than one CTA's shared memory (K > kRowStreamMaxK): a cluster of C
+// CTAs holds each row, CTA r its columns [r seg, (r+1) seg).  Each CTA streams
+// its segment with bulk copies (the run pieces inside the segment), takes the
+// maximum of its high words, and the cluster barrier lets every CTA read the
+// other segments' maxima from distributed shared memory: the row's scale is
+// the same in every CTA, each writes the digits of its own segment, and every
+// entry crosses HBM once.  Pipelined like the one-CTA kernel (the digits of
+// row i and the maxima of row i + 1 between one cluster barrier); a failed
+// copy wait is published in the same rotating slots, so the whole cluster
+// leaves the loop together.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t cl_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cl_size() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cl_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// a 32-bit / 64-bit word of CTA `rank`'s shared memory at this CTA's address of it
+__device__ __forceinline__ uint32_t cl_ld32(const void* p, uint32_t rank) {
+  uint32_t v;
+  asm volatile(
+      "{\n\t.reg .b32 ra;\n\tmapa.shared::cluster.u32 ra, %1, %2;\n\t"
+      "ld.shared::cluster.u32 %0, [ra];\n\t}\n"
+      : "=r"(v)
+      : "r"(smem_u32(p)), "r"(rank)
+      : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned long long cl_ld64(const void* p, uint32_t rank) {
+  unsigned long long v;
+  asm volatile(
+      "{\n\t.reg .b32 ra;\n\tmapa.shared::cluster.u32 ra, %1, %2;\n\t"
+      "ld.shared::cluster.u64 %0, [ra];\n\t}\n"
+      : "=l"(v)
+      : "r"(smem_u32(p)), "r"(rank)
+      : "memory");
+  return v;
+}
+
+// Warp 0: the bulk copies of row g's columns [s0, s1) into buf (the pieces of
+// the runs of L contiguous entries that overlap the segment).
+__device__ __forceinline__ void cl_issue(const RowStreamArgs& a, int64_t g, int64_t s0, int64_t s1, double* buf,
+                                         uint64_t* bar, int lane) {
+  const int64_t b = g / a.R;
+  const int64_t roff = a.rtab[g];
+  if (lane == 0)
+    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"((uint32_t)((s1 - s0) * 8))
+                 : "memory");
+  __syncwarp();
+  for (int64_t j = s0 / a.L + lane; j * a.L < s1; j += 32) {
+    const int64_t c0 = max(j * a.L, s0), c1 = min((j + 1) * a.L, s1);
+    const double* from = a.src + roff + a.ctab[b * a.K + j * a.L] + (c0 - j * a.L);
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(buf + (c0 - s0))),
+        "l"(from), "r"((uint32_t)((c1 - c0) * 8)), "r"(smem_u32(bar))
+        : "memory");
+  }
+}
+
+// Warp 0 reads slot x's maximum and copy-failure flag of every CTA of the
+// cluster (one remote load per lane) and leaves their maximum and OR in
+// this CTA's shared memory for all its threads (after the CTA barrier).
+__device__ __forceinline__ void cl_gather(const uint32_t* mx, const uint32_t* fl, uint32_t C, int warp, int lane,
+                                          uint32_t* gm, uint32_t* gf) {
+  if (warp == 0) {
+    uint32_t m = 0u, f = 0u;
+    if ((uint32_t)lane < C) {
+      m = cl_ld32(mx, (uint32_t)lane);
+      f = cl_ld32(fl, (uint32_t)lane);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+      f |= __shfl_xor_sync(0xffffffffu, f, o);
+    }
+    if (lane == 0) *gm = m, *gf = f;
+  }
+  __syncthreads();
+}
+
+// The row's scale from the cluster's high-word maximum m (the same in every
+// CTA, so the branch is uniform); m = 0: the exact maximum of the whole bit
+// patterns, exchanged through red64 with one more cluster barrier.  CTA 0
+// stores the exponent.
+template <int S>
+__device__ __forceinline__ int cl_row_k0(const RowStreamArgs& a, const double* seg_buf, int64_t n, int64_t g,
+                                         uint32_t m, unsigned long long* redw, unsigned long long* red64,
+                                         uint32_t C, uint32_t rank, int tid, int warp, int lane) {
+  uint64_t ab = (uint64_t)m << 32;
+  if (m == 0) {
+    uint64_t mx = 0;
+    for (int64_t c = tid; c < n; c += RS_THREADS) mx = max(mx, abs_bits(seg_buf[c]));
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, (uint64_t)__shfl_xor_sync(0xffffffffu, (unsigned long long)mx, o));
+    if (lane == 0) redw[warp] = mx;
+    __syncthreads();
+    if (tid == 0) {
+      uint64_t v = 0;
+      for (int w = 0; w < RS_THREADS / 32; ++w) v = max(v, (uint64_t)redw[w]);
+      *red64 = v;
+    }
+    cl_sync();
+    if (warp == 0) {
+      uint64_t v = (uint32_t)lane < C ? (uint64_t)cl_ld64(red64, (uint32_t)lane) : 0ull;
+      for (int o = 16; o > 0; o >>= 1) v = max(v, (uint64_t)__shfl_xor_sync(0xffffffffu, (unsigned long long)v, o));
+      if (lane == 0) redw[0] = v;
+    }
+    __syncthreads();
+    ab = max(ab, (uint64_t)redw[0]);
+  }
+  unsigned bad = 0;
+  const int32_t key = row_key<S>(ab, bad);
+  if (rank == 0 && tid == 0) {
+    if (bad) atomicOr(a.err, (unsigned)DEVERR_NONFINITE);
+    a.exps[g] = key;
+  }
+  return row_k0(key, S);
+}
+
+template <int S>
+__global__ void __launch_bounds__(RS_THREADS, 1) rowcluster_kernel(const __grid_constant__ RowStreamArgs a) {
+  extern __shared__ __align__(128) uint8_t rs_smem[];
+  __shared__ __align__(8) uint64_t bars[kRsMaxBufs];
+  __shared__ unsigned long long redw[RS_THREADS / 32];
+  __shared__ unsigned long long red64;
+  __shared__ uint32_t mxs[3];
+  __shared__ uint32_t flg[3];
+  __shared__ uint32_t gm, gf;   // the cluster's maximum and failure flag of the slot just gathered
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t C = cl_size(), rank = cl_rank();
+  const int64_t cid = blockIdx.x / C, ncl = gridDim.x / C;
+  const int64_t s0 = (int64_t)rank * a.seg, s1 = min(a.K, s0 + a.seg);
+  const int64_t n = s1 > s0 ? s1 - s0 : 0;                  // this CTA's columns of a row
+  const int64_t q0 = s0 / 4, q1 = rank == C - 1 ? a.kpad / 4 : s1 / 4;   // its digit quads
+  const int64_t buf_elems = (a.seg + 15) / 16 * 16;
+  double* bufs = (double*)rs_smem;
+  const int64_t rows = (int64_t)a.n_q * a.R;
+  const int nbuf = a.nbuf;
+  if (tid == 0) {
+    for (int i = 0; i < nbuf; ++i)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[i])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (tid < 3) mxs[tid] = 0u, flg[tid] = 0u;
+  cl_sync();
+  if (warp == 0 && n > 0)
+    for (int s = 0; s < nbuf; ++s) {
+      const int64_t g = cid + (int64_t)s * ncl;
+      if (g < rows) cl_issue(a, g, s0, s1, bufs + s * buf_elems, &bars[s], lane);
+    }
+  int64_t g = cid;
+  int it = 0;
+  bool abort = false;
+  int first_pending = 0;
+  int k0 = 0;
+  if (g < rows) {
+    const bool ok = n == 0 || rs_wait(&bars[0], 0u);
+    if (ok && n > 0) rs_hi_max(bufs, n, &mxs[0], tid, lane);
+    if (!ok) flg[0] = 1u;
+    cl_sync();
+    cl_gather(&mxs[0], &flg[0], C, warp, lane, &gm, &gf);
+    abort = gf != 0u;
+    if (abort) {
+      if (tid == 0 && !ok) atomicOr(a.err, (unsigned)DEVERR_TIMEOUT);
+    } else {
+      k0 = cl_row_k0<S>(a, bufs, n, g, gm, redw, &red64, C, rank, tid, warp, lane);
+    }
+  }
+  for (; !abort && g < rows; g += ncl, ++it) {
+    const int slot = it % nbuf;
+    const double* row = bufs + slot * buf_elems;
+    // the digits of this CTA's segment of row it (the last CTA also writes the
+    // zero digits of the padding columns K..kpad-1)
+    uint2* d = reinterpret_cast<uint2*>(a.dst) + g * (a.kpad / 4);
+    for (int64_t q = q0 + tid; q < q1; q += RS_THREADS) {
+      const int64_t c = 4 * q;
+      double x[4];
+      if (c + 4 <= s1) {
+        const double2 v0 = *reinterpret_cast<const double2*>(row + (c - s0));
+        const double2 v1 = *reinterpret_cast<const double2*>(row + (c - s0) + 2);
+        x[0] = v0.x, x[1] = v0.y, x[2] = v1.x, x[3] = v1.y;
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) x[e] = c + e < s1 ? row[c + e - s0] : 0.0;
+      }
+      put_slices_quad<S>(x, k0, d + q, a.slice_stride / 4);
+    }
+    // the maxima of row it + 1
+    const int64_t g1 = g + ncl;
+    const int slot1 = (it + 1) % nbuf;
+    bool ok = true;
+    if (g1 < rows && n > 0) {
+      ok = rs_wait(&bars[slot1], (uint32_t)((it + 1) / nbuf) & 1u);
+      if (ok) rs_hi_max(bufs + slot1 * buf_elems, n, &mxs[(it + 1) % 3], tid, lane);
+      if (!ok) flg[(it + 1) % 3] = 1u;
+    }
+    // row it's buffers are free in every CTA; row it + 1's maxima are complete
+    cl_sync();
+    cl_gather(&mxs[(it + 1) % 3], &flg[(it + 1) % 3], C, warp, lane, &gm, &gf);
+    if (gf != 0u) {
+      if (tid == 0 && !ok) atomicOr(a.err, (unsigned)DEVERR_TIMEOUT);
+      abort = true;
+      first_pending = it + 1;
+      break;
+    }
+    // row it + 3 collects in slot it % 3, after the next cluster barrier
+    if (tid == 0) mxs[it % 3] = 0u, flg[it % 3] = 0u;
+    const int64_t gn = g + (int64_t)nbuf * ncl;
+    if (warp == 0 && n > 0 && gn < rows) cl_issue(a, gn, s0, s1, bufs + slot * buf_elems, &bars[slot], lane);
+    if (g1 < rows) k0 = cl_row_k0<S>(a, bufs + slot1 * buf_elems, n, g1, gm, redw, &red64, C, rank, tid, warp, lane);
+  }
+  // the GEMM behind this kernel may start its launch
+  asm volatile("griddepcontrol.launch_dependents;");
+  if (abort && tid == 0 && n > 0) {
+    // let this CTA's copies still in flight land (bounded)
+    for (int k = first_pending; k < it + nbuf; ++k) {
+      const int64_t gk = cid + (int64_t)k * ncl;
+      if (gk >= rows) break;
+      rs_wait(&bars[k % nbuf], (uint32_t)(k / nbuf) & 1u);
+    }
+  }
+  // no CTA leaves while another may still read its shared memory
+  cl_sync();
 }
 
 int grid_for(int64_t tiles) {
@@ -1116,30 +1350,34 @@ cudaError_t launch_rowstream(const Problem& p, const Tables& t, int op, int n_sl
                              unsigned* err, cudaStream_t st) {
   if (n_slices < 2 || n_slices > kMaxSlices || p.es != 1 || p.general) return cudaErrorInvalidValue;
   const int64_t R = op == 0 ? p.M : p.N, K = p.K;
-  if (run <= 0 || K % run != 0 || (run * 8) % 16 != 0 || K > kRowStreamMaxK) return cudaErrorInvalidValue;
+  if (run <= 0 || K % run != 0 || (run * 8) % 16 != 0 || K > kRowClusterMaxK) return cudaErrorInvalidValue;
+  // rows beyond one CTA's buffers: clusters of C CTAs, CTA r holding columns
+  // [r seg, (r+1) seg) (seg a multiple of 4, so every piece of a run stays even)
+  const int C = (int)((K + kRowStreamMaxK - 1) / kRowStreamMaxK);
+  const int64_t seg = C > 1 ? ((K + C - 1) / C + 3) / 4 * 4 : K;
   void (*kern)(RowStreamArgs) = nullptr;
   switch (n_slices) {
-    case 2: kern = rowstream_kernel<2>; break;
-    case 3: kern = rowstream_kernel<3>; break;
-    case 4: kern = rowstream_kernel<4>; break;
-    case 5: kern = rowstream_kernel<5>; break;
-    default: kern = rowstream_kernel<6>; break;
+    case 2: kern = C > 1 ? rowcluster_kernel<2> : rowstream_kernel<2>; break;
+    case 3: kern = C > 1 ? rowcluster_kernel<3> : rowstream_kernel<3>; break;
+    case 4: kern = C > 1 ? rowcluster_kernel<4> : rowstream_kernel<4>; break;
+    case 5: kern = C > 1 ? rowcluster_kernel<5> : rowstream_kernel<5>; break;
+    default: kern = C > 1 ? rowcluster_kernel<6> : rowstream_kernel<6>; break;
   }
-  const size_t row_bytes = (size_t)((K + 15) / 16 * 16) * sizeof(double);
+  const size_t row_bytes = (size_t)((seg + 15) / 16 * 16) * sizeof(double);
   int nbuf = (int)(kRsSmem / row_bytes);
   if (nbuf > kRsMaxBufs) nbuf = kRsMaxBufs;
   if (nbuf < 2) return cudaErrorInvalidValue;
   const size_t smem = (size_t)nbuf * row_bytes;
   // the attribute is set once per instance and device (kept per host thread)
-  thread_local size_t set_for[kMaxSlices + 1][16] = {};
+  thread_local size_t set_for[2][kMaxSlices + 1][16] = {};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 16) return cudaErrorInvalidDevice;
-  if (set_for[n_slices][dev] < smem) {
+  if (set_for[C > 1][n_slices][dev] < smem) {
     e = cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    set_for[n_slices][dev] = smem;
+    set_for[C > 1][n_slices][dev] = smem;
   }
   int sms = 0;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1158,11 +1396,43 @@ cudaError_t launch_rowstream(const Problem& p, const Tables& t, int op, int n_sl
   a.exps = exps;
   a.err = err;
   a.nbuf = nbuf;
+  a.seg = seg;
   const int64_t rows = (int64_t)p.n_q * R;
-  const int grid = (int)(rows < sms ? (rows > 0 ? rows : 1) : sms);
-  kern<<<grid, RS_THREADS, smem, st>>>(a);
+  if (C == 1) {
+    const int grid = (int)(rows < sms ? (rows > 0 ? rows : 1) : sms);
+    kern<<<grid, RS_THREADS, smem, st>>>(a);
+    ++g_kernel_launches;
+    return cudaGetLastError();
+  }
+  // as many clusters as can be resident at once (a persistent loop over the
+  // rows, each row in one cluster): clusters that had to wait for a second wave
+  // would finish their rows after the rest
+  cudaLaunchConfig_t cfg = {};
+  cfg.blockDim = dim3(RS_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  thread_local int resident[kMaxSlices + 1][9][16] = {};
+  int& res = resident[n_slices][C][dev];
+  if (res == 0) {
+    cfg.gridDim = dim3((unsigned)((sms / C) * C));
+    int n = 0;
+    e = cudaOccupancyMaxActiveClusters(&n, (const void*)kern, &cfg);
+    if (e != cudaSuccess) return e;
+    res = n > 0 ? n : 1;
+  }
+  int64_t clusters = res;
+  if (clusters > rows) clusters = rows > 0 ? rows : 1;
+  cfg.gridDim = dim3((unsigned)(clusters * C));
+  e = cudaLaunchKernelEx(&cfg, kern, a);
   ++g_kernel_launches;
-  return cudaGetLastError();
+  return e;
 }
 
 cudaError_t launch_prep(const Problem& p, const Tables& t, bool split, int n_slices,

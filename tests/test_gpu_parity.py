@@ -318,12 +318,15 @@ def test_split_bit_exact_on_integer_inputs(sc, k_sectors, D):
 @pytest.mark.parametrize("einsum,D_i,D_j,prep", [("ij,jk->ik", 1024, 4096, 1), ("ij,kj->ik", 1024, 4096, 1 | 8),
                                                   ("ij,kj->ik", 1024, 1000, 4 | 8),
                                                   ("ij,jk->ik", 1024, 2000, 4 | 8),
-                                                  ("ij,jk->ik", 1024, 3000, 1), ("ij,jk->ik", 500, 3000, 4)])
+                                                  ("ij,jk->ik", 1024, 3000, 1), ("ij,jk->ik", 500, 3000, 4),
+                                                  ("ij,jk->ik", 512, 10000, 1), ("ij,jk->ik", 256, 16384, 1),
+                                                  ("ij,jk->ik", 128, 24578, 1), ("ij,jk->ik", 64, 65536, 1)])
 def test_single_read_prep_bit_exact_on_integer_inputs(sc, einsum, D_i, D_j, prep):
     """The single-read preparations on shapes that take them (plan bits 0/1:
-    rows streamed by bulk copies of contiguous runs; 2/3: whole short rows per
-    CTA, gathered along the rows or across them; neither: the two-phase
-    kernel), alone and side by side: integer inputs of two BF16 digits must give
+    rows streamed by bulk copies of contiguous runs, by one CTA up to K = 8192
+    and by clusters of 2 to 8 CTAs holding one segment each beyond; 2/3: whole
+    short rows per CTA, gathered along the rows or across them; neither: the
+    two-phase kernel), alone and side by side: integer inputs of two BF16 digits must give
     the exact integer product rounded once, bit for bit."""
     G, D_k = 2, 72
     su = ((1, -1), (0,), (D_i, D_j))
@@ -348,23 +351,24 @@ def test_single_read_prep_bit_exact_on_integer_inputs(sc, einsum, D_i, D_j, prep
     vm = v if einsum == "ij,jk->ik" else np.swapaxes(v, 1, 2)
     ui = u.copy()
     ui[:, 7, :] = 0.0
-    want = np.stack([np.matmul(ui[q].astype(np.int64), vm[q].astype(np.int64)) for q in range(G)])
-    want = want.astype(np.float64)
+    # integer sums below 2^53: exact in float64 in any order
+    want = np.stack([np.matmul(ui[q], vm[q]) for q in range(G)])
     for q in range(G):
-        want[q, 7, :] = np.ldexp((ks[q].astype(np.int64) @ vm[q].astype(np.int64)).astype(np.float64), -1050)
+        want[q, 7, :] = np.ldexp(ks[q].astype(np.float64) @ vm[q], -1050)
     assert np.array_equal(got, want)
 
 
-def test_single_read_prep_nonfinite_is_reported(sc):
+@pytest.mark.parametrize("D_j", [4096, 16384])
+def test_single_read_prep_nonfinite_is_reported(sc, D_j):
     """A NaN in an operand prepared by the single-read kernel sets the device
     error word (and nothing traps)."""
-    G, D_i, D_j, D_k = 2, 1024, 4096, 64
+    G, D_i, D_k = 2, 16777216 // (2 * D_j), 64
     p = sc.Plan("ij,jk->ik", (G,), ((1, -1), (0,), (D_i, D_j)), ((1, -1), (0,), (D_j, D_k)),
                 "split_bf16")
     assert p.info.single_read_prep & 1
     rng = np.random.default_rng(612)
     u = rng.standard_normal((G, D_i, D_j))
-    u[1, 77, 1234] = np.nan
+    u[1, 77, D_j - 1234] = np.nan   # in the last CTA's segment of a cluster
     v = rng.standard_normal((G, D_j, D_k))
     p.contract(dev(u), dev(v))
     with pytest.raises(sc.SymctrError) as ei:
