@@ -128,6 +128,24 @@ __device__ __forceinline__ uint64_t abs_bits(double x) {
   return (uint64_t)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
 }
 
+// Running maximum of |x| bit patterns kept as two 32-bit maxima: of the high
+// words (sign dropped) and of the low words.  Whenever some high word is
+// nonzero the row's scale depends on the high word of the largest entry only;
+// when all are zero the largest pattern is the largest low word.  Two 32-bit
+// integer max operations per entry instead of a 64-bit one.
+struct Max2 {
+  uint32_t hi = 0u, lo = 0u;
+  __device__ __forceinline__ void add(double x) {
+    hi = max(hi, (uint32_t)__double2hiint(x) & 0x7FFFFFFFu);
+    lo = max(lo, (uint32_t)__double2loint(x));
+  }
+  __device__ __forceinline__ void merge_xor(int o) {
+    hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    lo = max(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+  }
+  __device__ __forceinline__ uint64_t pattern() const { return hi != 0u ? (uint64_t)hi << 32 : (uint64_t)lo; }
+};
+
 // Biased row exponent key from the largest |x| bit pattern of a row: 0 for an
 // all-zero row; nonfinite entries set `bad`.  E is clamped below at 8S - 1076:
 // a row whose largest entry is smaller holds only subnormals, which are exact
@@ -276,8 +294,8 @@ __device__ void scan_tile(const PrepArgs& a, int op, uint32_t tile, int64_t* rof
   const bool masked = p.general != 0;
   constexpr int PER = SCAN_COLS / (THREADS / 32);
   constexpr int RPW = TILE / (THREADS / 32);   // rows per warp (column paths)
-  uint64_t mx = 0;          // fast rows: this thread's row (tx)
-  uint64_t mxr[RPW] = {};   // column paths: this lane's share of its warp's rows
+  Max2 mx;                  // fast rows: this thread's row (tx)
+  Max2 mxr[RPW];            // column paths: this lane's share of its warp's rows
   for (int64_t sb = cb; sb < ce; sb += kScanWidth) {
     const int64_t se = min(ce, sb + kScanWidth);
 #pragma unroll
@@ -301,7 +319,7 @@ __device__ void scan_tile(const PrepArgs& a, int op, uint32_t tile, int64_t* rof
             x[i] = (rok && c0 + cc < se && (!masked || co[cc] >= 0)) ? rowp[(int64_t)p.es * co[cc]] : 0.0;
           }
 #pragma unroll
-          for (int i = 0; i < PER / 2; ++i) mx = max(mx, abs_bits(x[i]));
+          for (int i = 0; i < PER / 2; ++i) mx.add(x[i]);
         }
       } else if (a.pair_ok[op]) {
         // lanes walk column pairs (16-byte loads), warps walk rows; per-row
@@ -320,7 +338,7 @@ __device__ void scan_tile(const PrepArgs& a, int op, uint32_t tile, int64_t* rof
           }
 #pragma unroll
           for (int i = 0; i < SCAN_COLS / 64; ++i)
-            mxr[h] = max(mxr[h], max(abs_bits(x[i].x), abs_bits(x[i].y)));
+            mxr[h].add(x[i].x), mxr[h].add(x[i].y);
         }
       } else {
         // lanes walk columns (contiguous), warps walk rows
@@ -336,7 +354,7 @@ __device__ void scan_tile(const PrepArgs& a, int op, uint32_t tile, int64_t* rof
             x[i] = (rok && c0 + cc < se && (!masked || co[cc] >= 0)) ? rowp[(int64_t)p.es * co[cc]] : 0.0;
           }
 #pragma unroll
-          for (int i = 0; i < SCAN_COLS / 32; ++i) mxr[h] = max(mxr[h], abs_bits(x[i]));
+          for (int i = 0; i < SCAN_COLS / 32; ++i) mxr[h].add(x[i]);
         }
       }
     }
@@ -345,12 +363,13 @@ __device__ void scan_tile(const PrepArgs& a, int op, uint32_t tile, int64_t* rof
   if (!fast_rows) {
 #pragma unroll
     for (int h = 0; h < RPW; ++h) {
-      uint64_t v = mxr[h];
-      for (int o = 16; o > 0; o >>= 1) v = max(v, (uint64_t)__shfl_xor_sync(0xffffffffu, (unsigned long long)v, o));
-      if (tx == 0) rmax[ty + h * (THREADS / 32)] = v;   // row belongs to this warp alone
+      Max2 v = mxr[h];
+      for (int o = 16; o > 0; o >>= 1) v.merge_xor(o);
+      if (tx == 0) rmax[ty + h * (THREADS / 32)] = v.pattern();   // row belongs to this warp alone
     }
   }
-  if (fast_rows) atomicMax(&rmax[tx], (unsigned long long)mx);
+  // the max of the patterns is the pattern of the merged maxima
+  if (fast_rows) atomicMax(&rmax[tx], (unsigned long long)mx.pattern());
   __syncthreads();
   if (threadIdx.x < TILE && r0 + threadIdx.x < R) {
     unsigned bad = 0;
