@@ -194,6 +194,11 @@ def test_preparation_kernel_of_each_operand_is_reported():
     p = sc.Plan("ij,jk->ik", (2,), ((1, -1), (0,), (1024, 4096)), ((1, -1), (0,), (4096, 64)),
                 "split_bf16")
     assert p.info.single_read_prep == 1
+    # rows of runs longer than one CTA's buffers (K > 8192): the cluster form of the
+    # bulk-copy kernel, up to K = 65536
+    for K, want in ((16384, 1), (65536, 1), (65538, 0)):  # 2 x 256 x K >= 4M entries
+        p = sc.Plan("ij,jk->ik", (2,), ((1, -1), (0,), (256, K)), ((1, -1), (0,), (K, 72)), "split_bf16")
+        assert p.info.single_read_prep == want
     # short rows with runs: the short-row kernel
     p = sc.Plan("ij,kj->ik", (2,), ((1, -1), (0,), (4096, 1024)), ((1, -1), (0,), (64, 1024)),
                 "split_bf16")
