@@ -143,8 +143,9 @@ __global__ void __launch_bounds__(THREADS) gemm_f64_tiled(const __grid_constant_
 // product of the fastest block dims of the column map up to kInnerMax.  The
 // offset is then aoff(o * I) + inner(i), inner(i) being the block part
 // of i alone (independent of Q); each block tabulates inner() in shared
-// memory and each lane recomputes aoff(o * I) only when o changes
-// (every I / 32 steps), instead of one mixed-radix decomposition per element.
+// memory, and a warp computes the offsets aoff(o * I) of the inner blocks of
+// its K range 16 at a time, one per lane, instead of one mixed-radix
+// decomposition per element.
 constexpr int SKINNY_MAX = 8;
 constexpr int kInnerMax = 2048;
 
@@ -159,23 +160,37 @@ __device__ __forceinline__ int64_t inner_extent(const AxisMap& a, const AxisMap&
   return e;
 }
 
-// inner(i) for i < I: the block digits of i over the fastest block axes.
-__device__ void fill_inner(const AxisMap& a, int64_t I, int64_t* tab) {
+// scale * inner(i) for i < I: the block digits of i over the fastest block
+// axes (scale: the element stride, so that the table holds array indices).
+__device__ void fill_inner(const AxisMap& a, int64_t I, int64_t scale, int64_t* tab) {
   for (int64_t i = threadIdx.x; i < I; i += blockDim.x) {
     int64_t r = i, off = 0;
     for (int d = a.n - 1; d >= 0 && r > 0; --d) {
       off += (r % a.D[d]) * a.bstride[d];
       r /= a.D[d];
     }
-    tab[i] = off;
+    tab[i] = off * scale;
   }
 }
+
+// Elements per lane whose loads (one of L, NS of S) are all issued before
+// their FMAs: fewer for more short-side rows, so that the registers they
+// take stay about the same.
+template <int NS>
+struct SkinnyUnroll {
+  static constexpr int value = NS <= 2 ? 4 : 2;
+};
 
 // NS = the short side's row count (one instance per count, so that no
 // float64 instruction of an absent row is issued: GB300's float64 pipe is
 // narrow and issues predicated-off instructions all the same).
+//
+// Work items: (irrep, long-side row, K range), the K ranges whole inner
+// blocks; the launcher sizes ksplit so that the items about fill the
+// resident warps once, which pays the offset arithmetic of an item (a
+// dependent chain of modular arithmetic under a product group) once per warp.
 template <int NS>
-__global__ void __launch_bounds__(THREADS) gemm_f64_skinny(const __grid_constant__ Problem p, bool long_is_u, int ksplit,
+__global__ void __launch_bounds__(THREADS, 3) gemm_f64_skinny(const __grid_constant__ Problem p, bool long_is_u, int ksplit,
                                                            const double* __restrict__ U,
                                                            const double* __restrict__ V,
                                                            double* __restrict__ W) {
@@ -184,85 +199,114 @@ __global__ void __launch_bounds__(THREADS) gemm_f64_skinny(const __grid_constant
   const AxisMap& Lcols = long_is_u ? p.u.cols : p.v.cols;
   const AxisMap& Srows = long_is_u ? p.v.rows : p.u.rows;
   const AxisMap& Scols = long_is_u ? p.v.cols : p.u.cols;
+  // W's axis along the long side and along the short side
+  const AxisMap& Wl = long_is_u ? p.w.rows : p.w.cols;
+  const AxisMap& Ws = long_is_u ? p.w.cols : p.w.rows;
   const double* Lp = long_is_u ? U : V;
   const double* Sp = long_is_u ? V : U;
   const int64_t nL = long_is_u ? p.M : p.N;
+  const int64_t es = p.es;
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t I = inner_extent(Lcols, Scols);
-  // K ranges start on multiples of I (K itself is one), so that a range
-  // covers whole inner blocks when I >= 32
-  const int64_t kchunk = ((p.K + ksplit - 1) / ksplit + I - 1) / I * I;
-  const int64_t items = nL * p.n_q * ksplit;
-  fill_inner(Lcols, I, tab_l);
-  fill_inner(Scols, I, tab_s);
+  fill_inner(Lcols, I, es, tab_l);
+  fill_inner(Scols, I, es, tab_s);
   __syncthreads();
+  // K ranges of whole inner blocks (K is a multiple of I)
+  const int64_t nb = p.K / I;
+  const int64_t per = (nb + ksplit - 1) / ksplit;
+  const int64_t parts = (nb + per - 1) / per;
+  const int64_t items = nL * p.n_q * parts;
   for (int64_t it = warp; it < items; it += nwarps) {
-    int64_t ks = it % ksplit;
-    int64_t t2 = it / ksplit;
-    int64_t b = t2 / nL;
-    int64_t l = t2 - b * nL;
-    int Q = batch_irrep(p, (int)b);
-    int64_t kbeg = ks * kchunk, kend = kbeg + kchunk < p.K ? kbeg + kchunk : p.K;
-    int64_t loff = aoff(Lrows, p.g, Q, l);
+    const int64_t ks = it % parts;
+    const int64_t t2 = it / parts;
+    const int64_t b = t2 / nL;
+    const int64_t l = t2 - b * nL;
+    const int Q = batch_irrep(p, (int)b);
+    // the row offsets, one per lane: lane 0 L's row, lanes 1..NS the short
+    // rows in S, lane NS+1 the long row along W, lanes NS+2..2NS+1 the short
+    // rows along W (the other lanes repeat lane 0's)
+    const AxisMap* rm = &Lrows;
+    int64_t rr = l;
+    if (lane >= 1 && lane <= NS) {
+      rm = &Srows;
+      rr = lane - 1;
+    } else if (lane == NS + 1) {
+      rm = &Wl;
+    } else if (lane >= NS + 2 && lane <= 2 * NS + 1) {
+      rm = &Ws;
+      rr = lane - NS - 2;
+    }
+    const int64_t ro = aoff(*rm, p.g, Q, rr);
+    const int64_t loff = es * __shfl_sync(0xffffffffu, ro, 0);
     int64_t soff[NS];
 #pragma unroll
-    for (int s = 0; s < NS; ++s) soff[s] = aoff(Srows, p.g, Q, s);
+    for (int s = 0; s < NS; ++s) soff[s] = es * __shfl_sync(0xffffffffu, ro, 1 + s);
     double acc[NS];
 #pragma unroll
     for (int s = 0; s < NS; ++s) acc[s] = 0.0;
+    const int64_t ob0 = ks * per, ob1 = ob0 + per < nb ? ob0 + per : nb;
     if (I >= 32) {
-      // whole inner blocks (kend is a multiple of I): lane j computes the two
-      // offsets of inner block ob + j, for 32 blocks at once, and the warp
-      // walks them with kUnroll independent loads per lane in flight
-      constexpr int kUnroll = 4;
-      for (int64_t ob = kbeg / I; ob * I < kend; ob += 32) {
-        const int64_t oj = ob + lane;
-        const bool own = oj * I < kend;
-        const int64_t lo_j = own ? loff + aoff(Lcols, p.g, Q, oj * I) : 0;
-        const int64_t so_j = own ? aoff(Scols, p.g, Q, oj * I) : 0;
-        const int64_t left = (kend - ob * I) / I;
-        const int nb = left < 32 ? (int)left : 32;
-        for (int j = 0; j < nb; ++j) {
-          const int64_t lo = __shfl_sync(0xffffffffu, lo_j, j);
-          const int64_t so = __shfl_sync(0xffffffffu, so_j, j);
-          for (int64_t i0 = lane; i0 < I; i0 += 32 * kUnroll) {
-            double x[kUnroll];
-            int64_t sc[kUnroll];
+      // inner blocks 16 at a time: lanes 0-15 compute the L offsets of blocks
+      // g0 + lane, lanes 16-31 the S offsets of blocks g0 + lane - 16
+      for (int64_t g0 = ob0; g0 < ob1; g0 += 16) {
+        const int64_t ob = g0 + (lane & 15);
+        const int64_t co = ob < ob1 ? aoff(lane < 16 ? Lcols : Scols, p.g, Q, ob * I) : 0;
+        const int nbk = ob1 - g0 < 16 ? (int)(ob1 - g0) : 16;
+        for (int j = 0; j < nbk; ++j) {
+          const double* Lb = Lp + (loff + es * __shfl_sync(0xffffffffu, co, j));
+          const int64_t sb = es * __shfl_sync(0xffffffffu, co, 16 + j);
+          const double* Sb[NS];
 #pragma unroll
-            for (int u = 0; u < kUnroll; ++u) {
-              const int64_t i = i0 + 32 * u;
-              const bool in = i < I;
-              x[u] = in ? Lp[p.es * (lo + tab_l[i])] : 0.0;
-              sc[u] = in ? so + tab_s[i] : -1;
-            }
+          for (int s = 0; s < NS; ++s) Sb[s] = Sp + (soff[s] + sb);
+          constexpr int kU = SkinnyUnroll<NS>::value;
+          for (int i0 = 0; i0 < (int)I; i0 += 32 * kU) {
+            if (i0 + 32 * kU <= (int)I) {
+              double x[kU], y[NS][kU];
 #pragma unroll
-            for (int u = 0; u < kUnroll; ++u) {
+              for (int u = 0; u < kU; ++u) {
+                const int i = i0 + 32 * u + lane;
+                const int64_t tl = tab_l[i], ts = tab_s[i];
+                x[u] = Lb[tl];
 #pragma unroll
-              for (int s = 0; s < NS; ++s)
-                if (sc[u] >= 0) acc[s] = fma(x[u], Sp[p.es * (soff[s] + sc[u])], acc[s]);
+                for (int s = 0; s < NS; ++s) y[s][u] = Sb[s][ts];
+              }
+#pragma unroll
+              for (int u = 0; u < kU; ++u) {
+#pragma unroll
+                for (int s = 0; s < NS; ++s) acc[s] = fma(x[u], y[s][u], acc[s]);
+              }
+            } else {
+              // the ragged end of an inner block (I not a multiple of 32 kU)
+              for (int i = i0 + lane; i < (int)I; i += 32) {
+                const double x = Lb[tab_l[i]];
+#pragma unroll
+                for (int s = 0; s < NS; ++s) acc[s] = fma(x, Sb[s][tab_s[i]], acc[s]);
+              }
             }
           }
         }
       }
     } else {
-      int64_t k = kbeg + lane;
+      // short inner blocks: lanes walk the elements, recomputing the two
+      // inner-block offsets when the block changes
+      const int64_t kend = ob1 * I;
+      int64_t k = ob0 * I + lane;
       int64_t o = k / I, i = k - o * I;
-      int64_t lo = aoff(Lcols, p.g, Q, o * I), so = aoff(Scols, p.g, Q, o * I);
+      int64_t lo = es * aoff(Lcols, p.g, Q, o * I), so = es * aoff(Scols, p.g, Q, o * I);
       for (; k < kend; k += 32) {
-        const double x = Lp[p.es * (loff + lo + tab_l[i])];
+        const double x = Lp[loff + lo + tab_l[i]];
         const int64_t sc = so + tab_s[i];
 #pragma unroll
-        for (int s = 0; s < NS; ++s)
-          acc[s] = fma(x, Sp[p.es * (soff[s] + sc)], acc[s]);
+        for (int s = 0; s < NS; ++s) acc[s] = fma(x, Sp[soff[s] + sc], acc[s]);
         i += 32;
         if (i >= I) {
           o += i / I;
           i %= I;
           if (k + 32 < kend) {
-            lo = aoff(Lcols, p.g, Q, o * I);
-            so = aoff(Scols, p.g, Q, o * I);
+            lo = es * aoff(Lcols, p.g, Q, o * I);
+            so = es * aoff(Scols, p.g, Q, o * I);
           }
         }
       }
@@ -273,11 +317,12 @@ __global__ void __launch_bounds__(THREADS) gemm_f64_skinny(const __grid_constant
       for (int o2 = 16; o2 > 0; o2 >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o2);
       acc[s] = a;
     }
-    if (lane == 0) {
+    const int64_t wlo = __shfl_sync(0xffffffffu, ro, NS + 1);
 #pragma unroll
-      for (int s = 0; s < NS; ++s) {
-        int64_t m = long_is_u ? l : s, n = long_is_u ? s : l;
-        double* dst = W + p.es * (aoff(p.w.rows, p.g, Q, m) + aoff(p.w.cols, p.g, Q, n));
+    for (int s = 0; s < NS; ++s) {
+      const int64_t wso = __shfl_sync(0xffffffffu, ro, NS + 2 + s);
+      if (lane == 0) {
+        double* dst = W + es * (wlo + wso);
         if (ksplit > 1) atomicAdd(dst, signed_result(p, acc[s]));
         else store_w(p, dst, acc[s]);
       }
@@ -286,26 +331,45 @@ __global__ void __launch_bounds__(THREADS) gemm_f64_skinny(const __grid_constant
 }
 
 // Skinny problems with K <= kShortK: one thread per row of the long side, a
-// block taking kShortRows consecutive rows at a time (kShortRows / THREADS
-// per thread).  The short side's values and the long side's column offsets
-// depend only on the irrep, so a block stages them in shared memory when the
-// irrep changes.  Row offsets in L and W use the inner-block split of the
-// skinny kernel above (l = o * I + i): a table of inner(i) per map, and
-// aoff(o * I) for the inner blocks of a chunk computed by as many
-// threads at once (the index arithmetic of one offset is a long dependent
-// chain under a product group, so it is never left to a single thread).
+// block taking kShortRows consecutive rows at a time.  The short side's
+// values and the long side's column offsets depend only on the irrep, so a
+// block stages them in shared memory when the irrep changes.  Row offsets in
+// L and W use the inner-block split of the skinny kernel above (l = o * I +
+// i): a table of inner(i) per map, and aoff(o * I) for the inner blocks of a
+// chunk computed by as many threads at once, spread over the warps (the
+// index arithmetic of one offset is a long dependent chain under a product
+// group, so it is never left to a single thread).  A thread issues the loads
+// of a few rows (ShortUnroll) before their FMAs.
 constexpr int kShortK = 32;
 constexpr int kShortRows = 4096;
 constexpr int kShortSlots = kShortRows / 32 + 2;
 
-template <int NS>
-__global__ void __launch_bounds__(THREADS) gemm_f64_shortk(const __grid_constant__ Problem p, bool long_is_u,
-                                                           const double* __restrict__ U,
-                                                           const double* __restrict__ V,
-                                                           double* __restrict__ W) {
+// Rows per thread whose loads are all issued before their FMAs.
+template <int KT>
+struct ShortUnroll {
+  static constexpr int value = KT == 1 ? 8 : (KT == 2 ? 4 : 2);
+};
+
+// Step (o, i) = divmod(l, I) by THREADS rows without dividing (64-bit integer
+// division runs on GB300's narrow float64 pipe).
+__device__ __forceinline__ void step_rows(int64_t I, int64_t& o, int64_t& i) {
+  i += THREADS;
+  while (i >= I) {
+    i -= I;
+    ++o;
+  }
+}
+
+// KT: K itself when it is 1 or 2 (the loads of a row unrolled), 0 for any
+// K <= kShortK (a loop over K).
+template <int NS, int KT>
+__global__ void __launch_bounds__(THREADS, 4) gemm_f64_shortk(const __grid_constant__ Problem p, bool long_is_u,
+                                                              const double* __restrict__ U,
+                                                              const double* __restrict__ V,
+                                                              double* __restrict__ W) {
   __shared__ double sval[SKINNY_MAX][kShortK];
-  __shared__ int64_t lco[kShortK];
-  __shared__ int64_t wso[SKINNY_MAX];
+  __shared__ int64_t lco[kShortK], scol[kShortK];
+  __shared__ int64_t wso[SKINNY_MAX], srow[SKINNY_MAX];
   __shared__ int64_t tab_lr[kInnerMax], tab_w[kInnerMax];
   __shared__ int64_t ob_l[kShortSlots], ob_w[kShortSlots];
   const AxisMap& Lrows = long_is_u ? p.u.rows : p.v.rows;
@@ -317,16 +381,21 @@ __global__ void __launch_bounds__(THREADS) gemm_f64_shortk(const __grid_constant
   const double* Lp = long_is_u ? U : V;
   const double* Sp = long_is_u ? V : U;
   const int64_t nL = long_is_u ? p.M : p.N;
-  constexpr int nS = NS;   // the launcher picks the instance with NS == the short side
-  const int K = (int)p.K;
+  const int64_t es = p.es;
+  constexpr int RU = ShortUnroll<KT>::value;
+  constexpr int KX = KT > 0 ? KT : 1;
+  const int K = KT ? KT : (int)p.K;
   const int64_t per_q = (nL + kShortRows - 1) / kShortRows;
   // the rows of L and W's axis along the long side index the same modes
   const int64_t I = inner_extent(Lrows, Wl);
   const bool tabulated = I >= 32;   // then a chunk touches <= kShortSlots inner blocks
   if (tabulated) {
-    fill_inner(Lrows, I, tab_lr);
-    fill_inner(Wl, I, tab_w);
+    fill_inner(Lrows, I, es, tab_lr);
+    fill_inner(Wl, I, es, tab_w);
   }
+  // this thread's share of a chunk's offsets: task t falls to lane t / 8 of
+  // warp t % 8, so that every warp computes about as many
+  const int task0 = (threadIdx.x & 31) * (THREADS / 32) + (threadIdx.x >> 5);
   int staged = -1;
   for (int64_t blk = blockIdx.x; blk < per_q * p.n_q; blk += gridDim.x) {
     const int b = (int)(blk / per_q);
@@ -335,54 +404,133 @@ __global__ void __launch_bounds__(THREADS) gemm_f64_shortk(const __grid_constant
     const int64_t o0 = l0 / I;
     const int Q = batch_irrep(p, b);
     __syncthreads();   // the previous chunk's readers are done
-    if (b != staged) {
-      for (int i = threadIdx.x; i < nS * K; i += THREADS) {
-        const int sr = i / K, k = i - sr * K;
-        sval[sr][k] = Sp[p.es * (aoff(Srows, p.g, Q, sr) + aoff(Scols, p.g, Q, k))];
+    // one offset per task: on a new irrep first the short rows in S, S's and
+    // L's columns and the short rows along W (2 NS + 2 K), then L's and W's
+    // offsets of the chunk's inner blocks (alternating)
+    const bool stage = b != staged;
+    const int n_s = stage ? 2 * NS + 2 * K : 0;
+    const int n_t = n_s + (tabulated ? 2 * (int)((lend - 1) / I - o0 + 1) : 0);
+    for (int t = task0; t < n_t; t += THREADS) {
+      const AxisMap* m;
+      int64_t r, sc = es;
+      int64_t* dst;
+      if (t >= n_s) {
+        const int j = (t - n_s) / 2;
+        m = ((t - n_s) & 1) ? &Wl : &Lrows;
+        r = (o0 + j) * I;
+        dst = ((t - n_s) & 1) ? &ob_w[j] : &ob_l[j];
+      } else if (t < NS) {
+        m = &Srows;
+        r = t;
+        sc = 1;
+        dst = &srow[t];
+      } else if (t < NS + K) {
+        m = &Scols;
+        r = t - NS;
+        sc = 1;
+        dst = &scol[t - NS];
+      } else if (t < NS + 2 * K) {
+        m = &Lcols;
+        r = t - NS - K;
+        dst = &lco[t - NS - K];
+      } else {
+        m = &Ws;
+        r = t - NS - 2 * K;
+        dst = &wso[t - NS - 2 * K];
       }
-      for (int k = threadIdx.x; k < K; k += THREADS) lco[k] = aoff(Lcols, p.g, Q, k);
-      for (int sr = threadIdx.x; sr < nS; sr += THREADS) wso[sr] = aoff(Ws, p.g, Q, sr);
-      staged = b;
-    }
-    if (tabulated) {
-      const int64_t n_o = (lend - 1) / I - o0 + 1;
-      for (int64_t j = threadIdx.x; j < n_o; j += THREADS) {
-        ob_l[j] = aoff(Lrows, p.g, Q, (o0 + j) * I);
-        ob_w[j] = aoff(Wl, p.g, Q, (o0 + j) * I);
-      }
+      *dst = sc * aoff(*m, p.g, Q, r);
     }
     __syncthreads();
-    // (o, i) of the thread's first row by one division; later rows step by
-    // THREADS without dividing (64-bit integer division runs on GB300's
-    // narrow float64 pipe)
-    int64_t o = tabulated ? (l0 + threadIdx.x) / I : 0;
-    int64_t i = tabulated ? l0 + threadIdx.x - o * I : 0;
-    for (int64_t l = l0 + threadIdx.x; l < lend; l += THREADS) {
-      int64_t loff, woff;
-      if (tabulated) {
-        loff = ob_l[o - o0] + tab_lr[i];
-        woff = ob_w[o - o0] + tab_w[i];
-        i += THREADS;
-        while (i >= I) {
-          i -= I;
-          ++o;
+    if (stage) {
+      for (int i = threadIdx.x; i < NS * K; i += THREADS) {
+        const int sr = i / K, k = i - sr * K;
+        sval[sr][k] = Sp[es * (srow[sr] + scol[k])];
+      }
+      staged = b;
+      __syncthreads();
+    }
+    if (!tabulated) {
+      // short inner blocks: the offsets of each row from scratch
+      for (int64_t l = l0 + threadIdx.x; l < lend; l += THREADS) {
+        const int64_t lo = es * aoff(Lrows, p.g, Q, l), wo = es * aoff(Wl, p.g, Q, l);
+        double acc[NS];
+#pragma unroll
+        for (int sr = 0; sr < NS; ++sr) acc[sr] = 0.0;
+        for (int k = 0; k < K; ++k) {
+          const double x = Lp[lo + lco[k]];
+#pragma unroll
+          for (int sr = 0; sr < NS; ++sr) acc[sr] = fma(x, sval[sr][k], acc[sr]);
+        }
+#pragma unroll
+        for (int sr = 0; sr < NS; ++sr) store_w(p, W + (wo + wso[sr]), acc[sr]);
+      }
+      continue;
+    }
+    // (o, i) of the thread's first row by one division
+    int64_t o = (l0 + threadIdx.x) / I;
+    int64_t i = l0 + threadIdx.x - o * I;
+    for (int64_t l = l0 + threadIdx.x; l < lend; l += (int64_t)THREADS * RU) {
+      // RU rows: first every load (K known), then the FMAs and stores, the
+      // row offsets in W found again from the saved (o, i)
+      const int64_t os = o, is = i;
+      if (KT > 0) {
+        double x[RU][KX];
+#pragma unroll
+        for (int r = 0; r < RU; ++r) {
+          const bool ok = l + (int64_t)r * THREADS < lend;
+          const int64_t lo = ok ? ob_l[o - o0] + tab_lr[i] : 0;
+#pragma unroll
+          for (int k = 0; k < KX; ++k) x[r][k] = ok ? Lp[lo + lco[k]] : 0.0;
+          if (ok) step_rows(I, o, i);
+        }
+        o = os;
+        i = is;
+#pragma unroll
+        for (int r = 0; r < RU; ++r) {
+          if (l + (int64_t)r * THREADS >= lend) break;
+          const int64_t wo = ob_w[o - o0] + tab_w[i];
+#pragma unroll
+          for (int sr = 0; sr < NS; ++sr) {
+            double a = 0.0;
+#pragma unroll
+            for (int k = 0; k < KX; ++k) a = fma(x[r][k], sval[sr][k], a);
+            store_w(p, W + (wo + wso[sr]), a);
+          }
+          step_rows(I, o, i);
         }
       } else {
-        loff = aoff(Lrows, p.g, Q, l);
-        woff = aoff(Wl, p.g, Q, l);
+        int64_t lo[RU];
+#pragma unroll
+        for (int r = 0; r < RU; ++r) {
+          const bool ok = l + (int64_t)r * THREADS < lend;
+          lo[r] = ok ? ob_l[o - o0] + tab_lr[i] : -1;
+          if (ok) step_rows(I, o, i);
+        }
+        double acc[RU][NS];
+#pragma unroll
+        for (int r = 0; r < RU; ++r)
+#pragma unroll
+          for (int sr = 0; sr < NS; ++sr) acc[r][sr] = 0.0;
+        for (int k = 0; k < K; ++k) {
+          double x[RU];
+#pragma unroll
+          for (int r = 0; r < RU; ++r) x[r] = lo[r] >= 0 ? Lp[lo[r] + lco[k]] : 0.0;
+#pragma unroll
+          for (int r = 0; r < RU; ++r)
+#pragma unroll
+            for (int sr = 0; sr < NS; ++sr) acc[r][sr] = fma(x[r], sval[sr][k], acc[r][sr]);
+        }
+        o = os;
+        i = is;
+#pragma unroll
+        for (int r = 0; r < RU; ++r) {
+          if (lo[r] < 0) break;
+          const int64_t wo = ob_w[o - o0] + tab_w[i];
+#pragma unroll
+          for (int sr = 0; sr < NS; ++sr) store_w(p, W + (wo + wso[sr]), acc[r][sr]);
+          step_rows(I, o, i);
+        }
       }
-      double acc[NS];
-#pragma unroll
-      for (int sr = 0; sr < NS; ++sr) acc[sr] = 0.0;
-      for (int k = 0; k < K; ++k) {
-        const double x = Lp[p.es * (loff + lco[k])];
-#pragma unroll
-        for (int sr = 0; sr < NS; ++sr)
-          acc[sr] = fma(x, sval[sr][k], acc[sr]);
-      }
-#pragma unroll
-      for (int sr = 0; sr < NS; ++sr)
-        store_w(p, W + p.es * (woff + wso[sr]), acc[sr]);
     }
   }
 }
@@ -406,6 +554,71 @@ __global__ void zero_w_entries(const __grid_constant__ Problem p, double* __rest
   }
 }
 
+// Resident blocks per SM of a kernel instance (cached per device).
+template <typename Kernel>
+int blocks_per_sm(Kernel kernel, int* cache) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int& c = cache[dev & 63];
+  if (c == 0) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, THREADS, 0) != cudaSuccess || n < 1) n = 1;
+    c = n;
+  }
+  return c;
+}
+
+template <int NS, int KT>
+void launch_shortk_kt(int sms, int64_t chunks, cudaStream_t st, const Problem& p, bool long_is_u, const double* u,
+                      const double* v, double* w) {
+  // a persistent grid: a block stages an irrep's values once and walks its chunks
+  static int cache[64] = {};
+  const int64_t resident = (int64_t)blocks_per_sm(gemm_f64_shortk<NS, KT>, cache) * sms;
+  const int grid = (int)(chunks < resident ? chunks : resident);
+  gemm_f64_shortk<NS, KT><<<grid, THREADS, 0, st>>>(p, long_is_u, u, v, w);
+}
+
+template <int NS>
+void launch_shortk_ns(int kt, int sms, int64_t chunks, cudaStream_t st, const Problem& p, bool long_is_u,
+                      const double* u, const double* v, double* w) {
+  if (kt == 1) launch_shortk_kt<NS, 1>(sms, chunks, st, p, long_is_u, u, v, w);
+  else if (kt == 2) launch_shortk_kt<NS, 2>(sms, chunks, st, p, long_is_u, u, v, w);
+  else launch_shortk_kt<NS, 0>(sms, chunks, st, p, long_is_u, u, v, w);
+}
+
+// Resident warps of the skinny kernel's instance for NS short-side rows
+// (cached per device).
+template <int NS>
+int64_t skinny_resident_warps(int sms) {
+  static int cache[64] = {};
+  return (int64_t)blocks_per_sm(gemm_f64_skinny<NS>, cache) * sms * (THREADS / 32);
+}
+
+template <int NS>
+void launch_skinny_ns(int sms, cudaStream_t st, const Problem& p, bool long_is_u, const double* u,
+                      const double* v, double* w) {
+  const int64_t nL = long_is_u ? p.M : p.N;
+  const int64_t rows = nL * p.n_q;
+  const int64_t resident = skinny_resident_warps<NS>(sms);
+  // one item per resident warp where the rows are fewer, K ranges of at
+  // least 512 entries
+  int64_t ksplit = 1;
+  if (rows < resident) {
+    ksplit = resident / rows;
+    const int64_t most = p.K / 512 > 1 ? p.K / 512 : 1;
+    if (ksplit > most) ksplit = most;
+  }
+  if (ksplit > 1 && !p.accumulate) {
+    zero_w_entries<<<sms * 4, 256, 0, st>>>(p, w);
+    ++g_kernel_launches;
+  }
+  const int64_t items = rows * ksplit;   // at most; the kernel rounds K ranges to inner blocks
+  const int64_t blocks = (items * 32 + THREADS - 1) / THREADS;
+  const int64_t cap = resident / (THREADS / 32);
+  const int grid = (int)(blocks < cap ? blocks : cap);
+  gemm_f64_skinny<NS><<<grid, THREADS, 0, st>>>(p, long_is_u, (int)ksplit, u, v, w);
+}
+
 }  // namespace
 
 cudaError_t launch_gemm_f64(const Problem& p, const double* u, const double* v, double* w,
@@ -421,45 +634,33 @@ cudaError_t launch_gemm_f64(const Problem& p, const double* u, const double* v, 
     // row along its K range, nL * (1 + nS) rows in all, fewest with the
     // shorter side as the long one
     if (p.M <= SKINNY_MAX && p.N <= SKINNY_MAX) long_is_u = p.M <= p.N;
+    const int nS = (int)(long_is_u ? p.N : p.M);
     if (p.K <= kShortK) {
       const int64_t nL = long_is_u ? p.M : p.N;
-      const int64_t blocks = (nL + kShortRows - 1) / kShortRows * p.n_q;
-      const int64_t cap = (int64_t)sms * 16;
-      const int grid = (int)(blocks < cap ? blocks : cap), nS = (int)(long_is_u ? p.N : p.M);
+      const int64_t chunks = (nL + kShortRows - 1) / kShortRows * p.n_q;
+      const int kt = p.K == 1 ? 1 : (p.K == 2 ? 2 : 0);
       switch (nS) {
-        case 1: gemm_f64_shortk<1><<<grid, THREADS, 0, st>>>(p, long_is_u, u, v, w); break;
-        case 2: gemm_f64_shortk<2><<<grid, THREADS, 0, st>>>(p, long_is_u, u, v, w); break;
-        case 3: gemm_f64_shortk<3><<<grid, THREADS, 0, st>>>(p, long_is_u, u, v, w); break;
-        case 4: gemm_f64_shortk<4><<<grid, THREADS, 0, st>>>(p, long_is_u, u, v, w); break;
-        case 5: gemm_f64_shortk<5><<<grid, THREADS, 0, st>>>(p, long_is_u, u, v, w); break;
-        case 6: gemm_f64_shortk<6><<<grid, THREADS, 0, st>>>(p, long_is_u, u, v, w); break;
-        case 7: gemm_f64_shortk<7><<<grid, THREADS, 0, st>>>(p, long_is_u, u, v, w); break;
-        default: gemm_f64_shortk<8><<<grid, THREADS, 0, st>>>(p, long_is_u, u, v, w); break;
+        case 1: launch_shortk_ns<1>(kt, sms, chunks, st, p, long_is_u, u, v, w); break;
+        case 2: launch_shortk_ns<2>(kt, sms, chunks, st, p, long_is_u, u, v, w); break;
+        case 3: launch_shortk_ns<3>(kt, sms, chunks, st, p, long_is_u, u, v, w); break;
+        case 4: launch_shortk_ns<4>(kt, sms, chunks, st, p, long_is_u, u, v, w); break;
+        case 5: launch_shortk_ns<5>(kt, sms, chunks, st, p, long_is_u, u, v, w); break;
+        case 6: launch_shortk_ns<6>(kt, sms, chunks, st, p, long_is_u, u, v, w); break;
+        case 7: launch_shortk_ns<7>(kt, sms, chunks, st, p, long_is_u, u, v, w); break;
+        default: launch_shortk_ns<8>(kt, sms, chunks, st, p, long_is_u, u, v, w); break;
       }
       ++g_kernel_launches;
       return cudaGetLastError();
     }
-    int64_t nL = long_is_u ? p.M : p.N;
-    int64_t warps = nL * p.n_q;
-    int ksplit = 1;
-    int64_t want_warps = (int64_t)sms * (THREADS / 32) * 4;
-    while (warps * ksplit < want_warps && p.K / (ksplit * 2) >= 256) ksplit *= 2;
-    if (ksplit > 1 && !p.accumulate) {
-      zero_w_entries<<<sms * 4, 256, 0, st>>>(p, w);
-      ++g_kernel_launches;
-    }
-    int64_t blocks = (warps * ksplit * 32 + THREADS - 1) / THREADS;
-    int64_t cap = (int64_t)sms * 16;
-    const int grid = (int)(blocks < cap ? blocks : cap), nS = (int)(long_is_u ? p.N : p.M);
     switch (nS) {
-      case 1: gemm_f64_skinny<1><<<grid, THREADS, 0, st>>>(p, long_is_u, ksplit, u, v, w); break;
-      case 2: gemm_f64_skinny<2><<<grid, THREADS, 0, st>>>(p, long_is_u, ksplit, u, v, w); break;
-      case 3: gemm_f64_skinny<3><<<grid, THREADS, 0, st>>>(p, long_is_u, ksplit, u, v, w); break;
-      case 4: gemm_f64_skinny<4><<<grid, THREADS, 0, st>>>(p, long_is_u, ksplit, u, v, w); break;
-      case 5: gemm_f64_skinny<5><<<grid, THREADS, 0, st>>>(p, long_is_u, ksplit, u, v, w); break;
-      case 6: gemm_f64_skinny<6><<<grid, THREADS, 0, st>>>(p, long_is_u, ksplit, u, v, w); break;
-      case 7: gemm_f64_skinny<7><<<grid, THREADS, 0, st>>>(p, long_is_u, ksplit, u, v, w); break;
-      default: gemm_f64_skinny<8><<<grid, THREADS, 0, st>>>(p, long_is_u, ksplit, u, v, w); break;
+      case 1: launch_skinny_ns<1>(sms, st, p, long_is_u, u, v, w); break;
+      case 2: launch_skinny_ns<2>(sms, st, p, long_is_u, u, v, w); break;
+      case 3: launch_skinny_ns<3>(sms, st, p, long_is_u, u, v, w); break;
+      case 4: launch_skinny_ns<4>(sms, st, p, long_is_u, u, v, w); break;
+      case 5: launch_skinny_ns<5>(sms, st, p, long_is_u, u, v, w); break;
+      case 6: launch_skinny_ns<6>(sms, st, p, long_is_u, u, v, w); break;
+      case 7: launch_skinny_ns<7>(sms, st, p, long_is_u, u, v, w); break;
+      default: launch_skinny_ns<8>(sms, st, p, long_is_u, u, v, w); break;
     }
     ++g_kernel_launches;
     return cudaGetLastError();

@@ -71,6 +71,13 @@ struct AxisMap {
 
 // Offset contribution of aligned index r at irrep Q.  Axes below 2^31
 // entries (all practical ones) take 32-bit divisions.
+//
+// Under a product group Z_m1 x ... x Z_mr the conservation law holds factor by
+// factor, so the sector labels are split into their factor digits straight
+// from r (one division per factor), the signed digit sums are kept per factor
+// without reduction, and the implicit sector's digits are reduced once at the
+// end: a handful of divisions per mode instead of the label arithmetic of
+// g_add / g_neg at every step.
 template <typename I>
 SC_HD int64_t axis_offset_t(const AxisMap& a, const GroupDesc& g, int Q, I r) {
   int64_t off = 0;
@@ -80,16 +87,65 @@ SC_HD int64_t axis_offset_t(const AxisMap& a, const GroupDesc& g, int Q, I r) {
     off += (int64_t)(r - q * d) * a.bstride[i];
     r = q;
   }
-  int partial = 0;
-  for (int i = a.n - 2; i >= 0; --i) {
-    const I q = r / (I)g.order;
-    const int s = (int)(r - q * (I)g.order);
-    r = q;
-    off += (int64_t)s * a.sstride[i];
-    partial = g_add(g, partial, g_signed(g, a.sign[i], s));
+  if (g.n == 1) {
+    int partial = 0;
+    for (int i = a.n - 2; i >= 0; --i) {
+      const I q = r / (I)g.order;
+      const int s = (int)(r - q * (I)g.order);
+      r = q;
+      off += (int64_t)s * a.sstride[i];
+      partial = g_add(g, partial, g_signed(g, a.sign[i], s));
+    }
+    int target = g_add(g, g_signed(g, a.qa, Q), a.z);
+    int last = g_signed(g, a.sign[a.n - 1], g_add(g, target, g_neg(g, partial)));
+    off += (int64_t)last * a.sstride[a.n - 1];
+    return off;
   }
-  int target = g_add(g, g_signed(g, a.qa, Q), a.z);
-  int last = g_signed(g, a.sign[a.n - 1], g_add(g, target, g_neg(g, partial)));
+  // part[k]: the signed digit sum of factor g.n - 1 - k (indexed by the
+  // unrolled counter, so that it stays in registers)
+  int part[SYMCTR_MAX_MODULI];
+#if defined(__CUDA_ARCH__)
+#pragma unroll
+#endif
+  for (int k = 0; k < SYMCTR_MAX_MODULI; ++k) part[k] = 0;
+  for (int i = a.n - 2; i >= 0; --i) {
+    int s = 0, scale = 1;
+#if defined(__CUDA_ARCH__)
+#pragma unroll
+#endif
+    for (int k = 0; k < SYMCTR_MAX_MODULI; ++k) {
+      if (k < g.n) {
+        const int mf = g.mod[g.n - 1 - k];
+        const I m = (I)mf;
+        const I q = r / m;
+        const int d = (int)(r - q * m);
+        r = q;
+        s += d * scale;
+        scale *= mf;
+        part[k] += a.sign[i] > 0 ? d : -d;
+      }
+    }
+    off += (int64_t)s * a.sstride[i];
+  }
+  // digit f of the implicit sector: sign_last * (qa * Q_f + z_f - part_f) mod m_f
+  int last = 0, scale = 1, qr = Q, zr = a.z;
+#if defined(__CUDA_ARCH__)
+#pragma unroll
+#endif
+  for (int k = 0; k < SYMCTR_MAX_MODULI; ++k) {
+    if (k < g.n) {
+      const int m = g.mod[g.n - 1 - k];
+      const int qf = qr % m, zf = zr % m;
+      qr /= m;
+      zr /= m;
+      int x = (a.qa > 0 ? qf : -qf) + zf - part[k];
+      if (!(a.sign[a.n - 1] > 0)) x = -x;
+      x %= m;
+      if (x < 0) x += m;
+      last += x * scale;
+      scale *= m;
+    }
+  }
   off += (int64_t)last * a.sstride[a.n - 1];
   return off;
 }

@@ -109,6 +109,33 @@ def test_mapback_zero_fill_outer_product(sc):
         assert rel(host(w), want) <= 1e-12
 
 
+@pytest.mark.parametrize("p_dim", [2, 3])
+def test_gemv_and_adjoints_many_chunks(sc, p_dim):
+    """A GEMV under Z_2 x Z_3 (M = p_dim, N = 1, K = 6^3 * 12^4 per irrep)
+    and its two adjoints in float64: an outer product (K = 1, p_dim short
+    rows) and a product with K = p_dim, both over 4.5M long-side rows, so that
+    the short-K kernel's persistent blocks walk several row chunks each (the
+    block offsets of every chunk after the first are computed without the
+    per-irrep staging) and the skinny kernel splits K over every resident
+    warp.  p_dim = 3 takes the short-K kernel's loop over a run-time K."""
+    moduli = (2, 3)
+    st = ((1, 1, -1, -1, 1), (0, 0), (12, 12, 12, 12, p_dim))
+    se = ((-1, -1, 1, 1), (0, 0), (12, 12, 12, 12))
+    T = WL.draw(WL.TensorSpec(*st, 1.0, 4301), moduli)
+    Env = WL.draw(WL.TensorSpec(*se, 1e-3, 4302), moduli)
+    py = sc.Plan("uldrp,uldr->p", moduli, st, se, "fp64")
+    Td, Ed = dev(T), dev(Env)
+    y = py.contract(Td, Ed)
+    oy = oplan("uldrp,uldr->p", moduli, st, se)
+    y_ref = O.contract_blockloop(oy, T, Env)
+    assert rel(host(y), y_ref) <= 1e-12
+    gy = np.random.default_rng(4303).standard_normal(y_ref.shape)
+    gT, gE = py.backward(dev(gy), Td, Ed)
+    torch.cuda.synchronize()
+    assert rel(host(gT), O.grad_u(oy, gy, Env)) <= 1e-12
+    assert rel(host(gE), O.grad_v(oy, T, gy)) <= 1e-12
+
+
 # ---------------------------------------------------------------------------
 # the paper-shaped workloads
 # ---------------------------------------------------------------------------
