@@ -160,14 +160,25 @@ __device__ __forceinline__ int64_t inner_extent(const AxisMap& a, const AxisMap&
   return e;
 }
 
+// 64-bit integer division runs on GB300's narrow float64 pipe, beside the
+// float64 FMAs of these kernels: quotients of values below 2^32 are taken
+// in 32 bits.
+__device__ __forceinline__ int64_t div_idx(int64_t a, int64_t b) {
+  if (((uint64_t)a | (uint64_t)b) <= 0xFFFFFFFFull) return (int64_t)((uint32_t)a / (uint32_t)b);
+  return a / b;
+}
+
 // scale * inner(i) for i < I: the block digits of i over the fastest block
 // axes (scale: the element stride, so that the table holds array indices).
+// I <= kInnerMax, so the digits are taken in 32 bits.
 __device__ void fill_inner(const AxisMap& a, int64_t I, int64_t scale, int64_t* tab) {
-  for (int64_t i = threadIdx.x; i < I; i += blockDim.x) {
-    int64_t r = i, off = 0;
+  for (int i = threadIdx.x; i < (int)I; i += blockDim.x) {
+    uint32_t r = (uint32_t)i;
+    int64_t off = 0;
     for (int d = a.n - 1; d >= 0 && r > 0; --d) {
-      off += (r % a.D[d]) * a.bstride[d];
-      r /= a.D[d];
+      const uint32_t D = (uint32_t)a.D[d], q = r / D;
+      off += (int64_t)(r - q * D) * a.bstride[d];
+      r = q;
     }
     tab[i] = off * scale;
   }
@@ -214,14 +225,14 @@ __global__ void __launch_bounds__(THREADS, 3) gemm_f64_skinny(const __grid_const
   fill_inner(Scols, I, es, tab_s);
   __syncthreads();
   // K ranges of whole inner blocks (K is a multiple of I)
-  const int64_t nb = p.K / I;
-  const int64_t per = (nb + ksplit - 1) / ksplit;
-  const int64_t parts = (nb + per - 1) / per;
+  const int64_t nb = div_idx(p.K, I);
+  const int64_t per = div_idx(nb + ksplit - 1, ksplit);
+  const int64_t parts = div_idx(nb + per - 1, per);
   const int64_t items = nL * p.n_q * parts;
   for (int64_t it = warp; it < items; it += nwarps) {
-    const int64_t ks = it % parts;
-    const int64_t t2 = it / parts;
-    const int64_t b = t2 / nL;
+    const int64_t t2 = div_idx(it, parts);
+    const int64_t ks = it - t2 * parts;
+    const int64_t b = div_idx(t2, nL);
     const int64_t l = t2 - b * nL;
     const int Q = batch_irrep(p, (int)b);
     // the row offsets, one per lane: lane 0 L's row, lanes 1..NS the short
@@ -293,7 +304,7 @@ __global__ void __launch_bounds__(THREADS, 3) gemm_f64_skinny(const __grid_const
       // inner-block offsets when the block changes
       const int64_t kend = ob1 * I;
       int64_t k = ob0 * I + lane;
-      int64_t o = k / I, i = k - o * I;
+      int64_t o = div_idx(k, I), i = k - o * I;
       int64_t lo = es * aoff(Lcols, p.g, Q, o * I), so = es * aoff(Scols, p.g, Q, o * I);
       for (; k < kend; k += 32) {
         const double x = Lp[loff + lo + tab_l[i]];
@@ -398,10 +409,10 @@ __global__ void __launch_bounds__(THREADS, 4) gemm_f64_shortk(const __grid_const
   const int task0 = (threadIdx.x & 31) * (THREADS / 32) + (threadIdx.x >> 5);
   int staged = -1;
   for (int64_t blk = blockIdx.x; blk < per_q * p.n_q; blk += gridDim.x) {
-    const int b = (int)(blk / per_q);
+    const int b = (int)div_idx(blk, per_q);
     const int64_t l0 = (blk - (int64_t)b * per_q) * kShortRows;
     const int64_t lend = l0 + kShortRows < nL ? l0 + kShortRows : nL;
-    const int64_t o0 = l0 / I;
+    const int64_t o0 = div_idx(l0, I);
     const int Q = batch_irrep(p, b);
     __syncthreads();   // the previous chunk's readers are done
     // one offset per task: on a new irrep first the short rows in S, S's and
@@ -409,7 +420,7 @@ __global__ void __launch_bounds__(THREADS, 4) gemm_f64_shortk(const __grid_const
     // offsets of the chunk's inner blocks (alternating)
     const bool stage = b != staged;
     const int n_s = stage ? 2 * NS + 2 * K : 0;
-    const int n_t = n_s + (tabulated ? 2 * (int)((lend - 1) / I - o0 + 1) : 0);
+    const int n_t = n_s + (tabulated ? 2 * (int)(div_idx(lend - 1, I) - o0 + 1) : 0);
     for (int t = task0; t < n_t; t += THREADS) {
       const AxisMap* m;
       int64_t r, sc = es;
@@ -467,7 +478,7 @@ __global__ void __launch_bounds__(THREADS, 4) gemm_f64_shortk(const __grid_const
       continue;
     }
     // (o, i) of the thread's first row by one division
-    int64_t o = (l0 + threadIdx.x) / I;
+    int64_t o = div_idx(l0 + threadIdx.x, I);
     int64_t i = l0 + threadIdx.x - o * I;
     for (int64_t l = l0 + threadIdx.x; l < lend; l += (int64_t)THREADS * RU) {
       // RU rows: first every load (K known), then the FMAs and stores, the
@@ -491,9 +502,11 @@ __global__ void __launch_bounds__(THREADS, 4) gemm_f64_shortk(const __grid_const
           const int64_t wo = ob_w[o - o0] + tab_w[i];
 #pragma unroll
           for (int sr = 0; sr < NS; ++sr) {
-            double a = 0.0;
+            // the sum starts from the first product (not an FMA onto 0.0:
+            // the float64 pipe is the bound here)
+            double a = x[r][0] * sval[sr][0];
 #pragma unroll
-            for (int k = 0; k < KX; ++k) a = fma(x[r][k], sval[sr][k], a);
+            for (int k = 1; k < KX; ++k) a = fma(x[r][k], sval[sr][k], a);
             store_w(p, W + (wo + wso[sr]), a);
           }
           step_rows(I, o, i);

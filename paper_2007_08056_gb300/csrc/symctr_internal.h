@@ -185,16 +185,25 @@ struct Problem {
 };
 
 #ifdef __CUDACC__
-// The result with the problem's sign (a sign-bit flip, no float64 arithmetic).
+// The result with the problem's sign: a flip of the sign bit, as an integer
+// XOR in inline PTX.  Written in C++, the conditional XOR may be folded into a
+// float64 negation, which GB300 issues on its narrow float64 pipe for every
+// stored value.
 __device__ __forceinline__ double signed_result(const Problem& p, double x) {
-  return p.negate ? __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ull) : x;
+  const unsigned mask = p.negate ? 0x80000000u : 0u;
+  unsigned hi = (unsigned)__double2hiint(x);
+  asm("xor.b32 %0, %0, %1;" : "+r"(hi) : "r"(mask));
+  return __hiloint2double((int)hi, __double2loint(x));
 }
 
-// Store of one result into W under the problem's output mode.
+// Store of one result into W under the problem's output mode.  The
+// accumulating store is a float64 atomic add (performed in L2, each entry
+// with a single writer: the same rounded sum), so that neither mode puts a
+// float64 add on the narrow float64 pipe.
 __device__ __forceinline__ void store_w(const Problem& p, double* dst, double x) {
   x = signed_result(p, x);
   if (p.accumulate)
-    *dst += x;
+    atomicAdd(dst, x);
   else
     *dst = x;
 }
