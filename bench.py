@@ -698,6 +698,27 @@ def run_small(args, rank, world):
             ts.append(ev_s.elapsed_time(ev_e))
         return statistics.median(ts)
 
+    def graphed(fn):
+        """fn captured once as a CUDA graph: (replay, None), or (None, why)
+        when the capture fails.  Warm-up and capture share one side stream, so
+        the plans have seen it before the capture starts."""
+        try:
+            side = torch.cuda.Stream()
+            side.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(side):
+                for _ in range(3):
+                    fn()
+            torch.cuda.current_stream().wait_stream(side)
+            torch.cuda.synchronize()
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=side):
+                fn()
+            torch.cuda.synchronize()
+            return g.replay, None
+        except Exception as e:
+            torch.cuda.synchronize()
+            return None, f"graph capture failed: {type(e).__name__}"
+
     if args.workload == "z3":
         c = WL.Z3_ORDER4
         uh, vh = WL.draw_pair(c)
@@ -727,8 +748,13 @@ def run_small(args, rank, world):
         y = sc.contract(py, T, Env)
         sc.contract(pl, y, y).backward()
 
-    ms = max_over_ranks(timed(step), world, dev)
-    step()
+    # The step issues about a dozen launches through autograd; replayed as one
+    # CUDA graph it no longer waits on the host between them.  The eager step
+    # is timed too.
+    ms_eager = max_over_ranks(timed(step), world, dev)
+    replay, graph_note = graphed(step)
+    ms = max_over_ranks(timed(replay), world, dev) if replay else ms_eager
+    (replay or step)()
     torch.cuda.synchronize()
     oy = O.plan(WL.PEPS_Y, O.Group(moduli), O.Sym(*spec(WL.PEPS_T)), O.Sym(*spec(WL.PEPS_ENV)))
     y_ref = O.contract_blockloop(oy, Th, Envh)
@@ -748,6 +774,8 @@ def run_small(args, rank, world):
     pk = peaks()
     return {"workload": "peps_grad (config 4: Z_2 x Z_3, T [6,6,6,6,16,16,16,16,2], Env [6,6,6,16,16,16,16])",
             "precision": args.precision, "ms_per_step": round(ms, 4),
+            "step": "CUDA graph replay" if replay else f"eager ({graph_note})",
+            "ms_per_step_eager": round(ms_eager, 4),
             "useful_tflops": round(replicas_value(flops, ms, world), 4),
             "roofline": {"kernel": "whole step (gemm_f64 GEMVs, fill, align)", "bound": "hbm",
                          "achieved": round(achieved, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
