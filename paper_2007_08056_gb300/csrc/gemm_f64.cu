@@ -361,14 +361,23 @@ struct ShortUnroll {
   static constexpr int value = KT == 1 ? 8 : (KT == 2 ? 4 : 2);
 };
 
-// Step (o, i) = divmod(l, I) by THREADS rows without dividing (64-bit integer
-// division runs on GB300's narrow float64 pipe).
-__device__ __forceinline__ void step_rows(int64_t I, int64_t& o, int64_t& i) {
+// Step (o, i) = divmod(l, I) by THREADS rows without dividing.
+__device__ __forceinline__ void step_rows(int I, int& o, int& i) {
   i += THREADS;
   while (i >= I) {
     i -= I;
     ++o;
   }
+}
+
+// A W entry of the short-K kernel, whose staged short-side values carry the
+// problem's sign (exact: x * (-s) = -(x * s)).  Accumulation is a float64
+// atomic add (a single writer per entry: the same rounded sum).
+__device__ __forceinline__ void put_w(int accumulate, double* dst, double x) {
+  if (accumulate)
+    atomicAdd(dst, x);
+  else
+    *dst = x;
 }
 
 // KT: K itself when it is 1 or 2 (the loads of a row unrolled), 0 for any
@@ -455,7 +464,7 @@ __global__ void __launch_bounds__(THREADS, 4) gemm_f64_shortk(const __grid_const
     if (stage) {
       for (int i = threadIdx.x; i < NS * K; i += THREADS) {
         const int sr = i / K, k = i - sr * K;
-        sval[sr][k] = Sp[es * (srow[sr] + scol[k])];
+        sval[sr][k] = signed_result(p, Sp[es * (srow[sr] + scol[k])]);
       }
       staged = b;
       __syncthreads();
@@ -473,33 +482,34 @@ __global__ void __launch_bounds__(THREADS, 4) gemm_f64_shortk(const __grid_const
           for (int sr = 0; sr < NS; ++sr) acc[sr] = fma(x, sval[sr][k], acc[sr]);
         }
 #pragma unroll
-        for (int sr = 0; sr < NS; ++sr) store_w(p, W + (wo + wso[sr]), acc[sr]);
+        for (int sr = 0; sr < NS; ++sr) put_w(p.accumulate, W + (wo + wso[sr]), acc[sr]);
       }
       continue;
     }
-    // (o, i) of the thread's first row by one division
-    int64_t o = div_idx(l0 + threadIdx.x, I);
-    int64_t i = l0 + threadIdx.x - o * I;
-    for (int64_t l = l0 + threadIdx.x; l < lend; l += (int64_t)THREADS * RU) {
-      // RU rows: first every load (K known), then the FMAs and stores, the
-      // row offsets in W found again from the saved (o, i)
-      const int64_t os = o, is = i;
+    // (o - o0, i) of the thread's first row by one division; rows and inner
+    // positions within a chunk in 32 bits (a chunk spans kShortRows rows)
+    const int nrows = (int)(lend - l0), Ii = (int)I;
+    int orel = (int)(div_idx(l0 + threadIdx.x, I) - o0);
+    int i = (int)(l0 + threadIdx.x - (o0 + orel) * I);
+    for (int t = threadIdx.x; t < nrows; t += THREADS * RU) {
+      // RU rows: every load first, then the products and stores, the W
+      // offsets found again from the saved (o - o0, i)
+      const int os = orel, is = i;
       if (KT > 0) {
         double x[RU][KX];
 #pragma unroll
         for (int r = 0; r < RU; ++r) {
-          const bool ok = l + (int64_t)r * THREADS < lend;
-          const int64_t lo = ok ? ob_l[o - o0] + tab_lr[i] : 0;
+          const bool ok = t + r * THREADS < nrows;
+          const int64_t lo = ok ? ob_l[orel] + tab_lr[i] : 0;
 #pragma unroll
           for (int k = 0; k < KX; ++k) x[r][k] = ok ? Lp[lo + lco[k]] : 0.0;
-          if (ok) step_rows(I, o, i);
+          if (ok) step_rows(Ii, orel, i);
         }
-        o = os;
-        i = is;
+        int o2 = os, i2 = is;
 #pragma unroll
         for (int r = 0; r < RU; ++r) {
-          if (l + (int64_t)r * THREADS >= lend) break;
-          const int64_t wo = ob_w[o - o0] + tab_w[i];
+          if (t + r * THREADS >= nrows) break;
+          const int64_t wo = ob_w[o2] + tab_w[i2];
 #pragma unroll
           for (int sr = 0; sr < NS; ++sr) {
             // the sum starts from the first product (not an FMA onto 0.0:
@@ -507,17 +517,19 @@ __global__ void __launch_bounds__(THREADS, 4) gemm_f64_shortk(const __grid_const
             double a = x[r][0] * sval[sr][0];
 #pragma unroll
             for (int k = 1; k < KX; ++k) a = fma(x[r][k], sval[sr][k], a);
-            store_w(p, W + (wo + wso[sr]), a);
+            put_w(p.accumulate, W + (wo + wso[sr]), a);
           }
-          step_rows(I, o, i);
+          step_rows(Ii, o2, i2);
         }
       } else {
+        int64_t wo[RU];
         int64_t lo[RU];
 #pragma unroll
         for (int r = 0; r < RU; ++r) {
-          const bool ok = l + (int64_t)r * THREADS < lend;
-          lo[r] = ok ? ob_l[o - o0] + tab_lr[i] : -1;
-          if (ok) step_rows(I, o, i);
+          const bool ok = t + r * THREADS < nrows;
+          lo[r] = ok ? ob_l[orel] + tab_lr[i] : -1;
+          wo[r] = ok ? ob_w[orel] + tab_w[i] : 0;
+          if (ok) step_rows(Ii, orel, i);
         }
         double acc[RU][NS];
 #pragma unroll
@@ -533,15 +545,11 @@ __global__ void __launch_bounds__(THREADS, 4) gemm_f64_shortk(const __grid_const
 #pragma unroll
             for (int sr = 0; sr < NS; ++sr) acc[r][sr] = fma(x[r], sval[sr][k], acc[r][sr]);
         }
-        o = os;
-        i = is;
 #pragma unroll
         for (int r = 0; r < RU; ++r) {
           if (lo[r] < 0) break;
-          const int64_t wo = ob_w[o - o0] + tab_w[i];
 #pragma unroll
-          for (int sr = 0; sr < NS; ++sr) store_w(p, W + (wo + wso[sr]), acc[r][sr]);
-          step_rows(I, o, i);
+          for (int sr = 0; sr < NS; ++sr) put_w(p.accumulate, W + (wo[r] + wso[sr]), acc[r][sr]);
         }
       }
     }
