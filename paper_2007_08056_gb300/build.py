@@ -20,7 +20,7 @@ LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libsymctr.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["plan.cpp", "transforms.cu", "gemm_f64.cu", "gemm_tc.cu", "static_scratch.cu"]
+SOURCES = ["plan.cpp", "transforms.cu", "gemm_f64.cu", "gemm_tc.cu", "fill.cu", "static_scratch.cu"]
 
 
 def nvcc() -> str:

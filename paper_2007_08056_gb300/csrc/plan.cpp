@@ -18,6 +18,7 @@
 #include <string>
 #include <vector>
 
+#include "fill.h"
 #include "symctr_internal.h"
 
 using namespace symctr;
@@ -269,6 +270,11 @@ struct symctr_plan {
   // W holds entries no aligned element covers (padding, sector tuples without
   // a solution): zeroed as a whole before each contraction
   bool fill_all = false;
+  // uniform plans whose irreps do not cover W: the sector combinations of W
+  // that the contraction writes whole (bit c of fill_written), each fill_bv
+  // doubles; the zero fill skips them (fill_bv == 0: zero all of W)
+  int64_t fill_bv = 0, fill_combos = 0;
+  std::vector<uint32_t> fill_written;
   symctr_plan* bwd_u = nullptr;
   symctr_plan* bwd_v = nullptr;
   bool prof = false;
@@ -709,6 +715,45 @@ symctr_status build(const char* einsum, int n_moduli, const int32_t* moduli, con
     }
   }
 
+  // Zero fill of the irreps that carry no work (uniform plans): a sector
+  // combination of W (its stored sector labels) is written at every block
+  // position by one irrep's row and column sector patterns, or not at all.
+  // The combinations written are found from the patterns' first entries and
+  // checked to hold exactly the n_q M N entries the contraction writes.
+  if (!P->general && (int64_t)pr.n_q * pr.M * pr.N < P->numel_w) {
+    int64_t bv = 1;
+    for (int i = 0; i < P->w.order(); ++i) bv *= P->w.dim[i];
+    const int64_t n_combo = bv > 0 ? P->numel_w / bv : 0;
+    if (n_combo > 0 && n_combo <= kFillMaskCombos && n_combo * bv == P->numel_w) {
+      std::vector<uint32_t> mask((size_t)(n_combo + 31) / 32, 0u);
+      const AxisMap& R = pr.w.rows;
+      const AxisMap& Cm = pr.w.cols;
+      int64_t rb = 1, cb = 1;
+      for (int i = 0; i < R.n; ++i) rb *= R.D[i];
+      for (int i = 0; i < Cm.n; ++i) cb *= Cm.D[i];
+      const int64_t rp = R.size / rb, cp = Cm.size / cb;
+      bool ok = rp * rb == pr.M && cp * cb == pr.N;
+      for (int b = 0; b < pr.n_q && ok; ++b) {
+        const int Q = batch_irrep(pr, b);
+        for (int64_t i = 0; i < rp && ok; ++i) {
+          const int64_t ro = axis_offset(R, pr.g, Q, i * rb);
+          for (int64_t j = 0; j < cp && ok; ++j) {
+            const int64_t c = (ro + axis_offset(Cm, pr.g, Q, j * cb)) / bv;
+            ok = c >= 0 && c < n_combo;
+            if (ok) mask[(size_t)(c >> 5)] |= 1u << (c & 31);
+          }
+        }
+      }
+      int64_t written = 0;
+      for (uint32_t m : mask) written += __builtin_popcount(m);
+      if (ok && written * bv == (int64_t)pr.n_q * pr.M * pr.N) {
+        P->fill_bv = bv;
+        P->fill_combos = n_combo;
+        P->fill_written.swap(mask);
+      }
+    }
+  }
+
   // Single-read preparation (split form): an operand whose aligned rows are
   // column-contiguous runs of at least 128 entries, at most kRowClusterMaxK
   // long (clusters of CTAs beyond kRowStreamMaxK), every run start and row
@@ -916,7 +961,11 @@ symctr_status run_contract_body(const symctr_plan* P, const double* u, const dou
   // solution: those plans zero W as a whole first.
   const int64_t fill_n = mode.fill_n < 0 ? P->numel_w : mode.fill_n;
   if ((P->fill_all || (int64_t)pr.n_q * pr.M * pr.N < P->numel_w) && fill_n > 0) {
-    e = launch_fill_zero(w, fill_n, st);
+    // W's own reduced form, real entries: only the sector blocks no irrep writes
+    if (P->fill_bv > 0 && !P->fill_all && !P->general && mode.fill_n < 0 && mode.es == 1)
+      e = launch_fill_dead(w, P->fill_bv, P->fill_combos, P->fill_written.data(), st);
+    else
+      e = launch_fill_zero(w, fill_n, st);
     if (e != cudaSuccess) return cuda_status(e, "zero fill");
   }
   if (pr.n_q == 0) return SYMCTR_OK;

@@ -187,8 +187,8 @@ def test_config4_peps_gradients(sc):
 def test_config4_peps_split_form_gradient(sc, precision):
     """A plan made in the split form on the skinny PEPS contractions, against
     the oracle gradient.  The split form does not run here: every contraction of
-    this step is a GEMV or an outer product (M = 2, or K <= 2), below the
-    32 x 32 x 16 shape the tensor-core forms take, so the library routes it to
+    this step is a GEMV or an outer product (one side of 1 or 2 rows), below the
+    M, N >= 8 the tensor-core forms take, so the library routes it to
     the float64 CUDA-core kernels (plan.info.tensor_core == 0, asserted below);
     the result is then exact to float64 rounding."""
     moduli = WL.PEPS_MODULI

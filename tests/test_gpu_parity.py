@@ -136,6 +136,27 @@ def test_gemv_and_adjoints_many_chunks(sc, p_dim):
     assert rel(host(gE), O.grad_v(oy, T, gy)) <= 1e-12
 
 
+@pytest.mark.parametrize("precision", ["fp64", "split_bf16"])
+def test_outer_product_fills_only_unwritten_sectors(sc, precision):
+    """An outer product under Z_2 x Z_3 (W's sector combinations: 6^4, one in
+    six written by the single irrep that carries work) into an output filled
+    with 7.0 first: the zero fill skips the written sector blocks, so every
+    other entry must still come out exactly zero and every written one must
+    match the oracle."""
+    moduli = (2, 3)
+    su = ((-1, -1, 1, 1), (0, 0), (6, 6, 6, 6))
+    sv = ((1,), (0, 0), (2,))
+    u = WL.draw(WL.TensorSpec(*su, 1.0, 4311), moduli)
+    v = WL.draw(WL.TensorSpec(*sv, 1.0, 4312), moduli)
+    p = sc.Plan("uldr,p->uldrp", moduli, su, sv, precision)
+    w = torch.full(p.shape_w, 7.0, dtype=torch.float64, device="cuda")
+    p.contract(dev(u), dev(v), out=w)
+    want = O.contract_blockloop(oplan("uldr,p->uldrp", moduli, su, sv), u, v)
+    got = host(w)
+    assert not got[want == 0].any()
+    assert rel(got, want) <= 1e-12
+
+
 # ---------------------------------------------------------------------------
 # the paper-shaped workloads
 # ---------------------------------------------------------------------------
