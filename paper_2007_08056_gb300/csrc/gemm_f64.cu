@@ -468,6 +468,9 @@ __global__ void __launch_bounds__(THREADS, 4) gemm_f64_shortk(const __grid_const
       staged = b;
       __syncthreads();
     }
+    // a row's two columns of L (two short rows of W) adjacent in memory
+    const bool pair_l = K == 2 && lco[1] == lco[0] + 1;
+    const bool pair_w = NS == 2 && wso[1] == wso[0] + 1;
     if (!tabulated) {
       // short inner blocks: the offsets of each row from scratch
       for (int64_t l = l0 + threadIdx.x; l < lend; l += THREADS) {
@@ -500,8 +503,16 @@ __global__ void __launch_bounds__(THREADS, 4) gemm_f64_shortk(const __grid_const
         for (int r = 0; r < RU; ++r) {
           const bool ok = t + r * THREADS < nrows;
           const int64_t lo = ok ? ob_l[orel] + tab_lr[i] : 0;
+          const double* src = Lp + (lo + lco[0]);
+          if (KX == 2 && ok && pair_l && ((uintptr_t)src & 15) == 0) {
+            // a row's two entries adjacent: one 16-byte load
+            const double2 v2 = *reinterpret_cast<const double2*>(src);
+            x[r][0] = v2.x;
+            x[r][KX - 1] = v2.y;
+          } else {
 #pragma unroll
-          for (int k = 0; k < KX; ++k) x[r][k] = ok ? Lp[lo + lco[k]] : 0.0;
+            for (int k = 0; k < KX; ++k) x[r][k] = ok ? Lp[lo + lco[k]] : 0.0;
+          }
           if (ok) step_rows(Ii, orel, i);
         }
         int o2 = os, i2 = is;
@@ -509,14 +520,22 @@ __global__ void __launch_bounds__(THREADS, 4) gemm_f64_shortk(const __grid_const
         for (int r = 0; r < RU; ++r) {
           if (t + r * THREADS >= nrows) break;
           const int64_t wo = ob_w[o2] + tab_w[i2];
+          double a[NS];
 #pragma unroll
           for (int sr = 0; sr < NS; ++sr) {
             // the sum starts from the first product (not an FMA onto 0.0:
             // the float64 pipe is the bound here)
-            double a = x[r][0] * sval[sr][0];
+            a[sr] = x[r][0] * sval[sr][0];
 #pragma unroll
-            for (int k = 1; k < KX; ++k) a = fma(x[r][k], sval[sr][k], a);
-            put_w(p.accumulate, W + (wo + wso[sr]), a);
+            for (int k = 1; k < KX; ++k) a[sr] = fma(x[r][k], sval[sr][k], a[sr]);
+          }
+          double* dst = W + (wo + wso[0]);
+          if (NS == 2 && pair_w && !p.accumulate && ((uintptr_t)dst & 15) == 0) {
+            // the row's two results adjacent: one 16-byte store
+            *reinterpret_cast<double2*>(dst) = make_double2(a[0], a[NS - 1]);
+          } else {
+#pragma unroll
+            for (int sr = 0; sr < NS; ++sr) put_w(p.accumulate, W + (wo + wso[sr]), a[sr]);
           }
           step_rows(Ii, o2, i2);
         }
