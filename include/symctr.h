@@ -123,9 +123,9 @@ typedef struct {
                                    plan has no offset tables, e.g. the float64 form) */
   int32_t tensor_core;          /* 1: the GEMM of the precision form runs on tcgen05;
                                    0: it runs on the float64 CUDA-core kernels (the float64
-                                   form, or an aligned GEMM below 32 x 32 x 16 in M x N x K,
-                                   e.g. a GEMV, where the tensor-core forms would gain
-                                   nothing; the result is then exact to float64 rounding) */
+                                   form, or an aligned GEMM with M or N below 8, e.g. a GEMV,
+                                   where the tensor-core forms would gain nothing; the
+                                   result is then exact to float64 rounding) */
   int32_t general;              /* 1: some mode has fewer than G sectors or non-uniform
                                    sector sizes (symctr_plan_create_general) */
   int32_t q_first, q_step;      /* batch b of the aligned forms is irrep
@@ -143,6 +143,12 @@ typedef struct {
                                    data takes the two-phase kernel) */
   int32_t chained;              /* 1 after symctr_plan_chain re-laid the plan out (numel_u,
                                    numel_v, numel_w then count the chained layouts) */
+  int64_t zero_fill_numel;      /* entries of W a contraction zeroes before the GEMM writes
+                                   the rest (Alg. 2's output step: entries of irreps that
+                                   carry no work are zero): 0 when the irreps cover W;
+                                   numel_w for general plans; otherwise the sector blocks
+                                   of W that no irrep writes (uniform plans of at most 8192
+                                   sector combinations; numel_w beyond) */
 } symctr_plan_info;
 
 /* One operand in the general form of Eq. symtsr, for symctr_plan_create_general.

@@ -65,7 +65,7 @@ class PlanInfo(ctypes.Structure):
         ("tensor_core", ctypes.c_int32), ("general", ctypes.c_int32),
         ("q_first", ctypes.c_int32), ("q_step", ctypes.c_int32),
         ("sectors_w", ctypes.c_int32 * MAX_ORDER), ("single_read_prep", ctypes.c_int32),
-        ("chained", ctypes.c_int32),
+        ("chained", ctypes.c_int32), ("zero_fill_numel", ctypes.c_int64),
     ]
 
 

@@ -1298,6 +1298,18 @@ symctr_status symctr_plan_query(const symctr_plan* P, symctr_plan_info* o) {
   o->single_read_prep = (P->row_run[0] > 0 ? 1 : 0) | (P->row_run[1] > 0 ? 2 : 0) |
                         (P->row_tile[0] ? 4 : 0) | (P->row_tile[1] ? 8 : 0);
   o->chained = P->chained ? 1 : 0;
+  // what a contraction zeroes first (real W in its own reduced form): the
+  // sector blocks no irrep writes, all of W, or nothing
+  o->zero_fill_numel = 0;
+  if (P->fill_all || (int64_t)pr.n_q * pr.M * pr.N < P->numel_w) {
+    if (P->fill_bv > 0 && !P->fill_all && !P->general) {
+      int64_t written = 0;
+      for (uint32_t m : P->fill_written) written += __builtin_popcount(m);
+      o->zero_fill_numel = (P->fill_combos - written) * P->fill_bv;
+    } else {
+      o->zero_fill_numel = P->numel_w;
+    }
+  }
   return SYMCTR_OK;
 }
 

@@ -205,6 +205,40 @@ def test_preparation_kernel_of_each_operand_is_reported():
     assert p.info.single_read_prep == 4 | 8
 
 
+def test_zero_fill_of_unwritten_sector_blocks():
+    """plan.info.zero_fill_numel: the entries of W a contraction zeroes before
+    the GEMM writes the rest (Alg. 2: entries of irreps that carry no work are
+    zero).  In a uniform plan only the sector blocks no irrep writes are
+    zeroed; the count is compared with the oracle's own sector bookkeeping
+    (the share of W's sector combinations whose implicit sector puts them in
+    an irrep that carries work)."""
+    spec = lambda t: (t.signs, t.charge, t.dims)
+    # an outer product under Z_2 x Z_3: one irrep carries work, and it writes
+    # one sixth of W's 6^4 sector combinations
+    su, sv = ((-1, -1, 1, 1), (0, 0), (6, 6, 6, 6)), ((1,), (0, 0), (2,))
+    for prec in ("fp64", "split_bf16"):
+        p = sc.Plan("uldr,p->uldrp", (2, 3), su, sv, prec)
+        assert p.info.n_q == 1 and p.info.aligned_numel_w * 6 == p.info.numel_w
+        assert p.info.zero_fill_numel == p.info.numel_w - p.info.aligned_numel_w
+    # the same count from the oracle's plan: W entries outside the live irrep
+    o = O.plan("uldr,p->uldrp", O.Group((2, 3)), O.Sym(*su), O.Sym(*sv))
+    G, M, N, K = O.aligned_dims(o)
+    assert int(np.prod(O.reduced_shape(o.group, o.sym_w))) - M * N == p.info.zero_fill_numel
+    # irreps covering W: nothing zeroed (the CC ladder, config 4's GEMV)
+    c = WL.CC_LADDER
+    assert sc.Plan(c.einsum, c.moduli, spec(c.u), spec(c.v), "split_bf16").info.zero_fill_numel == 0
+    y = sc.Plan(WL.PEPS_Y, WL.PEPS_MODULI, spec(WL.PEPS_T), spec(WL.PEPS_ENV), "fp64")
+    assert y.info.numel_w == y.info.aligned_numel_w and y.info.zero_fill_numel == 0
+    # no irrep carries work: all of W
+    p0 = sc.Plan("ij,ij->", (4,), ((1, -1), (1,), (3, 3)), ((1, -1), (2,), (3, 3)), "fp64")
+    assert p0.info.n_q == 0 and p0.info.zero_fill_numel == p0.info.numel_w
+    # general plans zero all of W
+    gp, _, _ = _general_cases()[0]
+    q = sc.Plan(f"{gp.lu},{gp.lv}->{gp.lw}", gp.group.moduli, _as_spec(gp.sym_u), _as_spec(gp.sym_v),
+                "fp64")
+    assert q.info.zero_fill_numel == q.info.numel_w
+
+
 class _FakeTensor:
     def __init__(self, dev):
         self.dev = dev
