@@ -200,10 +200,9 @@ struct SkinnyUnroll {
 // resident warps once, which pays the offset arithmetic of an item (a
 // dependent chain of modular arithmetic under a product group) once per warp.
 template <int NS>
-__global__ void __launch_bounds__(THREADS, 3) gemm_f64_skinny(const __grid_constant__ Problem p, bool long_is_u, int ksplit,
-                                                           const double* __restrict__ U,
-                                                           const double* __restrict__ V,
-                                                           double* __restrict__ W) {
+__global__ void __launch_bounds__(THREADS, 3)
+    gemm_f64_skinny(const __grid_constant__ Problem p, bool long_is_u, int ksplit, const double* __restrict__ U,
+                    const double* __restrict__ V, double* __restrict__ W) {
   __shared__ int64_t tab_l[kInnerMax], tab_s[kInnerMax];
   const AxisMap& Lrows = long_is_u ? p.u.rows : p.v.rows;
   const AxisMap& Lcols = long_is_u ? p.u.cols : p.v.cols;
@@ -382,10 +381,9 @@ __device__ __forceinline__ void put_w(int accumulate, double* dst, double x) {
 // KT: K itself when it is 1 or 2 (the loads of a row unrolled), 0 for any
 // K <= kShortK (a loop over K).
 template <int NS, int KT>
-__global__ void __launch_bounds__(THREADS, 4) gemm_f64_shortk(const __grid_constant__ Problem p, bool long_is_u,
-                                                              const double* __restrict__ U,
-                                                              const double* __restrict__ V,
-                                                              double* __restrict__ W) {
+__global__ void __launch_bounds__(THREADS, 4)
+    gemm_f64_shortk(const __grid_constant__ Problem p, bool long_is_u, const double* __restrict__ U,
+                    const double* __restrict__ V, double* __restrict__ W) {
   __shared__ double sval[SKINNY_MAX][kShortK];
   __shared__ int64_t lco[kShortK], scol[kShortK];
   __shared__ int64_t wso[SKINNY_MAX], srow[SKINNY_MAX];
