@@ -339,10 +339,11 @@ __global__ void __launch_bounds__(THREADS, 3)
   }
 }
 
-// Skinny problems with K <= kShortK: one thread per row of the long side, a
-// block taking kShortRows consecutive rows at a time.  The short side's
-// values and the long side's column offsets depend only on the irrep, so a
-// block stages them in shared memory when the irrep changes.  Row offsets in
+// Skinny problems with K <= kShortK: one thread per row of the long side, on
+// a persistent grid whose blocks take kShortRows consecutive rows (a chunk)
+// at a time.  The short side's values and the long side's column offsets
+// depend only on the irrep, so a block stages them in shared memory when the
+// irrep changes.  Row offsets in
 // L and W use the inner-block split of the skinny kernel above (l = o * I +
 // i): a table of inner(i) per map, and aoff(o * I) for the inner blocks of a
 // chunk computed by as many threads at once, spread over the warps (the
